@@ -1,0 +1,217 @@
+/*
+ * dts.h -- C ABI of the B300 discrete-ordinates (S_N) photon-transport solver.
+ *
+ * The library solves the multigroup, discrete-direction linear Boltzmann
+ * equation on a voxel grid (Eq. 2 of Norris, Wagstaff & Liu, "DOCTORS",
+ * arxiv 1910.11335) with vacuum boundaries (Sec. II.A) by source iteration:
+ * energy groups run from high energy (group 0) to low, because scattering only
+ * moves photons down in energy; inside a group every octant is swept along
+ * i+j+k wavefronts (Sec. II.B, Eqs. 8-22) with all of its level-symmetric
+ * directions (Sec. II.E: S2/S4/S6/S8) in flight, using diamond difference
+ * (Sec. IV) with a set-to-zero negative-flux fixup; the sweep is fed by a
+ * Legendre-moment scatter source and reduced to scalar fluence by the
+ * quadrature of Eq. 3. Point and cone-beam sources use the first-collision
+ * split of Eqs. 4-7: the uncollided fluence is ray traced and its first
+ * collisions drive the collided solve.
+ *
+ * Conventions (every entry point):
+ *   - Voxel arrays are [nz][ny][nx] with x fastest; V = nx*ny*nz.
+ *   - Group arrays put group 0 at the highest energy.
+ *   - Every call returns a dts_status and never throws. On failure the
+ *     problem keeps a message readable with dts_last_error(problem); failures
+ *     of dts_create_problem leave it in dts_last_error(NULL) (per thread).
+ *   - The caller owns every buffer it passes in or out. Input arrays are
+ *     copied before the call returns. Host pointers must stay valid only for
+ *     the duration of the call.
+ *   - All device work is ordered on the stream given in dts_problem_desc
+ *     (or an internal stream when that is NULL). One problem must be used by
+ *     one host thread at a time. Distinct problems are independent.
+ *   - Pointers named *_is_device select device (1) or host (0) memory.
+ */
+#ifndef DTS_H
+#define DTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dts_problem dts_problem;   /* opaque, owned by the library */
+
+typedef enum {
+    DTS_OK = 0,
+    DTS_ERR_INVALID_ARG = 1,    /* a size, pointer or value is out of range */
+    DTS_ERR_STATE = 2,          /* call order violated (e.g. solve before set_*) */
+    DTS_ERR_OOM = 3,            /* device or host allocation failed */
+    DTS_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    DTS_ERR_NOT_CONVERGED = 5,  /* max_iters reached above tol; results are usable */
+    DTS_ERR_TIMEOUT = 6,        /* reserved: a bounded device wait gave up */
+    DTS_ERR_INTERNAL = 7        /* a device-side consistency check failed */
+} dts_status;
+
+/* Arithmetic of the sweep and of the moment<->direction contractions.
+ * FP64: everything in FP64.
+ * FP32: sweep, scatter-source contraction and per-octant moment partials in
+ *       FP32; the Eq. 3 octant sum, the residual, the fixed sources and the
+ *       balance in FP64. */
+typedef enum {
+    DTS_PREC_FP64 = 0,
+    DTS_PREC_FP32 = 1
+} dts_precision;
+
+typedef enum {
+    DTS_COMP_UNCOLLIDED = 0,    /* ray-traced uncollided fluence (Eq. 4) */
+    DTS_COMP_COLLIDED = 1,      /* source-iteration fluence (Eqs. 6-7) */
+    DTS_COMP_TOTAL = 2          /* uncollided + collided (Sec. II.A) */
+} dts_component;
+
+typedef struct {
+    int nx, ny, nz;             /* voxels per axis, each >= 1 */
+    double dx, dy, dz;          /* voxel pitch in cm, > 0 */
+    double x0, y0, z0;          /* low corner of the grid in cm */
+    int n_groups;               /* G >= 1 */
+    int sn_order;               /* level-symmetric order N in {2,4,6,8}: N(N+2) directions */
+    int legendre_order;         /* scattering order L in 0..3: K = (L+1)^2 moments */
+    int batch;                  /* B >= 1 independent sources solved together */
+    dts_precision precision;
+    double tol;                 /* stop a (source, group) when the relative L2 change of
+                                   its scalar fluence drops below tol; 0 runs max_iters */
+    int max_iters;              /* source iterations per group, >= 1 */
+    void *cuda_stream;          /* cudaStream_t to order work on, or NULL */
+    int device;                 /* CUDA device ordinal */
+    int tile_x, tile_y, tile_z; /* wavefront tile in voxels (each 1..16); all 0 = tuned */
+    int keep_moments;           /* 1: keep all K collided moments of every group */
+} dts_problem_desc;
+
+typedef struct {
+    int kind;                   /* 0: isotropic volumetric source; 1: point / cone beam */
+    const double *q;            /* kind 0: [G][V] photons/cm^3 (total over 4 pi), host */
+    double pos[3];              /* kind 1: source position, cm (outside or inside the grid) */
+    double axis[3];             /* kind 1: cone axis (any non-zero length) */
+    double half_angle;          /* kind 1: cone half-angle in radians, (0, pi]; pi = isotropic */
+    const double *spectrum;     /* kind 1: [G] photons per source particle, host */
+} dts_source;
+
+typedef struct {
+    int64_t updates;            /* cell-direction-group updates executed: sum over executed
+                                   sweeps of V * N(N+2) */
+    int64_t sweeps;             /* executed (source, group, iteration) sweeps */
+    double max_residual;        /* largest final residual over sources and groups */
+    double solve_ms;            /* device time of dts_solve, CUDA events on the stream */
+    double sweep_ms;            /* device time of the wavefront sweep launches (all stages) */
+    double reduce_ms;           /* device time of the Eq. 3 reduction + residual launches */
+    int64_t launches;           /* kernels launched by this solve */
+    int converged;              /* 1 when every (source, group) reached tol */
+    int tile_x, tile_y, tile_z; /* wavefront tile used */
+} dts_solve_stats;
+
+/*
+ * Create a problem: validates desc, builds the quadrature (Sec. II.E) and the
+ * wavefront schedule (Eqs. 8-22, applied to tiles), and allocates every
+ * device buffer the solve needs (FP64 fluence outputs [B][G][V] for the
+ * uncollided and collided parts, per-octant moment partials, fixed-source
+ * ring, face buffers). Errors: DTS_ERR_INVALID_ARG for a bad desc,
+ * DTS_ERR_OOM, DTS_ERR_CUDA. *out is NULL on failure.
+ */
+dts_status dts_create_problem(const dts_problem_desc *desc, dts_problem **out);
+
+/*
+ * Materials (Sec. II.C: voxel phantom of material ids; multigroup library of
+ * total and Legendre scattering cross sections).
+ *   sigma_t [n_mat][G]          total cross section, 1/cm, finite and > 0
+ *   sigma_s [n_mat][L+1][G][G]  [l][g_from][g_to] Legendre moments in the
+ *                               convention sigma_s(mu0) = sum_l (2l+1)/(4 pi)
+ *                               sigma_{s,l} P_l(mu0); must be zero for
+ *                               g_to < g_from (downscatter only)
+ *   mat_id  [V]                 material index per voxel, in [0, n_mat)
+ *   scale_t, scale_s [V]        optional per-voxel multipliers (> 0) of
+ *                               sigma_t and of every sigma_s entry; NULL = 1
+ * All pointers are host memory. Errors: DTS_ERR_INVALID_ARG.
+ */
+dts_status dts_set_materials(dts_problem *p, int n_mat, const double *sigma_t,
+                             const double *sigma_s, const int32_t *mat_id,
+                             const double *scale_t, const double *scale_s);
+
+/*
+ * Source of batch member batch_index (Sec. II.C source tab; Eqs. 4-5).
+ * kind 0: volumetric isotropic source q[G][V]; the uncollided component is
+ *         then zero and the collided component holds the whole fluence.
+ * kind 1: point source at pos emitting spectrum[g] photons per source particle
+ *         isotropically into the cone |angle(r - pos, axis)| <= half_angle.
+ * Errors: DTS_ERR_INVALID_ARG (index, kind, NULL or non-finite data).
+ */
+dts_status dts_set_source(dts_problem *p, int batch_index, const dts_source *src);
+
+/*
+ * Solve every batch member: ray trace (Eq. 4), first-collision source (Eq. 5),
+ * then for g = 0..G-1 source iteration to tol (Eqs. 2-3, 6-7) followed by the
+ * downscatter into later groups. Blocks until the results are on the device.
+ * stats may be NULL. Errors: DTS_ERR_STATE if materials or any source are
+ * missing; DTS_ERR_NOT_CONVERGED if some (source, group) stopped at max_iters
+ * with tol > 0 (results and stats are still filled); DTS_ERR_CUDA.
+ */
+dts_status dts_solve(dts_problem *p, dts_solve_stats *stats);
+
+/*
+ * Copy one component of the scalar fluence of batch member batch_index into
+ * out[G][V] (photons/cm^2 per source particle). out_len counts doubles and
+ * must be >= G*V. Device copies are ordered on the problem's stream; host
+ * copies complete before return. Errors: DTS_ERR_STATE before a solve,
+ * DTS_ERR_INVALID_ARG.
+ */
+dts_status dts_get_scalar_fluence(dts_problem *p, int batch_index, dts_component comp,
+                                  double *out, size_t out_len, int out_is_device);
+
+/*
+ * All K = (L+1)^2 collided flux moments of one group, out[K][V], ordered
+ * k = l*l + l + m with real spherical harmonics normalised so that
+ * sum_m Y_lm(a) Y_lm(b) = P_l(a.b); k = 0 is the Eq. 3 scalar fluence.
+ * Needs desc.keep_moments = 1 (else DTS_ERR_STATE).
+ */
+dts_status dts_get_moments(dts_problem *p, int batch_index, int group, double *out,
+                           size_t out_len, int out_is_device);
+
+/* Per (source, group) results of the last solve, host arrays:
+ *   iterations [B][G]; residuals [B][G] (final relative L2 change);
+ *   balance [B][G][3] = (sum_v V T_00, sum_v V sigma_t phi_00, leakage) of the
+ *   last sweep, whose difference is zero up to rounding (particle balance). */
+dts_status dts_get_iterations(dts_problem *p, int32_t *out, size_t out_len);
+dts_status dts_get_residuals(dts_problem *p, double *out, size_t out_len);
+dts_status dts_get_balance(dts_problem *p, double *out, size_t out_len);
+
+/* Message of the last failed call on p (or of the calling thread when p is
+ * NULL). Never NULL; valid until the next call on p. */
+const char *dts_last_error(const dts_problem *p);
+
+/* Releases every device and host resource of p. NULL is a no-op. */
+void dts_destroy_problem(dts_problem *p);
+
+/* Name of a status code. */
+const char *dts_status_string(dts_status s);
+
+/* ABI version, incremented on incompatible changes. */
+int dts_version(void);
+
+/*
+ * Host-side helpers (no device work; usable without a GPU).
+ * dts_quadrature: the level-symmetric set the solver uses (Sec. II.E), with
+ *   octant o = sx + 2 sy + 4 sz (a set bit = negative cosine) holding
+ *   directions o*N(N+2)/8 .. ; arrays of >= 80 doubles; *n_dirs = N(N+2).
+ * dts_moment_tables: the moment operator D[K][nd] (phi_k = sum_n D[k][n]
+ *   psi_n; D[0][n] = w_n is Eq. 3) and the source operator M[nd][K]
+ *   (Q_n = sum_k M[n][k] T_k).
+ * dts_subsweep_size: Eq. 9, the number of voxels of an nx x ny x nz box with
+ *   i_x + i_y + i_z = S (Eqs. 8, 10-22); the solver applies it to tiles.
+ */
+dts_status dts_quadrature(int sn_order, double *mu, double *eta, double *xi, double *w,
+                          int *n_dirs);
+dts_status dts_moment_tables(int sn_order, int legendre_order, double *D, double *M);
+long long dts_subsweep_size(int nx, int ny, int nz, int S);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTS_H */

@@ -1,0 +1,653 @@
+// dts_kernels.cuh -- sm_103a kernels of the S_N source-iteration solve.
+//
+// Data layout in HBM ("tiled"): the grid is cut into TX x TY x TZ tiles
+// (NT of them, padded at the high end of each axis); a per-cell array of one
+// batch member stores tile after tile, and inside a tile moment k after
+// moment k, each a contiguous run of TV = TX*TY*TZ cells (x fastest). So a
+// tile's K moments are one contiguous block and every phase below reads and
+// writes whole 32-byte sectors.
+//
+//   T    [B][NT][K][TV]   R       scatter + fixed source moments (this iteration)
+//   part [8][B][NT][K][TV] R      per-octant moment partials of the last sweep
+//   phi  [B][NT][K][TV]   double  flux moments of the current group
+//   F    [W+1][B][NT][K][TV] double fixed-source ring (first-collision + downscatter)
+//   xf   [8][B][NTy*NTz][NDO][TY*TZ] R  x-faces in flight (likewise yf, zf)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dts {
+
+constexpr int kSweepThreads = 256;
+constexpr int kRedThreads = 256;
+constexpr int kRayGroups = 16;
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// real spherical harmonics in Cartesian form, l <= 3, k = l*l + l + m,
+// normalised so that sum_m Y_lm(a) Y_lm(b) = P_l(a.b)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline void sh_eval(int L, double x, double y, double z, double* Y)
+{
+    Y[0] = 1.0;
+    if (L < 1) return;
+    Y[1] = y;
+    Y[2] = z;
+    Y[3] = x;
+    if (L < 2) return;
+    const double s3 = 1.7320508075688772;   // sqrt(3)
+    Y[4] = s3 * x * y;
+    Y[5] = s3 * y * z;
+    Y[6] = 0.5 * (3.0 * z * z - 1.0);
+    Y[7] = s3 * x * z;
+    Y[8] = 0.5 * s3 * (x * x - y * y);
+    if (L < 3) return;
+    const double s58 = 0.7905694150420949;  // sqrt(5/8)
+    const double s15 = 3.872983346207417;   // sqrt(15)
+    const double s38 = 0.6123724356957945;  // sqrt(3/8)
+    Y[9] = s58 * (3.0 * x * x * y - y * y * y);
+    Y[10] = s15 * x * y * z;
+    Y[11] = s38 * y * (5.0 * z * z - 1.0);
+    Y[12] = 0.5 * (5.0 * z * z * z - 3.0 * z);
+    Y[13] = s38 * x * (5.0 * z * z - 1.0);
+    Y[14] = 0.5 * s15 * z * (x * x - y * y);
+    Y[15] = s58 * (x * x * x - 3.0 * x * y * y);
+}
+
+__host__ __device__ inline int l_of_k(int k) { return k >= 9 ? 3 : k >= 4 ? 2 : k >= 1 ? 1 : 0; }
+
+// ---------------------------------------------------------------------------
+// block reduction of doubles (result valid in thread 0)
+// ---------------------------------------------------------------------------
+__device__ inline double block_sum(double v, double* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    v = 0.0;
+    if (wid == 0) {
+        v = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// diamond-difference cell solve with set-to-zero fixup (Sec. IV)
+// psi = (q + sum_d a_d in_d) / (sigma + sum_d a_d), out_d = 2 psi - in_d; a
+// negative out_d is zeroed and dropped from the closure, its face entering the
+// balance with a_d/2, until no new negative appears.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R dd_cell(R q, R sig, R ax, R ay, R az, R ix, R iy, R iz,
+                                     R& ox, R& oy, R& oz)
+{
+    R psi = (q + ax * ix + ay * iy + az * iz) / (sig + ax + ay + az);
+    ox = R(2) * psi - ix;
+    oy = R(2) * psi - iy;
+    oz = R(2) * psi - iz;
+    if (ox < R(0) || oy < R(0) || oz < R(0)) {
+        bool fx = false, fy = false, fz = false;
+#pragma unroll 1
+        for (int pass = 0; pass < 3; ++pass) {
+            const bool nx = !fx && ox < R(0), ny = !fy && oy < R(0), nz = !fz && oz < R(0);
+            if (!(nx || ny || nz)) break;
+            fx |= nx;
+            fy |= ny;
+            fz |= nz;
+            const R num = q + (fx ? R(0.5) * ax : ax) * ix + (fy ? R(0.5) * ay : ay) * iy +
+                          (fz ? R(0.5) * az : az) * iz;
+            const R den = sig + (fx ? R(0) : ax) + (fy ? R(0) : ay) + (fz ? R(0) : az);
+            psi = num / den;
+            ox = fx ? R(0) : R(2) * psi - ix;
+            oy = fy ? R(0) : R(2) * psi - iy;
+            oz = fz ? R(0) : R(2) * psi - iz;
+        }
+    }
+    return psi;
+}
+
+// ---------------------------------------------------------------------------
+// A3 + A4: one tile-wavefront stage of the sweep, all octants and batch
+// members of the stage in one launch. One CTA = (tile, octant, source).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct SweepParams {
+    int nx, ny, nz;
+    int TX, TY, TZ, TV;
+    int NTx, NTy, NTz, NT;
+    int B, nsub;
+    const unsigned* stage_tiles;   // octant-local tile (a | b<<10 | c<<20), sorted by a+b+c
+    const int* stage_off;
+    const unsigned* diag_cells;    // octant-local cell (x | y<<8 | z<<16), sorted by x+y+z
+    const int* diag_off;
+    const R* M;                    // [nd][K] source operator
+    const R* Dt;                   // [nd][K] moment operator (transposed)
+    const R* A;                    // [nd][3] a_d = 2|Omega_d|/Delta_d
+    const double* Lw;              // [nd][3] w_n |Omega_d| A_d (leakage weights)
+    const R* T;
+    const R* sigt;                 // [NT][TV]
+    R* part;
+    R* xf;
+    R* yf;
+    R* zf;
+    const int* active;             // [B]
+    double* leak;                  // [B]
+};
+
+template <typename R, int NDO, int K>
+__host__ __device__ inline size_t sweep_smem_bytes(int TX, int TY, int TZ)
+{
+    const int TV = TX * TY * TZ;
+    size_t n = (size_t)NDO * TV + (size_t)NDO * (TY * TZ + TX * TZ + TX * TY) + TV +
+               2 * NDO * K + 4 * NDO;
+    size_t bytes = n * sizeof(R);
+    bytes = (bytes + 15) & ~size_t(15);
+    return bytes + sizeof(double) * (3 * NDO + 32);
+}
+
+// resident CTAs per SM the register allocation must allow (FP32: 4, FP64: 2)
+template <typename R> struct SweepOcc { static constexpr int value = sizeof(R) == 4 ? 4 : 2; };
+
+template <typename R, int NDO, int K>
+__global__ void __launch_bounds__(kSweepThreads, SweepOcc<R>::value)
+k_sweep_stage(const SweepParams<R> p, const int stage)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int TX = p.TX, TY = p.TY, TZ = p.TZ, TV = p.TV;
+    const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
+    int bid = blockIdx.x;
+    const int tl = bid % cnt;
+    bid /= cnt;
+    const int oct = bid & 7, b = bid >> 3;
+    if (!p.active[b]) return;
+
+    const unsigned pk = p.stage_tiles[s0 + tl];
+    const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
+    const bool negx = oct & 1, negy = oct & 2, negz = oct & 4;
+    const int tx = negx ? p.NTx - 1 - ta : ta;
+    const int ty = negy ? p.NTy - 1 - tb : tb;
+    const int tz = negz ? p.NTz - 1 - tc : tc;
+    const int tile = (tz * p.NTy + ty) * p.NTx + tx;
+    const int fxn = TY * TZ, fyn = TX * TZ, fzn = TX * TY;
+
+    R* Qs = reinterpret_cast<R*>(smem);        // [NDO][TV]: source, then psi
+    R* fx = Qs + NDO * TV;                      // [NDO][TY*TZ]
+    R* fy = fx + NDO * fxn;                     // [NDO][TX*TZ]
+    R* fz = fy + NDO * fyn;                     // [NDO][TX*TY]
+    R* sg = fz + NDO * fzn;                     // [TV]
+    R* Ms = sg + TV;                            // [NDO][K]
+    R* Ds = Ms + NDO * K;                       // [K][NDO]
+    R* As = Ds + NDO * K;                       // [NDO][4]
+    size_t off = ((size_t)(As + 4 * NDO - Qs) * sizeof(R) + 15) & ~size_t(15);
+    double* Lw = reinterpret_cast<double*>(smem + off);   // [NDO][3]
+    double* red = Lw + 3 * NDO;                            // [32]
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int n0 = oct * NDO;
+    for (int i = tid; i < NDO * K; i += nth) {
+        Ms[i] = p.M[n0 * K + i];                         // [NDO][K]
+        Ds[(i % K) * NDO + i / K] = p.Dt[n0 * K + i];    // [K][NDO]
+    }
+    for (int i = tid; i < NDO * 3; i += nth) {
+        As[(i / 3) * 4 + i % 3] = p.A[n0 * 3 + i];
+        Lw[i] = p.Lw[n0 * 3 + i];
+    }
+    const size_t BB = p.B;
+    R* gx = p.xf + (((size_t)oct * BB + b) * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * (size_t)(NDO * fxn);
+    R* gy = p.yf + (((size_t)oct * BB + b) * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * (size_t)(NDO * fyn);
+    R* gz = p.zf + (((size_t)oct * BB + b) * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * (size_t)(NDO * fzn);
+    // incoming faces: the upstream tile's outgoing faces, or vacuum on the boundary
+    for (int i = tid; i < NDO * fxn; i += nth) fx[i] = ta > 0 ? gx[i] : R(0);
+    for (int i = tid; i < NDO * fyn; i += nth) fy[i] = tb > 0 ? gy[i] : R(0);
+    for (int i = tid; i < NDO * fzn; i += nth) fz[i] = tc > 0 ? gz[i] : R(0);
+    __syncthreads();
+
+    // phase A: scatter-source contraction Q_n = sum_k M[n][k] T_k for the octant
+    const R* Tt = p.T + ((size_t)b * p.NT + tile) * (size_t)(K * TV);
+    const R* st = p.sigt + (size_t)tile * TV;
+#pragma unroll 1
+    for (int c = tid; c < TV; c += nth) {
+        R t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] = Tt[k * TV + c];
+        sg[c] = st[c];
+#pragma unroll 1
+        for (int d = 0; d < NDO; ++d) {
+            R q = R(0);
+#pragma unroll
+            for (int k = 0; k < K; ++k) q = fma(Ms[d * K + k], t[k], q);
+            Qs[d * TV + c] = q;
+        }
+    }
+    __syncthreads();
+
+    // phase B: intra-tile wavefront, sub-sweep by sub-sweep (Sec. II.B)
+    double leak = 0.0;
+    const int gx0 = tx * TX, gy0 = ty * TY, gz0 = tz * TZ;
+    const int bx = negx ? 0 : p.nx - 1, by = negy ? 0 : p.ny - 1, bz = negz ? 0 : p.nz - 1;
+    for (int s = 0; s < p.nsub; ++s) {
+        const int o0 = p.diag_off[s], cs = p.diag_off[s + 1] - o0;
+        const int items = cs * NDO;
+        for (int it = tid; it < items; it += nth) {
+            const int d = it / cs, e = it - d * cs;
+            const unsigned pc = p.diag_cells[o0 + e];
+            const int lx = pc & 255, ly = (pc >> 8) & 255, lz = (pc >> 16) & 255;
+            const int sx = negx ? TX - 1 - lx : lx;
+            const int sy = negy ? TY - 1 - ly : ly;
+            const int sz = negz ? TZ - 1 - lz : lz;
+            const int c = (sz * TY + sy) * TX + sx;
+            R* px = fx + d * fxn + sz * TY + sy;
+            R* py = fy + d * fyn + sz * TX + sx;
+            R* pz = fz + d * fzn + sy * TX + sx;
+            const int gi = gx0 + sx, gj = gy0 + sy, gk = gz0 + sz;
+            if (gi >= p.nx || gj >= p.ny || gk >= p.nz) {   // padding: vacuum in, nothing out
+                *px = R(0);
+                *py = R(0);
+                *pz = R(0);
+                Qs[d * TV + c] = R(0);
+                continue;
+            }
+            R ox, oy, oz;
+            const R psi = dd_cell<R>(Qs[d * TV + c], sg[c], As[d * 4], As[d * 4 + 1], As[d * 4 + 2],
+                                     *px, *py, *pz, ox, oy, oz);
+            *px = ox;
+            *py = oy;
+            *pz = oz;
+            Qs[d * TV + c] = psi;
+            if (gi == bx) leak += Lw[d * 3] * (double)ox;
+            if (gj == by) leak += Lw[d * 3 + 1] * (double)oy;
+            if (gk == bz) leak += Lw[d * 3 + 2] * (double)oz;
+        }
+        __syncthreads();
+    }
+
+    // phase C: per-octant moment partial P_o[k] = sum_n D[k][n] psi_n
+    R* out = p.part + (((size_t)oct * BB + b) * p.NT + tile) * (size_t)(K * TV);
+#pragma unroll 1
+    for (int c = tid; c < TV; c += nth) {
+        R ps[NDO];
+#pragma unroll
+        for (int d = 0; d < NDO; ++d) ps[d] = Qs[d * TV + c];
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            R acc = R(0);
+#pragma unroll
+            for (int d = 0; d < NDO; ++d) acc = fma(Ds[k * NDO + d], ps[d], acc);
+            out[k * TV + c] = acc;
+        }
+    }
+    // outgoing faces for the downstream tiles
+    for (int i = tid; i < NDO * fxn; i += nth) gx[i] = fx[i];
+    for (int i = tid; i < NDO * fyn; i += nth) gy[i] = fy[i];
+    for (int i = tid; i < NDO * fzn; i += nth) gz[i] = fz[i];
+    leak = block_sum(leak, red);
+    if (tid == 0 && leak != 0.0) atomicAdd(&p.leak[b], leak);
+}
+
+// ---------------------------------------------------------------------------
+// A5 + A6 (+ A10 terms): Eq. 3 octant sum in FP64 (fixed order 0..7), next
+// source T = F + sigma_s^{gg} phi, residual and balance partial sums.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct RedParams {
+    int B, NT, TV, NC;
+    const R* part;
+    double* phi;
+    R* T;
+    const double* F;
+    size_t Fstride;
+    const int* ctl;            // [0] group, [1] fixed-source slot
+    const double* sigs;        // [L+1][NC] in-group scatter per cell
+    const double* sigt64;      // [NC]
+    const int* mat_t;          // [NC], -1 = padding
+    const int* active;
+    double vol;
+    double* blk;               // [B][nblk][4]
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const RedParams<R> p)
+{
+    __shared__ double red[32];
+    const int b = blockIdx.y;
+    const int ct = blockIdx.x * blockDim.x + threadIdx.x;
+    double ds = 0.0, ns = 0.0, sr = 0.0, ab = 0.0;
+    const bool act = p.active[b] != 0;
+    if (act && ct < p.NC) {
+        const int tile = ct / p.TV, c = ct - tile * p.TV;
+        const size_t base = ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
+        const size_t ostride = (size_t)p.B * p.NT * K * p.TV;
+        if (p.mat_t[ct] >= 0) {
+            const double* F = p.F + (size_t)p.ctl[1] * p.Fstride + base;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const size_t ik = base + (size_t)k * p.TV;
+                double s = 0.0;
+#pragma unroll
+                for (int o = 0; o < 8; ++o) s += (double)p.part[o * ostride + ik];
+                const double sl = p.sigs[(size_t)l_of_k(k) * p.NC + ct];
+                if (k == 0) {
+                    const double old = p.phi[ik];
+                    const double dd = s - old;
+                    ds += dd * dd;
+                    ns += s * s;
+                    ab += p.vol * p.sigt64[ct] * s;
+                    sr += p.vol * (F[0] + sl * old);
+                }
+                p.phi[ik] = s;
+                p.T[ik] = (R)(F[(size_t)k * p.TV] + sl * s);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                p.phi[base + (size_t)k * p.TV] = 0.0;
+                p.T[base + (size_t)k * p.TV] = R(0);
+            }
+        }
+    }
+    ds = block_sum(ds, red);
+    ns = block_sum(ns, red);
+    sr = block_sum(sr, red);
+    ab = block_sum(ab, red);
+    if (threadIdx.x == 0) {
+        double* o = p.blk + ((size_t)b * gridDim.x + blockIdx.x) * 4;
+        o[0] = ds;
+        o[1] = ns;
+        o[2] = sr;
+        o[3] = ab;
+    }
+}
+
+// per source: residual = sqrt(sum dphi^2 / sum phi^2), balance terms, leakage
+// (then cleared for the next sweep); fixed summation order
+__global__ void k_resid_final(const double* blk, int nblk, double* leak, double* status)
+{
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        const double* o = blk + ((size_t)b * nblk + i) * 4;
+        a[0] += o[0];
+        a[1] += o[1];
+        a[2] += o[2];
+        a[3] += o[3];
+    }
+    for (int j = 0; j < 4; ++j) a[j] = block_sum(a[j], red);
+    if (threadIdx.x == 0) {
+        double* s = status + (size_t)b * 4;
+        s[0] = a[1] > 0.0 ? sqrt(a[0] / a[1]) : 0.0;
+        s[1] = a[2];
+        s[2] = a[3];
+        s[3] = leak[b];
+        leak[b] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// group set-up: per-cell cross sections of group g
+// ---------------------------------------------------------------------------
+struct CellParams {
+    int NC, TV, TX, TY, TZ, NTx, NTy, nx, ny, nz, G, L, B, K, NT;
+    double dx, dy, dz, x0, y0, z0;
+    const int* mat_t;              // [NC]
+    const double* scale_t_t;       // [NC] or null
+    const double* scale_s_t;       // [NC] or null
+    const double* sigma_t;         // [n_mat][G]
+    const double* sigma_s;         // [n_mat][L+1][G][G]
+};
+
+__device__ inline int tiled_to_natural(const CellParams& p, int ct, double* C)
+{
+    const int tile = ct / p.TV, c = ct - tile * p.TV;
+    const int tx = tile % p.NTx, ty = (tile / p.NTx) % p.NTy, tz = tile / (p.NTx * p.NTy);
+    const int sx = c % p.TX, sy = (c / p.TX) % p.TY, sz = c / (p.TX * p.TY);
+    const int i = tx * p.TX + sx, j = ty * p.TY + sy, k = tz * p.TZ + sz;
+    if (C) {
+        C[0] = p.x0 + (i + 0.5) * p.dx;
+        C[1] = p.y0 + (j + 0.5) * p.dy;
+        C[2] = p.z0 + (k + 0.5) * p.dz;
+    }
+    return (k * p.ny + j) * p.nx + i;
+}
+
+template <typename R>
+__global__ void k_group_xs(const CellParams p, int g, R* sigt_r, double* sigt64, double* sigs)
+{
+    const int ct = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ct >= p.NC) return;
+    const int m = p.mat_t[ct];
+    if (m < 0) {
+        sigt_r[ct] = R(1);
+        sigt64[ct] = 0.0;
+        for (int l = 0; l <= p.L; ++l) sigs[(size_t)l * p.NC + ct] = 0.0;
+        return;
+    }
+    double st = p.sigma_t[(size_t)m * p.G + g];
+    if (p.scale_t_t) st *= p.scale_t_t[ct];
+    sigt_r[ct] = (R)st;
+    sigt64[ct] = st;
+    const double ss = p.scale_s_t ? p.scale_s_t[ct] : 1.0;
+    for (int l = 0; l <= p.L; ++l)
+        sigs[(size_t)l * p.NC + ct] =
+            p.sigma_s[(((size_t)m * (p.L + 1) + l) * p.G + g) * p.G + g] * ss;
+}
+
+// phi = 0 and T = F[slot] at the start of a group (phi^(0) = 0)
+template <typename R>
+__global__ void k_group_init(int total, const double* F, double* phi, R* T)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)total) return;
+    phi[i] = 0.0;
+    T[i] = (R)F[i];
+}
+
+__global__ void k_set_ctl(int* ctl, int g, int slot)
+{
+    ctl[0] = g;
+    ctl[1] = slot;
+}
+
+// ---------------------------------------------------------------------------
+// A1: uncollided fluence by exact voxel traversal from the source to each
+// voxel centre (Eq. 4 with no scatter term); outside the grid is vacuum.
+// src rows: kind, pos[3], axis[3], half_angle.
+// ---------------------------------------------------------------------------
+struct RayParams {
+    int nx, ny, nz, V, G;
+    double dx, dy, dz, x0, y0, z0;
+    const int* mat;                // natural [V]
+    const double* scale_t;         // natural [V] or null
+    const double* sigma_t;         // [n_mat][G]
+    const double* src;             // [B][8]
+    const double* spec;            // [B][G]
+    double* unc;                   // [B][G][V]
+};
+
+__global__ void k_raytrace(const RayParams p, int g0)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (v >= p.V) return;
+    const double* s = p.src + (size_t)b * 8;
+    const int ng = min(kRayGroups, p.G - g0);
+    double* out = p.unc + ((size_t)b * p.G + g0) * p.V + v;
+    if (s[0] != 1.0) {
+        for (int gg = 0; gg < ng; ++gg) out[(size_t)gg * p.V] = 0.0;
+        return;
+    }
+    const int ci[3] = {v % p.nx, (v / p.nx) % p.ny, v / (p.nx * p.ny)};
+    const int n[3] = {p.nx, p.ny, p.nz};
+    const double lo[3] = {p.x0, p.y0, p.z0}, h[3] = {p.dx, p.dy, p.dz};
+    double P[3], d[3];
+    for (int a = 0; a < 3; ++a) {
+        P[a] = s[1 + a];
+        d[a] = lo[a] + (ci[a] + 0.5) * h[a] - P[a];
+    }
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double r = sqrt(r2);
+    const double an = sqrt(s[4] * s[4] + s[5] * s[5] + s[6] * s[6]);
+    const double cosang = (d[0] * s[4] + d[1] * s[5] + d[2] * s[6]) / (r * an);
+    if (s[7] < kPi && cosang < cos(s[7])) {
+        for (int gg = 0; gg < ng; ++gg) out[(size_t)gg * p.V] = 0.0;
+        return;
+    }
+    // parameter where the segment P -> C enters the grid box
+    double a_in = 0.0;
+    for (int a = 0; a < 3; ++a)
+        if (d[a] != 0.0) {
+            const double t0 = (lo[a] - P[a]) / d[a], t1 = (lo[a] + n[a] * h[a] - P[a]) / d[a];
+            a_in = fmax(a_in, fmin(t0, t1));
+        }
+    int idx[3], step[3];
+    double tnext[3];
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            idx[a] = ci[a];
+            step[a] = 0;
+            tnext[a] = 2.0;
+            continue;
+        }
+        int id = (int)floor((P[a] + a_in * d[a] - lo[a]) / h[a]);
+        id = id < 0 ? 0 : (id >= n[a] ? n[a] - 1 : id);
+        idx[a] = id;
+        step[a] = d[a] > 0.0 ? 1 : -1;
+        tnext[a] = (lo[a] + (id + (d[a] > 0.0 ? 1 : 0)) * h[a] - P[a]) / d[a];
+    }
+    double tau[kRayGroups];
+#pragma unroll
+    for (int gg = 0; gg < kRayGroups; ++gg) tau[gg] = 0.0;
+    double acur = a_in;
+    const int max_steps = p.nx + p.ny + p.nz + 3;
+    for (int it = 0; it < max_steps; ++it) {
+        int ax = 0;
+        if (tnext[1] < tnext[ax]) ax = 1;
+        if (tnext[2] < tnext[ax]) ax = 2;
+        const double a1 = fmin(tnext[ax], 1.0);
+        const double seg = (a1 - acur) * r;
+        if (seg > 0.0) {
+            const int vv = (idx[2] * p.ny + idx[1]) * p.nx + idx[0];
+            const int m = p.mat[vv];
+            const double sc = p.scale_t ? p.scale_t[vv] : 1.0;
+            const double* sgm = p.sigma_t + (size_t)m * p.G + g0;
+#pragma unroll
+            for (int gg = 0; gg < kRayGroups; ++gg)
+                if (gg < ng) tau[gg] += sgm[gg] * sc * seg;
+        }
+        if (a1 >= 1.0) break;
+        acur = a1;
+        idx[ax] += step[ax];
+        if (idx[ax] < 0 || idx[ax] >= n[ax]) break;
+        tnext[ax] = (lo[ax] + (idx[ax] + (step[ax] > 0 ? 1 : 0)) * h[ax] - P[ax]) / d[ax];
+    }
+    const double inv = 1.0 / (4.0 * kPi * r2);
+    for (int gg = 0; gg < ng; ++gg)
+        out[(size_t)gg * p.V] = p.spec[(size_t)b * p.G + g0 + gg] * exp(-tau[gg]) * inv;
+}
+
+// ---------------------------------------------------------------------------
+// A1 (second half) / A2: fixed source of group gt written into ring slot
+// slot: first-collision moments (Eq. 5)
+//   q_lm = sum_{g'<=gt} sigma_{s,l}^{g'->gt} phi_u^{g'} Y_lm(Omega_u)
+// or the volumetric source (l = 0 only).
+// ---------------------------------------------------------------------------
+struct SrcParams {
+    CellParams c;
+    const double* src;     // [B][8]
+    const double* unc;     // [B][G][V]
+    const double* q;       // [B][G][V] or null
+    double* F;
+    size_t Fstride;
+    int V;
+};
+
+__global__ void k_fixed_source(const SrcParams p, int gt, int slot)
+{
+    const int ct = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    const CellParams& c = p.c;
+    if (ct >= c.NC) return;
+    const int tile = ct / c.TV, cc = ct - tile * c.TV;
+    double* F = p.F + (size_t)slot * p.Fstride + ((size_t)b * c.NT + tile) * (size_t)(c.K * c.TV) + cc;
+    const int m = c.mat_t[ct];
+    const int kind = (int)p.src[(size_t)b * 8];
+    if (m < 0 || kind < 0) {
+        for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = 0.0;
+        return;
+    }
+    double C[3];
+    const int v = tiled_to_natural(c, ct, C);
+    if (kind == 0) {
+        F[0] = p.q[((size_t)b * c.G + gt) * p.V + v];
+        for (int k = 1; k < c.K; ++k) F[(size_t)k * c.TV] = 0.0;
+        return;
+    }
+    const double* s = p.src + (size_t)b * 8;
+    const double d0 = C[0] - s[1], d1 = C[1] - s[2], d2 = C[2] - s[3];
+    const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    double Y[16];
+    sh_eval(c.L, d0 / r, d1 / r, d2 / r, Y);
+    const double ss = c.scale_s_t ? c.scale_s_t[ct] : 1.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int gp = 0; gp <= gt; ++gp) {
+        const double phu = p.unc[((size_t)b * c.G + gp) * p.V + v];
+        for (int l = 0; l <= c.L; ++l)
+            acc[l] += c.sigma_s[(((size_t)m * (c.L + 1) + l) * c.G + gp) * c.G + gt] * ss * phu;
+    }
+    for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = acc[l_of_k(k)] * Y[k];
+}
+
+// ---------------------------------------------------------------------------
+// A2 / A7 at the end of group g: downscatter of the converged moments into
+// the fixed sources of groups g+1 .. g+W, and the outputs.
+// ---------------------------------------------------------------------------
+struct PushParams {
+    CellParams c;
+    const double* phi;
+    double* F;
+    size_t Fstride;
+    int W, V;
+    double* col;           // [B][G][V]
+    double* mom;           // [B][G][K][V] or null
+    const int* has_src;    // [B]
+};
+
+__global__ void k_push(const PushParams p, int g)
+{
+    const int ct = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    const CellParams& c = p.c;
+    if (ct >= c.NC) return;
+    const int m = c.mat_t[ct];
+    if (m < 0) return;
+    const int tile = ct / c.TV, cc = ct - tile * c.TV;
+    const size_t base = ((size_t)b * c.NT + tile) * (size_t)(c.K * c.TV) + cc;
+    const int v = tiled_to_natural(c, ct, nullptr);
+    const double ss = c.scale_s_t ? c.scale_s_t[ct] : 1.0;
+    const int W1 = p.W + 1;
+    const int gmax = min(c.G - 1, g + p.W);
+    for (int k = 0; k < c.K; ++k) {
+        const double ph = p.phi[base + (size_t)k * c.TV];
+        const int l = l_of_k(k);
+        if (k == 0) p.col[((size_t)b * c.G + g) * p.V + v] = ph;
+        if (p.mom) p.mom[(((size_t)b * c.G + g) * c.K + k) * p.V + v] = ph;
+        for (int g2 = g + 1; g2 <= gmax; ++g2) {
+            const double sgm = c.sigma_s[(((size_t)m * (c.L + 1) + l) * c.G + g) * c.G + g2];
+            if (sgm != 0.0)
+                p.F[(size_t)(g2 % W1) * p.Fstride + base + (size_t)k * c.TV] += sgm * ss * ph;
+        }
+    }
+}
+
+__global__ void k_add(size_t n, const double* a, const double* b, double* out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] + b[i];
+}
+
+}  // namespace dts

@@ -1,0 +1,1054 @@
+// dts_runtime.cu -- host runtime and C ABI of the B300 S_N solver (include/dts.h).
+//
+// The runtime owns the device buffers of a problem, the wavefront schedule
+// (tile stages of Eq. 9 applied to tiles, and the intra-tile sub-sweeps), the
+// group loop (high energy to low), the source-iteration loop with its
+// convergence control, and a CUDA graph holding one iteration (all tile
+// stages of the sweep, the Eq. 3 reduction and the residual), replayed for
+// every iteration of every group.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dts.h"
+#include "dts_kernels.cuh"
+
+using namespace dts;
+
+namespace {
+
+thread_local std::string g_thread_error = "no error";
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct dts_problem {
+    dts_problem_desc d{};
+    std::string err = "no error";
+    int V = 0, G = 0, L = 0, K = 0, nd = 0, ndo = 0, B = 0;
+    int TX = 0, TY = 0, TZ = 0, TV = 0, NTx = 0, NTy = 0, NTz = 0, NT = 0, NC = 0;
+    int n_stages = 0, nsub = 0, n_mat = 0, W = 0, nblk = 0;
+    bool fp64 = true;
+    size_t rsz = 8;                   // sizeof(R)
+    std::vector<int> stage_off_h;     // [n_stages+1]
+    std::vector<double> mu, eta, xi, w;
+    std::vector<double> sigma_s_h;    // kept for the band width
+    // device buffers
+    std::vector<void*> allocs;
+    unsigned *stage_tiles = nullptr, *diag_cells = nullptr;
+    int *stage_off = nullptr, *diag_off = nullptr;
+    void *Mt = nullptr, *Dt = nullptr, *At = nullptr;
+    double* Lw = nullptr;
+    double *sigma_t = nullptr, *sigma_s = nullptr;
+    int *mat_t = nullptr, *mat_nat = nullptr;
+    double *scale_t_t = nullptr, *scale_s_t = nullptr, *scale_t_nat = nullptr;
+    double *F = nullptr, *phi = nullptr, *sigt64 = nullptr, *sigs = nullptr;
+    void *T = nullptr, *part = nullptr, *xf = nullptr, *yf = nullptr, *zf = nullptr, *sigt_r = nullptr;
+    double *unc = nullptr, *col = nullptr, *mom = nullptr, *q = nullptr, *tmp = nullptr;
+    double *src = nullptr, *spec = nullptr, *leak = nullptr, *blk = nullptr, *status = nullptr;
+    int *active = nullptr, *ctl = nullptr, *has_src = nullptr;
+    size_t Fstride = 0;
+    int F_W = -1;
+    // host state
+    double* h_status = nullptr;       // pinned [B][4]
+    int* h_active = nullptr;          // pinned [B]
+    std::vector<double> src_h;        // [B][8]
+    std::vector<double> spec_h;       // [B][G]
+    std::vector<int> src_set;
+    bool materials_set = false, solved = false;
+    std::vector<int32_t> iters;       // [B][G]
+    std::vector<double> resid;        // [B][G]
+    std::vector<double> balance;      // [B][G][3]
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t eva = nullptr, evb = nullptr, evc = nullptr;   // recorded inside the graph
+    int graph_launches = 0;           // kernels per graph replay
+};
+
+namespace {
+
+dts_status fail(dts_problem* p, dts_status s, const std::string& msg)
+{
+    if (p) p->err = msg;
+    else g_thread_error = msg;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(p, e_ == cudaErrorMemoryAllocation ? DTS_ERR_OOM : DTS_ERR_CUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+#define TRY(expr)                          \
+    do {                                   \
+        dts_status s_ = (expr);            \
+        if (s_ != DTS_OK) return s_;       \
+    } while (0)
+
+dts_status dalloc(dts_problem* p, void** ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        char buf[160];
+        snprintf(buf, sizeof buf, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        return fail(p, e == cudaErrorMemoryAllocation ? DTS_ERR_OOM : DTS_ERR_CUDA, buf);
+    }
+    p->allocs.push_back(*ptr);
+    return DTS_OK;
+}
+
+template <typename T>
+dts_status dalloc_t(dts_problem* p, T** ptr, size_t count)
+{
+    return dalloc(p, reinterpret_cast<void**>(ptr), count * sizeof(T));
+}
+
+void dfree(dts_problem* p, void* ptr)
+{
+    if (!ptr) return;
+    auto it = std::find(p->allocs.begin(), p->allocs.end(), ptr);
+    if (it != p->allocs.end()) p->allocs.erase(it);
+    cudaFree(ptr);
+}
+
+bool isfin(double x) { return std::isfinite(x); }
+
+// ---------------------------------------------------------------------------
+// level-symmetric quadrature (Sec. II.E), octant-major
+// ---------------------------------------------------------------------------
+double det3(const double m[3][3])
+{
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+           m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+bool ls_set(int N, std::vector<double>& mu, std::vector<double>& eta, std::vector<double>& xi,
+            std::vector<double>& w)
+{
+    double m1sq;
+    if (N == 2) m1sq = 1.0 / 3.0;
+    else if (N == 4) m1sq = (4.0 - std::sqrt(6.4)) / 12.0;   // root of 6x^2 - 4x + 0.4 = 0
+    else if (N == 6) m1sq = 0.2666355 * 0.2666355;
+    else if (N == 8) m1sq = 0.2182179 * 0.2182179;
+    else return false;
+    const int h = N / 2;
+    std::vector<double> lev(h);
+    for (int i = 0; i < h; ++i)
+        lev[i] = std::sqrt(h == 1 ? m1sq : m1sq + 2.0 * i * (1.0 - 3.0 * m1sq) / (N - 2));
+    struct Pt { int a, b, c, cls; };
+    std::vector<Pt> pts;
+    std::vector<std::vector<int>> classes;
+    for (int a = 0; a < h; ++a)
+        for (int b = 0; a + b < h; ++b) {
+            int c = h - 1 - a - b;
+            std::vector<int> key = {a, b, c};
+            std::sort(key.begin(), key.end());
+            int cls = -1;
+            for (size_t i = 0; i < classes.size(); ++i)
+                if (classes[i] == key) cls = (int)i;
+            if (cls < 0) {
+                classes.push_back(key);
+                cls = (int)classes.size() - 1;
+            }
+            pts.push_back({a, b, c, cls});
+        }
+    const int nc = (int)classes.size();
+    const int ks[3] = {0, 2, 3};
+    // even-moment matching, octant-normalised: sum_c w_c sum_{p in c} mu_x^(2k) = 1/(2k+1)
+    double A[3][3] = {{0}}, r[3] = {0};
+    for (int e = 0; e < nc; ++e) {
+        for (const Pt& pt : pts) A[e][pt.cls] += std::pow(lev[pt.a], 2.0 * ks[e]);
+        r[e] = 1.0 / (2.0 * ks[e] + 1.0);
+    }
+    double wc[3] = {0};
+    if (nc == 1) {
+        wc[0] = r[0] / A[0][0];
+    } else {
+        double M[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[i][j] = (i < nc && j < nc) ? A[i][j] : (i == j ? 1.0 : 0.0);
+        const double dt = det3(M);
+        if (dt == 0.0) return false;
+        for (int c = 0; c < nc; ++c) {   // Cramer's rule
+            double Mc[3][3];
+            std::memcpy(Mc, M, sizeof M);
+            for (int i = 0; i < nc; ++i) Mc[i][c] = r[i];
+            wc[c] = det3(Mc) / dt;
+        }
+    }
+    const int npo = (int)pts.size();
+    mu.assign(8 * npo, 0.0);
+    eta.assign(8 * npo, 0.0);
+    xi.assign(8 * npo, 0.0);
+    w.assign(8 * npo, 0.0);
+    const double octant_weight = std::acos(-1.0) / 2.0;   // each octant carries pi/2
+    for (int o = 0; o < 8; ++o)
+        for (int i = 0; i < npo; ++i) {
+            const int n = o * npo + i;
+            mu[n] = (o & 1 ? -1.0 : 1.0) * lev[pts[i].a];
+            eta[n] = (o & 2 ? -1.0 : 1.0) * lev[pts[i].b];
+            xi[n] = (o & 4 ? -1.0 : 1.0) * lev[pts[i].c];
+            w[n] = wc[pts[i].cls] * octant_weight;
+        }
+    return true;
+}
+
+// D[k][n] = w_n Y_k(O_n); M[n][k] = (2l+1)/(4 pi) Y_k(O_n)
+void moment_tables(int L, const std::vector<double>& mu, const std::vector<double>& eta,
+                   const std::vector<double>& xi, const std::vector<double>& w,
+                   std::vector<double>& D, std::vector<double>& M)
+{
+    const int nd = (int)w.size(), K = (L + 1) * (L + 1);
+    D.assign((size_t)K * nd, 0.0);
+    M.assign((size_t)nd * K, 0.0);
+    for (int n = 0; n < nd; ++n) {
+        double Y[16];
+        sh_eval(L, mu[n], eta[n], xi[n], Y);
+        for (int k = 0; k < K; ++k) {
+            D[(size_t)k * nd + n] = w[n] * Y[k];
+            M[(size_t)n * K + k] = (2.0 * l_of_k(k) + 1.0) / (4.0 * kPi) * Y[k];
+        }
+    }
+}
+
+long long eq9(int nx, int ny, int nz, int S)
+{
+    auto t = [](long long d) { return d > 0 ? d * (d + 1) / 2 : 0LL; };
+    return (long long)(S + 1) * (S + 2) / 2 - t(S + 1 - nx) - t(S + 1 - ny) - t(S + 1 - nz) +
+           t(S + 1 - nx - ny) + t(S + 1 - ny - nz) + t(S + 1 - nx - nz);
+}
+
+// ---------------------------------------------------------------------------
+// kernel dispatch on (precision, directions per octant, moments)
+// ---------------------------------------------------------------------------
+template <typename R>
+using SweepFn = void (*)(const SweepParams<R>, int);
+template <typename R>
+using RedFn = void (*)(const RedParams<R>);
+
+template <typename R, int NDO>
+SweepFn<R> sweep_fn_k(int K)
+{
+    switch (K) {
+    case 1: return k_sweep_stage<R, NDO, 1>;
+    case 4: return k_sweep_stage<R, NDO, 4>;
+    case 9: return k_sweep_stage<R, NDO, 9>;
+    case 16: return k_sweep_stage<R, NDO, 16>;
+    }
+    return nullptr;
+}
+
+template <typename R>
+SweepFn<R> sweep_fn(int ndo, int K)
+{
+    switch (ndo) {
+    case 1: return sweep_fn_k<R, 1>(K);
+    case 3: return sweep_fn_k<R, 3>(K);
+    case 6: return sweep_fn_k<R, 6>(K);
+    case 10: return sweep_fn_k<R, 10>(K);
+    }
+    return nullptr;
+}
+
+template <typename R>
+RedFn<R> reduce_fn(int K)
+{
+    switch (K) {
+    case 1: return k_reduce<R, 1>;
+    case 4: return k_reduce<R, 4>;
+    case 9: return k_reduce<R, 9>;
+    case 16: return k_reduce<R, 16>;
+    }
+    return nullptr;
+}
+
+size_t sweep_smem(const dts_problem* p)
+{
+    const size_t n = (size_t)p->ndo * p->TV +
+                     (size_t)p->ndo * (p->TY * p->TZ + p->TX * p->TZ + p->TX * p->TY) + p->TV +
+                     2 * p->ndo * p->K + 4 * p->ndo;
+    size_t bytes = (n * p->rsz + 15) & ~size_t(15);
+    return bytes + sizeof(double) * (3 * p->ndo + 32);
+}
+
+CellParams cell_params(const dts_problem* p)
+{
+    CellParams c;
+    c.NC = p->NC; c.TV = p->TV; c.TX = p->TX; c.TY = p->TY; c.TZ = p->TZ;
+    c.NTx = p->NTx; c.NTy = p->NTy; c.nx = p->d.nx; c.ny = p->d.ny; c.nz = p->d.nz;
+    c.G = p->G; c.L = p->L; c.B = p->B; c.K = p->K; c.NT = p->NT;
+    c.dx = p->d.dx; c.dy = p->d.dy; c.dz = p->d.dz;
+    c.x0 = p->d.x0; c.y0 = p->d.y0; c.z0 = p->d.z0;
+    c.mat_t = p->mat_t; c.scale_t_t = p->scale_t_t; c.scale_s_t = p->scale_s_t;
+    c.sigma_t = p->sigma_t; c.sigma_s = p->sigma_s;
+    return c;
+}
+
+template <typename R>
+dts_status record_iteration(dts_problem* p)
+{
+    SweepParams<R> sp;
+    sp.nx = p->d.nx; sp.ny = p->d.ny; sp.nz = p->d.nz;
+    sp.TX = p->TX; sp.TY = p->TY; sp.TZ = p->TZ; sp.TV = p->TV;
+    sp.NTx = p->NTx; sp.NTy = p->NTy; sp.NTz = p->NTz; sp.NT = p->NT;
+    sp.B = p->B; sp.nsub = p->nsub;
+    sp.stage_tiles = p->stage_tiles; sp.stage_off = p->stage_off;
+    sp.diag_cells = p->diag_cells; sp.diag_off = p->diag_off;
+    sp.M = (const R*)p->Mt; sp.Dt = (const R*)p->Dt; sp.A = (const R*)p->At; sp.Lw = p->Lw;
+    sp.T = (const R*)p->T; sp.sigt = (const R*)p->sigt_r; sp.part = (R*)p->part;
+    sp.xf = (R*)p->xf; sp.yf = (R*)p->yf; sp.zf = (R*)p->zf;
+    sp.active = p->active; sp.leak = p->leak;
+    SweepFn<R> sf = sweep_fn<R>(p->ndo, p->K);
+    if (!sf) return fail(p, DTS_ERR_INTERNAL, "no sweep kernel for this (S_N, P_L)");
+    const size_t smem = sweep_smem(p);
+    CK(cudaEventRecord(p->eva, p->stream));
+    for (int s = 0; s < p->n_stages; ++s) {
+        const int cnt = p->stage_off_h[s + 1] - p->stage_off_h[s];
+        const unsigned grid = (unsigned)cnt * 8u * (unsigned)p->B;
+        sf<<<grid, kSweepThreads, smem, p->stream>>>(sp, s);
+    }
+    CK(cudaEventRecord(p->evb, p->stream));
+    RedParams<R> rp;
+    rp.B = p->B; rp.NT = p->NT; rp.TV = p->TV; rp.NC = p->NC;
+    rp.part = (const R*)p->part; rp.phi = p->phi; rp.T = (R*)p->T; rp.F = p->F;
+    rp.Fstride = p->Fstride; rp.ctl = p->ctl; rp.sigs = p->sigs; rp.sigt64 = p->sigt64;
+    rp.mat_t = p->mat_t; rp.active = p->active; rp.vol = p->d.dx * p->d.dy * p->d.dz;
+    rp.blk = p->blk;
+    RedFn<R> rf = reduce_fn<R>(p->K);
+    rf<<<dim3(p->nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
+    k_resid_final<<<p->B, 256, 0, p->stream>>>(p->blk, p->nblk, p->leak, p->status);
+    CK(cudaEventRecord(p->evc, p->stream));
+    p->graph_launches = p->n_stages + 2;
+    CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(double) * 4 * p->B, cudaMemcpyDeviceToHost,
+                       p->stream));
+    return DTS_OK;
+}
+
+dts_status build_graph(dts_problem* p)
+{
+    if (p->graph) return DTS_OK;
+    // kernels with more than 48 KB of dynamic shared memory need the opt-in
+    const size_t smem = sweep_smem(p);
+    cudaError_t e;
+    if (p->fp64) e = cudaFuncSetAttribute(sweep_fn<double>(p->ndo, p->K),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else e = cudaFuncSetAttribute(sweep_fn<float>(p->ndo, p->K),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("sweep smem attribute: ") + cudaGetErrorString(e));
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    dts_status s = p->fp64 ? record_iteration<double>(p) : record_iteration<float>(p);
+    cudaError_t ec = cudaStreamEndCapture(p->stream, &g);
+    if (s != DTS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (ec != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    ec = cudaGraphInstantiate(&p->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ec != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+    return DTS_OK;
+}
+
+// fixed-source ring: (W+1) slots of [B][NT][K][TV] doubles
+dts_status ensure_ring(dts_problem* p)
+{
+    if (p->F && p->F_W == p->W) return DTS_OK;
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    dfree(p, p->F);
+    p->F = nullptr;
+    p->Fstride = (size_t)p->B * p->NC * p->K;
+    TRY(dalloc_t(p, &p->F, p->Fstride * (p->W + 1)));
+    p->F_W = p->W;
+    return DTS_OK;
+}
+
+template <typename R>
+void launch_group_xs(dts_problem* p, int g)
+{
+    const int nb = (p->NC + 255) / 256;
+    k_group_xs<R><<<nb, 256, 0, p->stream>>>(cell_params(p), g, (R*)p->sigt_r, p->sigt64, p->sigs);
+}
+
+template <typename R>
+void launch_group_init(dts_problem* p, int slot)
+{
+    const int total = p->B * p->NC * p->K;
+    k_group_init<R><<<(total + 255) / 256, 256, 0, p->stream>>>(total, p->F + (size_t)slot * p->Fstride,
+                                                                 p->phi, (R*)p->T);
+}
+
+dts_status run_solve(dts_problem* p, dts_solve_stats* st)
+{
+    const int B = p->B, G = p->G;
+    const int W1 = p->W + 1;
+    TRY(ensure_ring(p));
+    TRY(build_graph(p));
+    CK(cudaEventRecord(p->ev0, p->stream));
+    // A1: uncollided fluence, all sources and groups
+    {
+        RayParams rp;
+        rp.nx = p->d.nx; rp.ny = p->d.ny; rp.nz = p->d.nz; rp.V = p->V; rp.G = G;
+        rp.dx = p->d.dx; rp.dy = p->d.dy; rp.dz = p->d.dz;
+        rp.x0 = p->d.x0; rp.y0 = p->d.y0; rp.z0 = p->d.z0;
+        rp.mat = p->mat_nat; rp.scale_t = p->scale_t_nat; rp.sigma_t = p->sigma_t;
+        rp.src = p->src; rp.spec = p->spec; rp.unc = p->unc;
+        for (int g0 = 0; g0 < G; g0 += kRayGroups)
+            k_raytrace<<<dim3((p->V + 127) / 128, B), 128, 0, p->stream>>>(rp, g0);
+        CK(cudaGetLastError());
+    }
+    SrcParams sp;
+    sp.c = cell_params(p);
+    sp.src = p->src; sp.unc = p->unc; sp.q = p->q; sp.F = p->F; sp.Fstride = p->Fstride; sp.V = p->V;
+    const dim3 cgrid((p->NC + 255) / 256, B);
+    for (int g = 0; g < std::min(G, W1); ++g)
+        k_fixed_source<<<cgrid, 256, 0, p->stream>>>(sp, g, g % W1);
+    PushParams pp;
+    pp.c = cell_params(p);
+    pp.phi = p->phi; pp.F = p->F; pp.Fstride = p->Fstride; pp.W = p->W; pp.V = p->V;
+    pp.col = p->col; pp.mom = p->d.keep_moments ? p->mom : nullptr; pp.has_src = p->has_src;
+
+    int64_t updates = 0, sweeps = 0;
+    int64_t launches = (G + kRayGroups - 1) / kRayGroups + std::min(G, W1);
+    double max_res = 0.0, sweep_ms = 0.0, reduce_ms = 0.0;
+    bool all_conv = true;
+    const int64_t u_per_sweep = (int64_t)p->V * p->nd;
+    std::vector<double> best(B), last_improve(B);
+    for (int g = 0; g < G; ++g) {
+        const int slot = g % W1;
+        k_set_ctl<<<1, 1, 0, p->stream>>>(p->ctl, g, slot);
+        if (p->fp64) {
+            launch_group_xs<double>(p, g);
+            launch_group_init<double>(p, slot);
+        } else {
+            launch_group_xs<float>(p, g);
+            launch_group_init<float>(p, slot);
+        }
+        for (int b = 0; b < B; ++b) {
+            p->h_active[b] = 1;
+            p->iters[(size_t)b * G + g] = 0;
+            best[b] = INFINITY;
+            last_improve[b] = 0;
+        }
+        CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+        CK(cudaGetLastError());
+        int n_active = B;
+        for (int it = 1; it <= p->d.max_iters && n_active > 0; ++it) {
+            CK(cudaGraphLaunch(p->graph, p->stream));
+            CK(cudaStreamSynchronize(p->stream));
+            launches += p->graph_launches;
+            {
+                float a = 0.f, b2 = 0.f;
+                CK(cudaEventElapsedTime(&a, p->eva, p->evb));
+                CK(cudaEventElapsedTime(&b2, p->evb, p->evc));
+                sweep_ms += a;
+                reduce_ms += b2;
+            }
+            bool changed = false;
+            for (int b = 0; b < B; ++b) {
+                if (!p->h_active[b]) continue;
+                const double* s = p->h_status + 4 * b;
+                const size_t bg = (size_t)b * G + g;
+                p->iters[bg] = it;
+                p->resid[bg] = s[0];
+                p->balance[bg * 3 + 0] = s[1];
+                p->balance[bg * 3 + 1] = s[2];
+                p->balance[bg * 3 + 2] = s[3];
+                updates += u_per_sweep;
+                ++sweeps;
+                bool stop = p->d.tol > 0.0 && s[0] < p->d.tol;
+                if (!stop && !p->fp64 && p->d.tol > 0.0) {
+                    // FP32 forms: stop when the residual has stagnated at the rounding floor
+                    if (s[0] < 0.99 * best[b]) {
+                        best[b] = s[0];
+                        last_improve[b] = it;
+                    } else if (it - last_improve[b] >= 10) {
+                        stop = true;
+                    }
+                }
+                if (stop) {
+                    p->h_active[b] = 0;
+                    --n_active;
+                    changed = true;
+                }
+            }
+            if (changed && n_active > 0)
+                CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+        }
+        for (int b = 0; b < B; ++b) {
+            const size_t bg = (size_t)b * G + g;
+            max_res = std::max(max_res, p->resid[bg]);
+            if (p->d.tol > 0.0 && !(p->resid[bg] < p->d.tol)) all_conv = false;
+        }
+        k_push<<<cgrid, 256, 0, p->stream>>>(pp, g);
+        launches += 4;   // set_ctl, group_xs, group_init, push
+        if (g + W1 < G) {
+            k_fixed_source<<<cgrid, 256, 0, p->stream>>>(sp, g + W1, slot);
+            ++launches;
+        }
+        CK(cudaGetLastError());
+    }
+    CK(cudaEventRecord(p->ev1, p->stream));
+    CK(cudaEventSynchronize(p->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    p->solved = true;
+    if (st) {
+        st->updates = updates;
+        st->sweeps = sweeps;
+        st->max_residual = max_res;
+        st->solve_ms = ms;
+        st->sweep_ms = sweep_ms;
+        st->reduce_ms = reduce_ms;
+        st->launches = launches;
+        st->converged = all_conv ? 1 : 0;
+        st->tile_x = p->TX;
+        st->tile_y = p->TY;
+        st->tile_z = p->TZ;
+    }
+    if (!all_conv) return fail(p, DTS_ERR_NOT_CONVERGED, "some (source, group) stopped above tol");
+    return DTS_OK;
+}
+
+void choose_tile(dts_problem* p)
+{
+    if (p->d.tile_x > 0) {
+        p->TX = p->d.tile_x;
+        p->TY = p->d.tile_y;
+        p->TZ = p->d.tile_z;
+        return;
+    }
+    // default: 8^3 tiles (clipped to the grid), which keeps the FP64 S8 P3
+    // working set of a CTA near 64 KB of shared memory
+    p->TX = std::min(8, p->d.nx);
+    p->TY = std::min(8, p->d.ny);
+    p->TZ = std::min(8, p->d.nz);
+}
+
+dts_status setup_schedule(dts_problem* p)
+{
+    p->TV = p->TX * p->TY * p->TZ;
+    p->NTx = (p->d.nx + p->TX - 1) / p->TX;
+    p->NTy = (p->d.ny + p->TY - 1) / p->TY;
+    p->NTz = (p->d.nz + p->TZ - 1) / p->TZ;
+    if (p->NTx > 1023 || p->NTy > 1023 || p->NTz > 1023)
+        return fail(p, DTS_ERR_INVALID_ARG, "too many tiles along an axis (max 1023)");
+    p->NT = p->NTx * p->NTy * p->NTz;
+    p->NC = p->NT * p->TV;
+    // tile stages: Eq. 9 applied to the NTx x NTy x NTz tile grid
+    p->n_stages = p->NTx + p->NTy + p->NTz - 2;
+    p->stage_off_h.assign(p->n_stages + 1, 0);
+    for (int s = 0; s < p->n_stages; ++s)
+        p->stage_off_h[s + 1] = p->stage_off_h[s] + (int)eq9(p->NTx, p->NTy, p->NTz, s);
+    if (p->stage_off_h[p->n_stages] != p->NT) return fail(p, DTS_ERR_INTERNAL, "stage count mismatch");
+    std::vector<unsigned> tiles(p->NT);
+    std::vector<int> fill(p->stage_off_h.begin(), p->stage_off_h.end() - 1);
+    for (int c = 0; c < p->NTz; ++c)
+        for (int b = 0; b < p->NTy; ++b)
+            for (int a = 0; a < p->NTx; ++a)
+                if (fill[a + b + c] < p->stage_off_h[a + b + c + 1])
+                    tiles[fill[a + b + c]++] = (unsigned)a | ((unsigned)b << 10) | ((unsigned)c << 20);
+    for (int s = 0; s < p->n_stages; ++s)
+        if (fill[s] != p->stage_off_h[s + 1]) return fail(p, DTS_ERR_INTERNAL, "Eq. 9 stage size mismatch");
+    // intra-tile sub-sweeps (Table 1 ordering is irrelevant inside a sub-sweep)
+    p->nsub = p->TX + p->TY + p->TZ - 2;
+    std::vector<int> doff(p->nsub + 1, 0);
+    for (int s = 0; s < p->nsub; ++s) doff[s + 1] = doff[s] + (int)eq9(p->TX, p->TY, p->TZ, s);
+    std::vector<unsigned> cells(p->TV);
+    std::vector<int> dfill(doff.begin(), doff.end() - 1);
+    for (int z = 0; z < p->TZ; ++z)
+        for (int y = 0; y < p->TY; ++y)
+            for (int x = 0; x < p->TX; ++x)
+                if (dfill[x + y + z] < doff[x + y + z + 1])
+                    cells[dfill[x + y + z]++] = (unsigned)x | ((unsigned)y << 8) | ((unsigned)z << 16);
+    for (int s = 0; s < p->nsub; ++s)
+        if (dfill[s] != doff[s + 1]) return fail(p, DTS_ERR_INTERNAL, "Eq. 9 sub-sweep size mismatch");
+    TRY(dalloc_t(p, &p->stage_tiles, tiles.size()));
+    TRY(dalloc_t(p, &p->stage_off, p->stage_off_h.size()));
+    TRY(dalloc_t(p, &p->diag_cells, cells.size()));
+    TRY(dalloc_t(p, &p->diag_off, doff.size()));
+    CK(cudaMemcpy(p->stage_tiles, tiles.data(), tiles.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->stage_off, p->stage_off_h.data(), p->stage_off_h.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->diag_cells, cells.data(), cells.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->diag_off, doff.data(), doff.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return DTS_OK;
+}
+
+template <typename R>
+dts_status upload_tables(dts_problem* p, const std::vector<double>& Dkn, const std::vector<double>& Mnk)
+{
+    const int nd = p->nd, K = p->K;
+    std::vector<R> M(nd * K), Dt(nd * K), A(nd * 3);
+    std::vector<double> Lw(nd * 3);
+    for (int n = 0; n < nd; ++n) {
+        for (int k = 0; k < K; ++k) {
+            M[n * K + k] = (R)Mnk[(size_t)n * K + k];
+            Dt[n * K + k] = (R)Dkn[(size_t)k * nd + n];
+        }
+        const double om[3] = {std::fabs(p->mu[n]), std::fabs(p->eta[n]), std::fabs(p->xi[n])};
+        const double h[3] = {p->d.dx, p->d.dy, p->d.dz};
+        const double area[3] = {p->d.dy * p->d.dz, p->d.dx * p->d.dz, p->d.dx * p->d.dy};
+        for (int a = 0; a < 3; ++a) {
+            A[n * 3 + a] = (R)(2.0 * om[a] / h[a]);
+            Lw[n * 3 + a] = p->w[n] * om[a] * area[a];
+        }
+    }
+    TRY(dalloc(p, &p->Mt, M.size() * sizeof(R)));
+    TRY(dalloc(p, &p->Dt, Dt.size() * sizeof(R)));
+    TRY(dalloc(p, &p->At, A.size() * sizeof(R)));
+    TRY(dalloc_t(p, &p->Lw, Lw.size()));
+    CK(cudaMemcpy(p->Mt, M.data(), M.size() * sizeof(R), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->Dt, Dt.data(), Dt.size() * sizeof(R), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->At, A.data(), A.size() * sizeof(R), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->Lw, Lw.data(), Lw.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return DTS_OK;
+}
+
+dts_status create(const dts_problem_desc* desc, dts_problem* p)
+{
+    p->d = *desc;
+    const dts_problem_desc& d = p->d;
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nx > 65536 || d.ny > 65536 || d.nz > 65536)
+        return fail(p, DTS_ERR_INVALID_ARG, "grid extents must be in 1..65536");
+    if (!(d.dx > 0 && d.dy > 0 && d.dz > 0) || !isfin(d.dx) || !isfin(d.dy) || !isfin(d.dz))
+        return fail(p, DTS_ERR_INVALID_ARG, "voxel pitch must be finite and > 0");
+    if (!isfin(d.x0) || !isfin(d.y0) || !isfin(d.z0))
+        return fail(p, DTS_ERR_INVALID_ARG, "grid origin must be finite");
+    if (d.n_groups < 1) return fail(p, DTS_ERR_INVALID_ARG, "n_groups must be >= 1");
+    if (d.legendre_order < 0 || d.legendre_order > 3)
+        return fail(p, DTS_ERR_INVALID_ARG, "legendre_order must be in 0..3");
+    if (d.batch < 1) return fail(p, DTS_ERR_INVALID_ARG, "batch must be >= 1");
+    if (d.precision != DTS_PREC_FP64 && d.precision != DTS_PREC_FP32)
+        return fail(p, DTS_ERR_INVALID_ARG, "unknown precision");
+    if (!(d.tol >= 0.0) || !isfin(d.tol)) return fail(p, DTS_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (d.max_iters < 1) return fail(p, DTS_ERR_INVALID_ARG, "max_iters must be >= 1");
+    const bool tile_given = d.tile_x || d.tile_y || d.tile_z;
+    if (tile_given && (d.tile_x < 1 || d.tile_y < 1 || d.tile_z < 1 || d.tile_x > 16 ||
+                       d.tile_y > 16 || d.tile_z > 16))
+        return fail(p, DTS_ERR_INVALID_ARG, "tile extents must all be 0 or all in 1..16");
+    if (!ls_set(d.sn_order, p->mu, p->eta, p->xi, p->w))
+        return fail(p, DTS_ERR_INVALID_ARG, "sn_order must be 2, 4, 6 or 8");
+    p->V = d.nx * d.ny * d.nz;
+    p->G = d.n_groups;
+    p->L = d.legendre_order;
+    p->K = (p->L + 1) * (p->L + 1);
+    p->nd = (int)p->w.size();
+    p->ndo = p->nd / 8;
+    p->B = d.batch;
+    p->fp64 = d.precision == DTS_PREC_FP64;
+    p->rsz = p->fp64 ? sizeof(double) : sizeof(float);
+    choose_tile(p);
+
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (d.device < 0 || d.device >= ndev) return fail(p, DTS_ERR_INVALID_ARG, "device ordinal out of range");
+    DevGuard guard(d.device);
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, d.device));
+    if (sweep_smem(p) > prop.sharedMemPerBlockOptin)
+        return fail(p, DTS_ERR_INVALID_ARG, "wavefront tile needs more shared memory than a CTA has");
+    if (d.cuda_stream) {
+        p->stream = (cudaStream_t)d.cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+        p->own_stream = true;
+    }
+    CK(cudaEventCreate(&p->ev0));
+    CK(cudaEventCreate(&p->ev1));
+    CK(cudaEventCreate(&p->eva));
+    CK(cudaEventCreate(&p->evb));
+    CK(cudaEventCreate(&p->evc));
+    TRY(setup_schedule(p));
+    std::vector<double> D, M;
+    moment_tables(p->L, p->mu, p->eta, p->xi, p->w, D, M);
+    TRY(p->fp64 ? upload_tables<double>(p, D, M) : upload_tables<float>(p, D, M));
+
+    const size_t B = p->B, NC = p->NC, K = p->K, G = p->G, V = p->V;
+    TRY(dalloc_t(p, &p->mat_t, NC));
+    TRY(dalloc_t(p, &p->mat_nat, V));
+    TRY(dalloc_t(p, &p->phi, B * NC * K));
+    TRY(dalloc(p, &p->T, B * NC * K * p->rsz));
+    TRY(dalloc(p, &p->part, 8 * B * NC * K * p->rsz));
+    const size_t nf = (size_t)p->ndo;
+    TRY(dalloc(p, &p->xf, 8 * B * (size_t)p->NTy * p->NTz * nf * p->TY * p->TZ * p->rsz));
+    TRY(dalloc(p, &p->yf, 8 * B * (size_t)p->NTx * p->NTz * nf * p->TX * p->TZ * p->rsz));
+    TRY(dalloc(p, &p->zf, 8 * B * (size_t)p->NTx * p->NTy * nf * p->TX * p->TY * p->rsz));
+    TRY(dalloc(p, &p->sigt_r, NC * p->rsz));
+    TRY(dalloc_t(p, &p->sigt64, NC));
+    TRY(dalloc_t(p, &p->sigs, NC * (p->L + 1)));
+    TRY(dalloc_t(p, &p->unc, B * G * V));
+    TRY(dalloc_t(p, &p->col, B * G * V));
+    TRY(dalloc_t(p, &p->tmp, G * V));
+    if (d.keep_moments) TRY(dalloc_t(p, &p->mom, B * G * K * V));
+    TRY(dalloc_t(p, &p->src, B * 8));
+    TRY(dalloc_t(p, &p->spec, B * G));
+    TRY(dalloc_t(p, &p->leak, B));
+    p->nblk = (p->NC + kRedThreads - 1) / kRedThreads;
+    TRY(dalloc_t(p, &p->blk, B * p->nblk * 4));
+    TRY(dalloc_t(p, &p->status, B * 4));
+    TRY(dalloc_t(p, &p->active, B));
+    TRY(dalloc_t(p, &p->has_src, B));
+    TRY(dalloc_t(p, &p->ctl, 4));
+    CK(cudaMemset(p->leak, 0, sizeof(double) * B));
+    CK(cudaMemset(p->col, 0, sizeof(double) * B * G * V));
+    CK(cudaMallocHost((void**)&p->h_status, sizeof(double) * 4 * B));
+    CK(cudaMallocHost((void**)&p->h_active, sizeof(int) * B));
+    p->src_h.assign(B * 8, 0.0);
+    for (size_t b = 0; b < B; ++b) p->src_h[b * 8] = -1.0;
+    p->spec_h.assign(B * G, 0.0);
+    p->src_set.assign(B, 0);
+    p->iters.assign(B * G, 0);
+    p->resid.assign(B * G, 0.0);
+    p->balance.assign(B * G * 3, 0.0);
+    return DTS_OK;
+}
+
+void destroy(dts_problem* p)
+{
+    DevGuard guard(p->d.device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (void* a : p->allocs) cudaFree(a);
+    p->allocs.clear();
+    if (p->h_status) cudaFreeHost(p->h_status);
+    if (p->h_active) cudaFreeHost(p->h_active);
+    for (cudaEvent_t e : {p->ev0, p->ev1, p->eva, p->evb, p->evc})
+        if (e) cudaEventDestroy(e);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+}
+
+// natural [V] -> tiled [NC] (padding gets `pad`)
+template <typename T>
+std::vector<T> to_tiled(const dts_problem* p, const T* nat, T pad)
+{
+    std::vector<T> out(p->NC, pad);
+    for (int tz = 0; tz < p->NTz; ++tz)
+        for (int ty = 0; ty < p->NTy; ++ty)
+            for (int tx = 0; tx < p->NTx; ++tx) {
+                const size_t tile = ((size_t)tz * p->NTy + ty) * p->NTx + tx;
+                for (int sz = 0; sz < p->TZ; ++sz)
+                    for (int sy = 0; sy < p->TY; ++sy)
+                        for (int sx = 0; sx < p->TX; ++sx) {
+                            const int i = tx * p->TX + sx, j = ty * p->TY + sy, k = tz * p->TZ + sz;
+                            if (i >= p->d.nx || j >= p->d.ny || k >= p->d.nz) continue;
+                            out[tile * p->TV + (sz * p->TY + sy) * p->TX + sx] =
+                                nat[((size_t)k * p->d.ny + j) * p->d.nx + i];
+                        }
+            }
+    return out;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+dts_status dts_create_problem(const dts_problem_desc* desc, dts_problem** out)
+{
+    if (!out) return fail(nullptr, DTS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(nullptr, DTS_ERR_INVALID_ARG, "desc is NULL");
+    dts_problem* p = new (std::nothrow) dts_problem();
+    if (!p) return fail(nullptr, DTS_ERR_OOM, "host allocation failed");
+    dts_status s = create(desc, p);
+    if (s != DTS_OK) {
+        g_thread_error = p->err;
+        destroy(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return DTS_OK;
+}
+
+dts_status dts_set_materials(dts_problem* p, int n_mat, const double* sigma_t, const double* sigma_s,
+                             const int32_t* mat_id, const double* scale_t, const double* scale_s)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (n_mat < 1 || !sigma_t || !sigma_s || !mat_id)
+        return fail(p, DTS_ERR_INVALID_ARG, "n_mat >= 1 and non-NULL sigma_t, sigma_s, mat_id required");
+    const int G = p->G, L = p->L, V = p->V;
+    for (size_t i = 0; i < (size_t)n_mat * G; ++i)
+        if (!(sigma_t[i] > 0.0) || !isfin(sigma_t[i]))
+            return fail(p, DTS_ERR_INVALID_ARG, "sigma_t must be finite and > 0");
+    int W = 0;
+    for (int m = 0; m < n_mat; ++m)
+        for (int l = 0; l <= L; ++l)
+            for (int gf = 0; gf < G; ++gf)
+                for (int gt = 0; gt < G; ++gt) {
+                    const double s = sigma_s[(((size_t)m * (L + 1) + l) * G + gf) * G + gt];
+                    if (!isfin(s)) return fail(p, DTS_ERR_INVALID_ARG, "sigma_s must be finite");
+                    if (l == 0 && s < 0.0) return fail(p, DTS_ERR_INVALID_ARG, "sigma_s0 must be >= 0");
+                    if (s != 0.0 && gt < gf)
+                        return fail(p, DTS_ERR_INVALID_ARG, "sigma_s must be downscatter only (g_to >= g_from)");
+                    if (s != 0.0) W = std::max(W, gt - gf);
+                }
+    for (int v = 0; v < V; ++v)
+        if (mat_id[v] < 0 || mat_id[v] >= n_mat) return fail(p, DTS_ERR_INVALID_ARG, "mat_id out of range");
+    for (const double* sc : {scale_t, scale_s})
+        if (sc)
+            for (int v = 0; v < V; ++v)
+                if (!(sc[v] > 0.0) || !isfin(sc[v]))
+                    return fail(p, DTS_ERR_INVALID_ARG, "scale factors must be finite and > 0");
+    DevGuard guard(p->d.device);
+    CK(cudaStreamSynchronize(p->stream));
+    if (n_mat != p->n_mat) {
+        dfree(p, p->sigma_t);
+        dfree(p, p->sigma_s);
+        p->sigma_t = p->sigma_s = nullptr;
+        TRY(dalloc_t(p, &p->sigma_t, (size_t)n_mat * G));
+        TRY(dalloc_t(p, &p->sigma_s, (size_t)n_mat * (L + 1) * G * G));
+        p->n_mat = n_mat;
+    }
+    CK(cudaMemcpy(p->sigma_t, sigma_t, sizeof(double) * n_mat * G, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->sigma_s, sigma_s, sizeof(double) * (size_t)n_mat * (L + 1) * G * G, cudaMemcpyHostToDevice));
+    std::vector<int32_t> mt = to_tiled<int32_t>(p, mat_id, -1);
+    CK(cudaMemcpy(p->mat_t, mt.data(), sizeof(int32_t) * p->NC, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->mat_nat, mat_id, sizeof(int32_t) * V, cudaMemcpyHostToDevice));
+    struct { const double* h; double** t; double** n; } sc[2] = {
+        {scale_t, &p->scale_t_t, &p->scale_t_nat}, {scale_s, &p->scale_s_t, nullptr}};
+    for (auto& e : sc) {
+        dfree(p, *e.t);
+        *e.t = nullptr;
+        if (e.n) {
+            dfree(p, *e.n);
+            *e.n = nullptr;
+        }
+        if (!e.h) continue;
+        std::vector<double> tt = to_tiled<double>(p, e.h, 1.0);
+        TRY(dalloc_t(p, e.t, p->NC));
+        CK(cudaMemcpy(*e.t, tt.data(), sizeof(double) * p->NC, cudaMemcpyHostToDevice));
+        if (e.n) {
+            TRY(dalloc_t(p, e.n, V));
+            CK(cudaMemcpy(*e.n, e.h, sizeof(double) * V, cudaMemcpyHostToDevice));
+        }
+    }
+    p->W = std::min(W, G - 1);
+    p->materials_set = true;
+    p->solved = false;
+    return DTS_OK;
+}
+
+dts_status dts_set_source(dts_problem* p, int batch_index, const dts_source* s)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!s) return fail(p, DTS_ERR_INVALID_ARG, "source is NULL");
+    if (batch_index < 0 || batch_index >= p->B) return fail(p, DTS_ERR_INVALID_ARG, "batch_index out of range");
+    const int G = p->G, V = p->V;
+    DevGuard guard(p->d.device);
+    double* row = &p->src_h[(size_t)batch_index * 8];
+    if (s->kind == 0) {
+        if (!s->q) return fail(p, DTS_ERR_INVALID_ARG, "kind 0 needs q");
+        for (size_t i = 0; i < (size_t)G * V; ++i)
+            if (!isfin(s->q[i])) return fail(p, DTS_ERR_INVALID_ARG, "q must be finite");
+        if (!p->q) {
+            TRY(dalloc_t(p, &p->q, (size_t)p->B * G * V));
+            CK(cudaMemset(p->q, 0, sizeof(double) * (size_t)p->B * G * V));
+        }
+        CK(cudaMemcpy(p->q + (size_t)batch_index * G * V, s->q, sizeof(double) * G * V, cudaMemcpyHostToDevice));
+        for (int i = 0; i < 8; ++i) row[i] = 0.0;
+        for (int g = 0; g < G; ++g) p->spec_h[(size_t)batch_index * G + g] = 0.0;
+    } else if (s->kind == 1) {
+        if (!s->spectrum) return fail(p, DTS_ERR_INVALID_ARG, "kind 1 needs a spectrum");
+        const double an = std::sqrt(s->axis[0] * s->axis[0] + s->axis[1] * s->axis[1] + s->axis[2] * s->axis[2]);
+        if (!(an > 0.0) || !isfin(an)) return fail(p, DTS_ERR_INVALID_ARG, "cone axis must be non-zero");
+        if (!(s->half_angle > 0.0) || !(s->half_angle <= kPi + 1e-12))
+            return fail(p, DTS_ERR_INVALID_ARG, "half_angle must be in (0, pi]");
+        for (int i = 0; i < 3; ++i)
+            if (!isfin(s->pos[i])) return fail(p, DTS_ERR_INVALID_ARG, "source position must be finite");
+        for (int g = 0; g < G; ++g) {
+            if (!isfin(s->spectrum[g]) || s->spectrum[g] < 0.0)
+                return fail(p, DTS_ERR_INVALID_ARG, "spectrum must be finite and >= 0");
+            p->spec_h[(size_t)batch_index * G + g] = s->spectrum[g];
+        }
+        row[0] = 1.0;
+        for (int i = 0; i < 3; ++i) {
+            row[1 + i] = s->pos[i];
+            row[4 + i] = s->axis[i];
+        }
+        row[7] = s->half_angle >= kPi ? kPi : s->half_angle;
+    } else {
+        return fail(p, DTS_ERR_INVALID_ARG, "source kind must be 0 or 1");
+    }
+    CK(cudaMemcpy(p->src + (size_t)batch_index * 8, row, sizeof(double) * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->spec + (size_t)batch_index * G, &p->spec_h[(size_t)batch_index * G],
+                  sizeof(double) * G, cudaMemcpyHostToDevice));
+    p->src_set[batch_index] = 1;
+    p->solved = false;
+    return DTS_OK;
+}
+
+dts_status dts_solve(dts_problem* p, dts_solve_stats* stats)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->materials_set) return fail(p, DTS_ERR_STATE, "dts_set_materials has not been called");
+    for (int b = 0; b < p->B; ++b)
+        if (!p->src_set[b]) return fail(p, DTS_ERR_STATE, "a batch member has no source");
+    DevGuard guard(p->d.device);
+    std::vector<int> hs(p->B, 1);
+    CK(cudaMemcpy(p->has_src, hs.data(), sizeof(int) * p->B, cudaMemcpyHostToDevice));
+    return run_solve(p, stats);
+}
+
+dts_status dts_get_scalar_fluence(dts_problem* p, int batch_index, dts_component comp, double* out,
+                                  size_t out_len, int out_is_device)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->solved) return fail(p, DTS_ERR_STATE, "no solve has completed");
+    if (batch_index < 0 || batch_index >= p->B) return fail(p, DTS_ERR_INVALID_ARG, "batch_index out of range");
+    if (!out) return fail(p, DTS_ERR_INVALID_ARG, "out is NULL");
+    const size_t n = (size_t)p->G * p->V;
+    if (out_len < n) return fail(p, DTS_ERR_INVALID_ARG, "out_len < G*V");
+    DevGuard guard(p->d.device);
+    const double* u = p->unc + (size_t)batch_index * n;
+    const double* c = p->col + (size_t)batch_index * n;
+    const double* srcp;
+    if (comp == DTS_COMP_UNCOLLIDED) srcp = u;
+    else if (comp == DTS_COMP_COLLIDED) srcp = c;
+    else if (comp == DTS_COMP_TOTAL) {
+        k_add<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(n, u, c, p->tmp);
+        CK(cudaGetLastError());
+        srcp = p->tmp;
+    } else return fail(p, DTS_ERR_INVALID_ARG, "unknown component");
+    if (out_is_device) {
+        CK(cudaMemcpyAsync(out, srcp, sizeof(double) * n, cudaMemcpyDeviceToDevice, p->stream));
+    } else {
+        CK(cudaMemcpyAsync(out, srcp, sizeof(double) * n, cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+    }
+    return DTS_OK;
+}
+
+dts_status dts_get_moments(dts_problem* p, int batch_index, int group, double* out, size_t out_len,
+                           int out_is_device)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->d.keep_moments) return fail(p, DTS_ERR_STATE, "problem was created without keep_moments");
+    if (!p->solved) return fail(p, DTS_ERR_STATE, "no solve has completed");
+    if (batch_index < 0 || batch_index >= p->B || group < 0 || group >= p->G)
+        return fail(p, DTS_ERR_INVALID_ARG, "batch_index or group out of range");
+    const size_t n = (size_t)p->K * p->V;
+    if (!out || out_len < n) return fail(p, DTS_ERR_INVALID_ARG, "out is NULL or out_len < K*V");
+    DevGuard guard(p->d.device);
+    const double* s = p->mom + ((size_t)batch_index * p->G + group) * n;
+    CK(cudaMemcpyAsync(out, s, sizeof(double) * n,
+                       out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+    if (!out_is_device) CK(cudaStreamSynchronize(p->stream));
+    return DTS_OK;
+}
+
+dts_status dts_get_iterations(dts_problem* p, int32_t* out, size_t out_len)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!out || out_len < p->iters.size()) return fail(p, DTS_ERR_INVALID_ARG, "out too small");
+    std::copy(p->iters.begin(), p->iters.end(), out);
+    return DTS_OK;
+}
+
+dts_status dts_get_residuals(dts_problem* p, double* out, size_t out_len)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!out || out_len < p->resid.size()) return fail(p, DTS_ERR_INVALID_ARG, "out too small");
+    std::copy(p->resid.begin(), p->resid.end(), out);
+    return DTS_OK;
+}
+
+dts_status dts_get_balance(dts_problem* p, double* out, size_t out_len)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!out || out_len < p->balance.size()) return fail(p, DTS_ERR_INVALID_ARG, "out too small");
+    std::copy(p->balance.begin(), p->balance.end(), out);
+    return DTS_OK;
+}
+
+const char* dts_last_error(const dts_problem* p) { return p ? p->err.c_str() : g_thread_error.c_str(); }
+
+void dts_destroy_problem(dts_problem* p)
+{
+    if (!p) return;
+    destroy(p);
+    delete p;
+}
+
+const char* dts_status_string(dts_status s)
+{
+    switch (s) {
+    case DTS_OK: return "DTS_OK";
+    case DTS_ERR_INVALID_ARG: return "DTS_ERR_INVALID_ARG";
+    case DTS_ERR_STATE: return "DTS_ERR_STATE";
+    case DTS_ERR_OOM: return "DTS_ERR_OOM";
+    case DTS_ERR_CUDA: return "DTS_ERR_CUDA";
+    case DTS_ERR_NOT_CONVERGED: return "DTS_ERR_NOT_CONVERGED";
+    case DTS_ERR_TIMEOUT: return "DTS_ERR_TIMEOUT";
+    case DTS_ERR_INTERNAL: return "DTS_ERR_INTERNAL";
+    }
+    return "unknown status";
+}
+
+int dts_version(void) { return 1; }
+
+dts_status dts_quadrature(int sn_order, double* mu, double* eta, double* xi, double* w, int* n_dirs)
+{
+    std::vector<double> a, b, c, d;
+    if (!ls_set(sn_order, a, b, c, d)) return fail(nullptr, DTS_ERR_INVALID_ARG, "sn_order must be 2, 4, 6 or 8");
+    if (!mu || !eta || !xi || !w) return fail(nullptr, DTS_ERR_INVALID_ARG, "NULL output");
+    std::copy(a.begin(), a.end(), mu);
+    std::copy(b.begin(), b.end(), eta);
+    std::copy(c.begin(), c.end(), xi);
+    std::copy(d.begin(), d.end(), w);
+    if (n_dirs) *n_dirs = (int)d.size();
+    return DTS_OK;
+}
+
+dts_status dts_moment_tables(int sn_order, int legendre_order, double* D, double* M)
+{
+    std::vector<double> a, b, c, w, Dv, Mv;
+    if (!ls_set(sn_order, a, b, c, w)) return fail(nullptr, DTS_ERR_INVALID_ARG, "sn_order must be 2, 4, 6 or 8");
+    if (legendre_order < 0 || legendre_order > 3)
+        return fail(nullptr, DTS_ERR_INVALID_ARG, "legendre_order must be in 0..3");
+    if (!D || !M) return fail(nullptr, DTS_ERR_INVALID_ARG, "NULL output");
+    moment_tables(legendre_order, a, b, c, w, Dv, Mv);
+    std::copy(Dv.begin(), Dv.end(), D);
+    std::copy(Mv.begin(), Mv.end(), M);
+    return DTS_OK;
+}
+
+long long dts_subsweep_size(int nx, int ny, int nz, int S)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || S < 0 || S > nx + ny + nz - 3) return 0;
+    return eq9(nx, ny, nz, S);
+}
+
+}  // extern "C"

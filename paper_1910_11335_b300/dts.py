@@ -1,0 +1,260 @@
+"""Python binding of the C ABI in include/dts.h (argument marshalling only).
+
+Every step of the solve runs in libdts.so (CUDA, sm_103a). There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import inputs
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdts.so")
+
+DTS_OK, DTS_ERR_INVALID_ARG, DTS_ERR_STATE, DTS_ERR_OOM, DTS_ERR_CUDA, DTS_ERR_NOT_CONVERGED, \
+    DTS_ERR_TIMEOUT, DTS_ERR_INTERNAL = range(8)
+PREC_FP64, PREC_FP32 = 0, 1
+UNCOLLIDED, COLLIDED, TOTAL = 0, 1, 2
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("n_groups", C.c_int), ("sn_order", C.c_int), ("legendre_order", C.c_int),
+                ("batch", C.c_int), ("precision", C.c_int), ("tol", C.c_double),
+                ("max_iters", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int),
+                ("keep_moments", C.c_int)]
+
+
+class SourceDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("q", _dp), ("pos", C.c_double * 3), ("axis", C.c_double * 3),
+                ("half_angle", C.c_double), ("spectrum", _dp)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("updates", C.c_int64), ("sweeps", C.c_int64), ("max_residual", C.c_double),
+                ("solve_ms", C.c_double), ("sweep_ms", C.c_double), ("reduce_ms", C.c_double),
+                ("launches", C.c_int64), ("converged", C.c_int),
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class DTSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+#: every function include/dts.h declares
+EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_solve",
+           "dts_get_scalar_fluence", "dts_get_moments", "dts_get_iterations", "dts_get_residuals",
+           "dts_get_balance", "dts_last_error", "dts_destroy_problem", "dts_status_string",
+           "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size")
+
+
+def lib():
+    """Load libdts.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1910_11335_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    pp = C.POINTER(C.c_void_p)
+    sig = {
+        "dts_create_problem": ([C.POINTER(ProblemDesc), pp], C.c_int),
+        "dts_set_materials": ([C.c_void_p, C.c_int, _dp, _dp, _ip, _dp, _dp], C.c_int),
+        "dts_set_source": ([C.c_void_p, C.c_int, C.POINTER(SourceDesc)], C.c_int),
+        "dts_solve": ([C.c_void_p, C.POINTER(SolveStats)], C.c_int),
+        "dts_get_scalar_fluence": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
+        "dts_get_moments": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
+        "dts_get_iterations": ([C.c_void_p, _ip, C.c_size_t], C.c_int),
+        "dts_get_residuals": ([C.c_void_p, _dp, C.c_size_t], C.c_int),
+        "dts_get_balance": ([C.c_void_p, _dp, C.c_size_t], C.c_int),
+        "dts_last_error": ([C.c_void_p], C.c_char_p),
+        "dts_destroy_problem": ([C.c_void_p], None),
+        "dts_status_string": ([C.c_int], C.c_char_p),
+        "dts_version": ([], C.c_int),
+        "dts_quadrature": ([C.c_int, _dp, _dp, _dp, _dp, C.POINTER(C.c_int)], C.c_int),
+        "dts_moment_tables": ([C.c_int, C.c_int, _dp, _dp], C.c_int),
+        "dts_subsweep_size": ([C.c_int, C.c_int, C.c_int, C.c_int], C.c_longlong),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().dts_status_string(s).decode()
+    except Exception:  # pragma: no cover
+        return f"status {s}"
+
+
+def _check(status: int, handle=None):
+    if status != DTS_OK:
+        msg = lib().dts_last_error(handle).decode()
+        raise DTSError(status, msg)
+
+
+def _dptr(a: Optional[np.ndarray]):
+    return C.cast(None, _dp) if a is None else a.ctypes.data_as(_dp)
+
+
+# ------------------------------------------------------------------ host helpers
+def quadrature(sn_order: int):
+    mu, eta, xi, w = (np.zeros(80) for _ in range(4))
+    n = C.c_int(0)
+    _check(lib().dts_quadrature(sn_order, _dptr(mu), _dptr(eta), _dptr(xi), _dptr(w), C.byref(n)))
+    k = n.value
+    return mu[:k].copy(), eta[:k].copy(), xi[:k].copy(), w[:k].copy()
+
+
+def moment_tables(sn_order: int, legendre_order: int):
+    """(D[K][nd], M[nd][K]) as the solver uses them."""
+    nd, K = sn_order * (sn_order + 2), (legendre_order + 1) ** 2
+    D, M = np.zeros((K, nd)), np.zeros((nd, K))
+    _check(lib().dts_moment_tables(sn_order, legendre_order, _dptr(D), _dptr(M)))
+    return D, M
+
+
+def subsweep_size(nx, ny, nz, S) -> int:
+    return int(lib().dts_subsweep_size(nx, ny, nz, S))
+
+
+# ------------------------------------------------------------------ problems
+class Problem:
+    """A solver instance on one GPU (wraps dts_problem)."""
+
+    def __init__(self, *, nx, ny, nz, dx, dy, dz, x0=0.0, y0=0.0, z0=0.0, n_groups=1,
+                 sn_order=4, legendre_order=0, batch=1, precision=PREC_FP64, tol=1e-8,
+                 max_iters=1000, device=0, stream=None, tile=(0, 0, 0), keep_moments=False):
+        d = ProblemDesc(nx, ny, nz, dx, dy, dz, x0, y0, z0, n_groups, sn_order, legendre_order,
+                        batch, precision, tol, max_iters, stream, device, tile[0], tile[1],
+                        tile[2], int(keep_moments))
+        h = C.c_void_p()
+        _check(lib().dts_create_problem(C.byref(d), C.byref(h)))
+        self._h = h
+        self.desc = d
+        self.V = nx * ny * nz
+        self.G, self.B = n_groups, batch
+        self.K = (legendre_order + 1) ** 2
+        self.nd = sn_order * (sn_order + 2)
+
+    # context manager / lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().dts_destroy_problem(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # inputs
+    def set_materials(self, sigma_t, sigma_s, mat_id, scale_t=None, scale_s=None):
+        st = np.ascontiguousarray(sigma_t, dtype=np.float64)
+        ss = np.ascontiguousarray(sigma_s, dtype=np.float64)
+        mi = np.ascontiguousarray(mat_id, dtype=np.int32)
+        a = None if scale_t is None else np.ascontiguousarray(scale_t, dtype=np.float64)
+        b = None if scale_s is None else np.ascontiguousarray(scale_s, dtype=np.float64)
+        _check(lib().dts_set_materials(self._h, st.shape[0], _dptr(st), _dptr(ss),
+                                       mi.ctypes.data_as(_ip), _dptr(a), _dptr(b)), self._h)
+
+    def set_source(self, b: int, src: inputs.Source):
+        q = None if src.q is None else np.ascontiguousarray(src.q, dtype=np.float64)
+        sp = None if src.spectrum is None else np.ascontiguousarray(src.spectrum, dtype=np.float64)
+        s = SourceDesc(src.kind, _dptr(q), (C.c_double * 3)(*src.pos),
+                       (C.c_double * 3)(*src.axis), src.half_angle, _dptr(sp))
+        _check(lib().dts_set_source(self._h, b, C.byref(s)), self._h)
+
+    # solve
+    def solve(self, allow_not_converged: bool = False) -> SolveStats:
+        st = SolveStats()
+        rc = lib().dts_solve(self._h, C.byref(st))
+        if rc == DTS_ERR_NOT_CONVERGED and allow_not_converged:
+            return st
+        _check(rc, self._h)
+        return st
+
+    # outputs
+    def fluence(self, b: int = 0, comp: int = TOTAL, out=None):
+        """Scalar fluence [G][V] of batch member b: a numpy array, or written
+        into `out` (a contiguous float64 CUDA tensor) on the problem's stream."""
+        n = self.G * self.V
+        if out is not None and hasattr(out, "data_ptr") and getattr(out, "is_cuda", False):
+            assert out.dtype.itemsize == 8 and out.is_contiguous() and out.numel() >= n
+            _check(lib().dts_get_scalar_fluence(self._h, b, comp, C.c_void_p(out.data_ptr()), n, 1),
+                   self._h)
+            return out
+        host = np.empty(n) if out is None else out
+        _check(lib().dts_get_scalar_fluence(self._h, b, comp, host.ctypes.data_as(C.c_void_p), n, 0),
+               self._h)
+        return host.reshape(self.G, self.V)
+
+    def moments(self, b: int, g: int):
+        out = np.empty(self.K * self.V)
+        _check(lib().dts_get_moments(self._h, b, g, out.ctypes.data_as(C.c_void_p), out.size, 0),
+               self._h)
+        return out.reshape(self.K, self.V)
+
+    def iterations(self):
+        out = np.zeros(self.B * self.G, dtype=np.int32)
+        _check(lib().dts_get_iterations(self._h, out.ctypes.data_as(_ip), out.size), self._h)
+        return out.reshape(self.B, self.G)
+
+    def residuals(self):
+        out = np.zeros(self.B * self.G)
+        _check(lib().dts_get_residuals(self._h, _dptr(out), out.size), self._h)
+        return out.reshape(self.B, self.G)
+
+    def balance(self):
+        out = np.zeros(self.B * self.G * 3)
+        _check(lib().dts_get_balance(self._h, _dptr(out), out.size), self._h)
+        return out.reshape(self.B, self.G, 3)
+
+
+def problem_from_workload(w: inputs.Workload, precision=PREC_FP64, tol=None, max_iters=None,
+                          tile=(0, 0, 0), keep_moments=False, device=0, stream=None,
+                          sources=None) -> Problem:
+    """Create a Problem for workload w and upload its materials and sources
+    (all of w.sources, or the subset `sources`)."""
+    srcs = w.sources if sources is None else [w.sources[i] for i in sources]
+    p = Problem(nx=w.nx, ny=w.ny, nz=w.nz, dx=w.dx, dy=w.dy, dz=w.dz, x0=w.x0, y0=w.y0, z0=w.z0,
+                n_groups=w.n_groups, sn_order=w.sn_order, legendre_order=w.legendre_order,
+                batch=len(srcs), precision=precision, tol=w.tol if tol is None else tol,
+                max_iters=w.max_iters if max_iters is None else max_iters, device=device,
+                stream=stream, tile=tile, keep_moments=keep_moments)
+    p.set_materials(w.sigma_t, w.sigma_s, w.mat_id.reshape(-1),
+                    None if w.scale_t is None else w.scale_t.reshape(-1),
+                    None if w.scale_s is None else w.scale_s.reshape(-1))
+    for b, s in enumerate(srcs):
+        p.set_source(b, s)
+    return p

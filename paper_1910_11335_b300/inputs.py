@@ -364,6 +364,37 @@ def detector_target_noise(n_pixels: int, seed_index: int = 3) -> np.ndarray:
     return 1.0 + 0.05 * rng.standard_normal(n_pixels)
 
 
+def first_groups(w: Workload, n_groups: int) -> Workload:
+    """The same problem restricted to its first n_groups (highest energies).
+    With downscatter only, groups 0..n-1 do not depend on later groups, so a
+    solve of the truncated problem reproduces them."""
+    import copy
+    t = copy.copy(w)
+    t.n_groups = n_groups
+    t.sigma_t = np.ascontiguousarray(w.sigma_t[:, :n_groups])
+    t.sigma_s = np.ascontiguousarray(w.sigma_s[:, :, :n_groups, :n_groups])
+    srcs = []
+    for s in w.sources:
+        s2 = copy.copy(s)
+        if s.q is not None:
+            s2.q = np.ascontiguousarray(s.q[:n_groups])
+        if s.spectrum is not None:
+            s2.spectrum = np.ascontiguousarray(s.spectrum[:n_groups])
+        srcs.append(s2)
+    t.sources = srcs
+    if w.group_energy_kev is not None:
+        t.group_energy_kev = w.group_energy_kev[:n_groups]
+    return t
+
+
+def with_sources(w: Workload, idx) -> Workload:
+    """The same problem with the batch restricted to sources idx."""
+    import copy
+    t = copy.copy(w)
+    t.sources = [w.sources[i] for i in idx]
+    return t
+
+
 WORKLOADS = {
     "plain16": plain_16,
     "hetero64": hetero_64,
