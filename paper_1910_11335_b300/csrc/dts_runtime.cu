@@ -78,9 +78,9 @@ struct dts_problem {
     std::vector<double> balance;      // [B][G][3]
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr, graph_red = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t eva = nullptr, evb = nullptr, evc = nullptr;   // recorded inside the graph
+    cudaEvent_t eva = nullptr, evb = nullptr, evc = nullptr;   // around the two graph replays
     int graph_launches = 0;           // kernels per graph replay
 };
 
@@ -312,7 +312,7 @@ CellParams cell_params(const dts_problem* p)
 }
 
 template <typename R>
-dts_status record_iteration(dts_problem* p)
+dts_status record_sweep(dts_problem* p)
 {
     SweepParams<R> sp;
     sp.nx = p->d.nx; sp.ny = p->d.ny; sp.nz = p->d.nz;
@@ -328,13 +328,17 @@ dts_status record_iteration(dts_problem* p)
     SweepFn<R> sf = sweep_fn<R>(p->ndo, p->K);
     if (!sf) return fail(p, DTS_ERR_INTERNAL, "no sweep kernel for this (S_N, P_L)");
     const size_t smem = sweep_smem(p);
-    CK(cudaEventRecord(p->eva, p->stream));
     for (int s = 0; s < p->n_stages; ++s) {
         const int cnt = p->stage_off_h[s + 1] - p->stage_off_h[s];
         const unsigned grid = (unsigned)cnt * 8u * (unsigned)p->B;
         sf<<<grid, kSweepThreads, smem, p->stream>>>(sp, s);
     }
-    CK(cudaEventRecord(p->evb, p->stream));
+    return DTS_OK;
+}
+
+template <typename R>
+dts_status record_reduce(dts_problem* p)
+{
     RedParams<R> rp;
     rp.B = p->B; rp.NT = p->NT; rp.TV = p->TV; rp.NC = p->NC;
     rp.part = (const R*)p->part; rp.phi = p->phi; rp.T = (R*)p->T; rp.F = p->F;
@@ -344,13 +348,32 @@ dts_status record_iteration(dts_problem* p)
     RedFn<R> rf = reduce_fn<R>(p->K);
     rf<<<dim3(p->nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
     k_resid_final<<<p->B, 256, 0, p->stream>>>(p->blk, p->nblk, p->leak, p->status);
-    CK(cudaEventRecord(p->evc, p->stream));
     p->graph_launches = p->n_stages + 2;
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(double) * 4 * p->B, cudaMemcpyDeviceToHost,
                        p->stream));
     return DTS_OK;
 }
 
+dts_status capture(dts_problem* p, dts_status (*rec)(dts_problem*), cudaGraphExec_t* out)
+{
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    dts_status s = rec(p);
+    cudaError_t ec = cudaStreamEndCapture(p->stream, &g);
+    if (s != DTS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (ec != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    ec = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ec != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+    return DTS_OK;
+}
+
+// one source iteration = two graphs (all tile stages of the sweep; the Eq. 3
+// reduction, residual and status copy), so that CUDA events recorded between
+// the two replays time the sweep and the reduction separately
 dts_status build_graph(dts_problem* p)
 {
     if (p->graph) return DTS_OK;
@@ -362,18 +385,8 @@ dts_status build_graph(dts_problem* p)
     else e = cudaFuncSetAttribute(sweep_fn<float>(p->ndo, p->K),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("sweep smem attribute: ") + cudaGetErrorString(e));
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    dts_status s = p->fp64 ? record_iteration<double>(p) : record_iteration<float>(p);
-    cudaError_t ec = cudaStreamEndCapture(p->stream, &g);
-    if (s != DTS_OK) {
-        if (g) cudaGraphDestroy(g);
-        return s;
-    }
-    if (ec != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
-    ec = cudaGraphInstantiate(&p->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (ec != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+    TRY(capture(p, p->fp64 ? record_sweep<double> : record_sweep<float>, &p->graph));
+    TRY(capture(p, p->fp64 ? record_reduce<double> : record_reduce<float>, &p->graph_red));
     return DTS_OK;
 }
 
@@ -384,6 +397,10 @@ dts_status ensure_ring(dts_problem* p)
     if (p->graph) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
+    }
+    if (p->graph_red) {
+        cudaGraphExecDestroy(p->graph_red);
+        p->graph_red = nullptr;
     }
     dfree(p, p->F);
     p->F = nullptr;
@@ -464,7 +481,11 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         CK(cudaGetLastError());
         int n_active = B;
         for (int it = 1; it <= p->d.max_iters && n_active > 0; ++it) {
+            CK(cudaEventRecord(p->eva, p->stream));
             CK(cudaGraphLaunch(p->graph, p->stream));
+            CK(cudaEventRecord(p->evb, p->stream));
+            CK(cudaGraphLaunch(p->graph_red, p->stream));
+            CK(cudaEventRecord(p->evc, p->stream));
             CK(cudaStreamSynchronize(p->stream));
             launches += p->graph_launches;
             {
@@ -546,6 +567,7 @@ void choose_tile(dts_problem* p)
         p->TX = p->d.tile_x;
         p->TY = p->d.tile_y;
         p->TZ = p->d.tile_z;
+        p->TV = p->TX * p->TY * p->TZ;
         return;
     }
     // default: 8^3 tiles (clipped to the grid), which keeps the FP64 S8 P3
@@ -553,6 +575,7 @@ void choose_tile(dts_problem* p)
     p->TX = std::min(8, p->d.nx);
     p->TY = std::min(8, p->d.ny);
     p->TZ = std::min(8, p->d.nz);
+    p->TV = p->TX * p->TY * p->TZ;
 }
 
 dts_status setup_schedule(dts_problem* p)
@@ -738,6 +761,7 @@ void destroy(dts_problem* p)
     DevGuard guard(p->d.device);
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->graph_red) cudaGraphExecDestroy(p->graph_red);
     for (void* a : p->allocs) cudaFree(a);
     p->allocs.clear();
     if (p->h_status) cudaFreeHost(p->h_status);
