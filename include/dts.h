@@ -210,6 +210,41 @@ dts_status dts_quadrature(int sn_order, double *mu, double *eta, double *xi, dou
 dts_status dts_moment_tables(int sn_order, int legendre_order, double *D, double *M);
 long long dts_subsweep_size(int nx, int ny, int nz, int S);
 
+/*
+ * One FP64 source iteration of a single group with no memory allocation.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory when they need a sweep -- code running inside a fixed,
+ * caller-managed memory pool, or hosts that forbid further cudaMalloc/cudaFree
+ * (those calls also synchronise the device). Everything the sweep needs
+ * besides the caller's inputs and outputs lives in one static device array of
+ * DTS_NOALLOC_SCRATCH_BYTES bytes that every GPU loading this library reserves
+ * until the process exits.
+ *
+ * Computes phi_k = sum_n D[k][n] psi_n for all K = (L+1)^2 moments, where psi_n
+ * is the diamond-difference sweep (set-to-zero fixup, vacuum boundaries) of
+ * direction n of the S_N set with angular source Q_n = sum_k M[n][k] T_k
+ * (dts_moment_tables gives D and M). This is what dts_solve does in each
+ * source iteration, for one group and one source.
+ *   src_moments [K][V] device, T_k per voxel (x fastest)
+ *   sigma_t     [V]    device, total cross section per voxel, > 0
+ *   phi         [K][V] device output
+ *   cuda_stream        stream to enqueue on (NULL = legacy default stream);
+ *                      the call returns without waiting, phi is ready when
+ *                      the stream reaches it
+ * The first call on a device looks up the device address of the scratch
+ * array (with that device current); make that first call before any stream
+ * capture. All calls share the array: calls whose work overlaps on the GPU
+ * (different streams, or devices sharing nothing but the same process are
+ * fine only if their streams are ordered) race and give wrong results.
+ * Errors: DTS_ERR_INVALID_ARG for bad sizes or when the grid needs more
+ * scratch than DTS_NOALLOC_SCRATCH_BYTES (about 1.2 KB per voxel at L = 3,
+ * 80 bytes at L = 0; message in dts_last_error(NULL)); DTS_ERR_CUDA.
+ */
+#define DTS_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+dts_status dts_sweep_once_noalloc(int nx, int ny, int nz, double dx, double dy, double dz,
+                                  int sn_order, int legendre_order, const double *src_moments,
+                                  const double *sigma_t, double *phi, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -289,6 +289,10 @@ k_sweep_stage(const SweepParams<R> p, const int stage)
     if (tid == 0 && leak != 0.0) atomicAdd(&p.leak[b], leak);
 }
 
+// Translation units that only launch the sweep define DTS_SWEEP_KERNEL_ONLY so
+// that the solver's other (non-template) kernels are defined once per library.
+#ifndef DTS_SWEEP_KERNEL_ONLY
+
 // ---------------------------------------------------------------------------
 // A5 + A6 (+ A10 terms): Eq. 3 octant sum in FP64 (fixed order 0..7), next
 // source T = F + sigma_s^{gg} phi, residual and balance partial sums.
@@ -649,5 +653,7 @@ __global__ void k_add(size_t n, const double* a, const double* b, double* out)
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[i] + b[i];
 }
+
+#endif  // DTS_SWEEP_KERNEL_ONLY
 
 }  // namespace dts

@@ -39,6 +39,12 @@ struct DevGuard {
 
 }  // namespace
 
+// lets other translation units of the library report a thread's last error
+__attribute__((visibility("hidden"))) void dts_internal_set_thread_error(const char* msg)
+{
+    g_thread_error = msg;
+}
+
 struct dts_problem {
     dts_problem_desc d{};
     std::string err = "no error";

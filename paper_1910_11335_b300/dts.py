@@ -64,7 +64,8 @@ _lib = None
 EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_solve",
            "dts_get_scalar_fluence", "dts_get_moments", "dts_get_iterations", "dts_get_residuals",
            "dts_get_balance", "dts_last_error", "dts_destroy_problem", "dts_status_string",
-           "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size")
+           "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size",
+           "dts_sweep_once_noalloc")
 
 
 def lib():
@@ -94,6 +95,9 @@ def lib():
         "dts_quadrature": ([C.c_int, _dp, _dp, _dp, _dp, C.POINTER(C.c_int)], C.c_int),
         "dts_moment_tables": ([C.c_int, C.c_int, _dp, _dp], C.c_int),
         "dts_subsweep_size": ([C.c_int, C.c_int, C.c_int, C.c_int], C.c_longlong),
+        "dts_sweep_once_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                    C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -139,6 +143,20 @@ def moment_tables(sn_order: int, legendre_order: int):
 
 def subsweep_size(nx, ny, nz, S) -> int:
     return int(lib().dts_subsweep_size(nx, ny, nz, S))
+
+
+def sweep_once_noalloc(nx, ny, nz, dx, dy, dz, sn_order, legendre_order, src_moments, sigma_t,
+                       phi, stream=None):
+    """One FP64 source iteration (sweep + moments) of one group using only the
+    library's fixed device scratch array, for callers that must not allocate.
+    src_moments [K][V], sigma_t [V] and phi [K][V] are contiguous float64 CUDA
+    tensors; work is enqueued on `stream` (a cudaStream_t handle or None)."""
+    for t in (src_moments, sigma_t, phi):
+        assert t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous()
+    _check(lib().dts_sweep_once_noalloc(nx, ny, nz, dx, dy, dz, sn_order, legendre_order,
+                                        C.c_void_p(src_moments.data_ptr()),
+                                        C.c_void_p(sigma_t.data_ptr()), C.c_void_p(phi.data_ptr()),
+                                        stream))
 
 
 # ------------------------------------------------------------------ problems
