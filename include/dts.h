@@ -81,7 +81,7 @@ typedef struct {
     int max_iters;              /* source iterations per group, >= 1 */
     void *cuda_stream;          /* cudaStream_t to order work on, or NULL */
     int device;                 /* CUDA device ordinal */
-    int tile_x, tile_y, tile_z; /* wavefront tile in voxels (each 1..16); all 0 = tuned */
+    int tile_x, tile_y, tile_z; /* wavefront tile in voxels (each 1..64); all 0 = default */
     int keep_moments;           /* 1: keep all K collided moments of every group */
 } dts_problem_desc;
 

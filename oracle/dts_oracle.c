@@ -367,8 +367,18 @@ int ora_uncollided_voxel(const ora_problem *p, const ora_source *s, int v,
  * repeated until no new negative appears (all negatives of a pass are zeroed
  * together). Returns psi_c; writes out[3]; *nfix counts the passes taken.
  */
+static double ora_dd_cell_mask(double q, double sig, const double a[3], const double in[3],
+                               double out[3], int *nfix, unsigned char *mask);
+
 double ora_dd_cell(double q, double sig, const double a[3], const double in[3],
                    double out[3], int *nfix)
+{
+    return ora_dd_cell_mask(q, sig, a, in, out, nfix, NULL);
+}
+
+/* the same cell solve, also reporting the fixup set (bit d = face d zeroed) */
+static double ora_dd_cell_mask(double q, double sig, const double a[3], const double in[3],
+                               double out[3], int *nfix, unsigned char *mask)
 {
     int fixed[3] = {0, 0, 0}, d, passes = 0;
     double psi = (q + a[0] * in[0] + a[1] * in[1] + a[2] * in[2]) / (sig + a[0] + a[1] + a[2]);
@@ -388,6 +398,7 @@ double ora_dd_cell(double q, double sig, const double a[3], const double in[3],
         for (d = 0; d < 3; ++d) out[d] = fixed[d] ? 0.0 : 2.0 * psi - in[d];
     }
     if (nfix) *nfix = passes;
+    if (mask) *mask = (unsigned char)(fixed[0] | fixed[1] << 1 | fixed[2] << 2);
     return psi;
 }
 
@@ -594,6 +605,260 @@ int ora_solve(const ora_problem *p, const ora_source *s, ora_result *res)
     }
     free(Y); free(D); free(M); free(phi_u); free(omu); free(F); free(phi); free(T);
     free(sigt); free(sigs); free(part); free(leak_o); free(fix_o);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Discrete adjoint of the converged solve (gradients of a linear functional) */
+/* ------------------------------------------------------------------------- */
+
+/* Forward sweep of one direction that also records each cell's fixup set
+ * (bit d set = face d zeroed) and its cell-centre flux. */
+static void ora_sweep_dir_record(const ora_problem *p, const double *sigt, double mu, double eta,
+                                 double xi, const double *Q, double *psi, unsigned char *fixset)
+{
+    int nx = p->nx, ny = p->ny, nz = p->nz, ii, jj, kk;
+    double a[3] = {2.0 * fabs(mu) / p->dx, 2.0 * fabs(eta) / p->dy, 2.0 * fabs(xi) / p->dz};
+    double *fx = (double *)calloc((size_t)ny * nz, sizeof(double));
+    double *fy = (double *)calloc((size_t)nx * nz, sizeof(double));
+    double *fz = (double *)calloc((size_t)nx * ny, sizeof(double));
+    for (kk = 0; kk < nz; ++kk) {
+        int k = xi > 0 ? kk : nz - 1 - kk;
+        for (jj = 0; jj < ny; ++jj) {
+            int j = eta > 0 ? jj : ny - 1 - jj;
+            for (ii = 0; ii < nx; ++ii) {
+                int i = mu > 0 ? ii : nx - 1 - ii, v = (k * ny + j) * nx + i, np;
+                double in[3] = {fx[k * ny + j], fy[k * nx + i], fz[j * nx + i]}, out[3];
+                psi[v] = ora_dd_cell_mask(Q[v], sigt[v], a, in, out, &np, &fixset[v]);
+                fx[k * ny + j] = out[0];
+                fy[k * nx + i] = out[1];
+                fz[j * nx + i] = out[2];
+            }
+        }
+    }
+    free(fx); free(fy); free(fz);
+}
+
+/* Transpose of the recorded sweep: cells in the reverse of the forward
+ * order; y[V] = dL/dpsi (direct), faces carry zeta = 2 (dL/d out-face) / a_d.
+ * Per cell, with F the recorded fixup set:
+ *   chi = (y + sum_{d not in F} a_d zeta_d) / (sigma + sum_{d not in F} a_d)
+ *   zeta passed upstream = 2 chi - zeta_d (d not in F), chi (d in F).
+ * chi = dL/dQ for the cell. */
+static void ora_sweep_dir_adjoint(const ora_problem *p, const double *sigt, double mu, double eta,
+                                  double xi, const double *y, const unsigned char *fixset, double *chi)
+{
+    int nx = p->nx, ny = p->ny, nz = p->nz, ii, jj, kk;
+    double a[3] = {2.0 * fabs(mu) / p->dx, 2.0 * fabs(eta) / p->dy, 2.0 * fabs(xi) / p->dz};
+    double *fx = (double *)calloc((size_t)ny * nz, sizeof(double));
+    double *fy = (double *)calloc((size_t)nx * nz, sizeof(double));
+    double *fz = (double *)calloc((size_t)nx * ny, sizeof(double));
+    for (kk = 0; kk < nz; ++kk) {
+        int k = xi > 0 ? nz - 1 - kk : kk;
+        for (jj = 0; jj < ny; ++jj) {
+            int j = eta > 0 ? ny - 1 - jj : jj;
+            for (ii = 0; ii < nx; ++ii) {
+                int i = mu > 0 ? nx - 1 - ii : ii, v = (k * ny + j) * nx + i, d;
+                double z[3] = {fx[k * ny + j], fy[k * nx + i], fz[j * nx + i]};
+                double num = y[v], den = sigt[v], c;
+                for (d = 0; d < 3; ++d)
+                    if (!(fixset[v] >> d & 1u)) { num += a[d] * z[d]; den += a[d]; }
+                c = num / den;
+                chi[v] = c;
+                for (d = 0; d < 3; ++d) z[d] = (fixset[v] >> d & 1u) ? c : 2.0 * c - z[d];
+                fx[k * ny + j] = z[0];
+                fy[k * nx + i] = z[1];
+                fz[j * nx + i] = z[2];
+            }
+        }
+    }
+    free(fx); free(fy); free(fz);
+}
+
+static int ora_l_of_k(int k)
+{
+    int l = 0;
+    while ((l + 1) * (l + 1) <= k) ++l;
+    return l;
+}
+
+/*
+ * Gradient of L = sum_g sum_v a^g(v) phi_total^g(v) (a = dL_dphi, [G][V]) with
+ * respect to the per-voxel multipliers scale_t and scale_s, at the solution of
+ * ora_solve (Eqs. 2-7 with the readings above). The discrete adjoint of the
+ * converged system: groups run G-1 -> 0; for each, the forward sweep is
+ * recomputed from the converged moments to record psi and the fixup sets;
+ * the adjoint source s = a e_0 + sum_{g2 > g} sigma_s^{g->g2} u^{g2} is
+ * iterated with u = M^T H^T D^T (s + sigma_s^{gg} u) to p->tol; then
+ *   dL/dsigma_t^g(v) = -sum_n chi_n psi_n,
+ *   dL/dsigma_{s,l}^{g'->g}(v) = sum_{k in l} u_k (phi_c,k^{g'} + phi_u^{g'} Y_k(Omega_u)),
+ *   dL/dphi_u^{g'} += sum_g sum_k u^g_k sigma_{s,l}^{g'->g} Y_k(Omega_u),
+ * and the uncollided part goes back through the ray trace:
+ *   dL/dtau^{g'}(v) = -phi_u^{g'}(v) dL/dphi_u^{g'}(v), tau = sum ell sigma_t.
+ * dsig_t_g [G][V] (may be NULL) receives dL/dsigma_t^g(v) of the collided part.
+ * Returns 0 on success.
+ */
+int ora_adjoint(const ora_problem *p, const ora_source *s, const double *dL_dphi,
+                double *dL_dscale_t, double *dL_dscale_s, double *dsig_t_g)
+{
+    const int V = p->nx * p->ny * p->nz, G = p->G, L = p->L, K = (L + 1) * (L + 1);
+    int nd, n, k, g, gp, v, it, l;
+    double mu[80], eta[80], xi[80], w[80];
+    double *Y, *D, *M, *omu, *Yu, *phic, *phiu, *T, *sigt, *psi, *u, *unew, *wv, *y, *chi, *sadj, *dphiu;
+    unsigned char *fix;
+    ora_result r;
+    nd = ora_quadrature(p->N, mu, eta, xi, w);
+    if (nd < 0) return -1;
+    Y = (double *)malloc(sizeof(double) * K * nd);
+    D = (double *)malloc(sizeof(double) * K * nd);
+    M = (double *)malloc(sizeof(double) * K * nd);
+    for (l = 0; l <= L; ++l)
+        for (k = l * l; k < (l + 1) * (l + 1); ++k)
+            for (n = 0; n < nd; ++n) {
+                Y[k * nd + n] = ora_real_sh(l, k - l * l - l, mu[n], eta[n], xi[n]);
+                D[k * nd + n] = w[n] * Y[k * nd + n];
+                M[k * nd + n] = (2.0 * l + 1.0) / (4.0 * ORA_PI) * Y[k * nd + n];
+            }
+    phic = (double *)calloc((size_t)G * K * V, sizeof(double));
+    phiu = (double *)calloc((size_t)G * V, sizeof(double));
+    memset(&r, 0, sizeof r);
+    r.phi_u = phiu;
+    r.phi_c = phic;
+    if (ora_solve(p, s, &r) != 0) return -2;
+    omu = (double *)calloc((size_t)3 * V, sizeof(double));
+    Yu = (double *)calloc((size_t)K * V, sizeof(double));
+    if (s->kind == 1) {
+        double *pg = (double *)malloc(sizeof(double) * G);
+        for (v = 0; v < V; ++v) {
+            ora_uncollided_voxel(p, s, v, pg, &omu[3 * v]);
+            for (l = 0; l <= L; ++l)
+                for (k = l * l; k < (l + 1) * (l + 1); ++k)
+                    Yu[(size_t)k * V + v] = ora_real_sh(l, k - l * l - l, omu[3 * v], omu[3 * v + 1], omu[3 * v + 2]);
+        }
+        free(pg);
+    }
+    T = (double *)malloc(sizeof(double) * (size_t)K * V);
+    sigt = (double *)malloc(sizeof(double) * V);
+    psi = (double *)malloc(sizeof(double) * (size_t)nd * V);
+    fix = (unsigned char *)malloc((size_t)nd * V);
+    u = (double *)malloc(sizeof(double) * (size_t)K * V);
+    unew = (double *)malloc(sizeof(double) * (size_t)K * V);
+    wv = (double *)malloc(sizeof(double) * (size_t)K * V);
+    y = (double *)malloc(sizeof(double) * V);
+    chi = (double *)malloc(sizeof(double) * (size_t)nd * V);
+    sadj = (double *)calloc((size_t)G * K * V, sizeof(double));   /* adjoint sources per group */
+    dphiu = (double *)calloc((size_t)G * V, sizeof(double));
+    for (v = 0; v < V; ++v) { dL_dscale_t[v] = 0.0; dL_dscale_s[v] = 0.0; }
+    for (g = 0; g < G; ++g)
+        for (v = 0; v < V; ++v) sadj[(size_t)g * K * V + v] = dL_dphi[(size_t)g * V + v];
+
+    for (g = G - 1; g >= 0; --g) {
+        /* converged source of group g: T = q + downscatter + in-group scatter */
+        for (v = 0; v < V; ++v) sigt[v] = ora_sigt(p, v, g);
+        for (k = 0; k < K; ++k) {
+            l = ora_l_of_k(k);
+            for (v = 0; v < V; ++v) {
+                double t = (s->kind == 0 && k == 0) ? s->q[(size_t)g * V + v] : 0.0;
+                for (gp = 0; gp <= g; ++gp) {
+                    double sg = ora_sigs(p, v, l, gp, g);
+                    if (s->kind == 1) t += sg * phiu[(size_t)gp * V + v] * Yu[(size_t)k * V + v];
+                    t += sg * phic[((size_t)gp * K + k) * V + v];
+                }
+                T[(size_t)k * V + v] = t;
+            }
+        }
+        /* record psi and the fixup sets of the converged sweep */
+        for (n = 0; n < nd; ++n) {
+            double *Q = unew;   /* scratch */
+            for (v = 0; v < V; ++v) {
+                double q = 0.0;
+                for (k = 0; k < K; ++k) q += M[k * nd + n] * T[(size_t)k * V + v];
+                Q[v] = q;
+            }
+            ora_sweep_dir_record(p, sigt, mu[n], eta[n], xi[n], Q, psi + (size_t)n * V, fix + (size_t)n * V);
+        }
+        /* adjoint source iteration */
+        for (v = 0; v < K * V; ++v) u[v] = 0.0;
+        for (it = 1; it <= p->max_iters; ++it) {
+            double dn = 0.0, nn = 0.0;
+            for (k = 0; k < K; ++k) {
+                l = ora_l_of_k(k);
+                for (v = 0; v < V; ++v)
+                    wv[(size_t)k * V + v] = sadj[((size_t)g * K + k) * V + v] + ora_sigs(p, v, l, g, g) * u[(size_t)k * V + v];
+            }
+            for (v = 0; v < K * V; ++v) unew[v] = 0.0;
+            for (n = 0; n < nd; ++n) {
+                for (v = 0; v < V; ++v) {
+                    double t = 0.0;
+                    for (k = 0; k < K; ++k) t += D[k * nd + n] * wv[(size_t)k * V + v];
+                    y[v] = t;
+                }
+                ora_sweep_dir_adjoint(p, sigt, mu[n], eta[n], xi[n], y, fix + (size_t)n * V, chi + (size_t)n * V);
+                for (k = 0; k < K; ++k)
+                    for (v = 0; v < V; ++v) unew[(size_t)k * V + v] += M[k * nd + n] * chi[(size_t)n * V + v];
+            }
+            for (v = 0; v < V; ++v) {
+                double d = unew[v] - u[v];
+                dn += d * d;
+                nn += unew[v] * unew[v];
+            }
+            memcpy(u, unew, sizeof(double) * (size_t)K * V);
+            if (!(nn > 0.0) || sqrt(dn / nn) < p->tol) break;
+        }
+        /* gradients of group g */
+        for (v = 0; v < V; ++v) {
+            const int m = p->mat[v];
+            const double ss = p->scale_s ? p->scale_s[v] : 1.0;
+            double gst = 0.0, gss = 0.0;
+            for (n = 0; n < nd; ++n) gst -= chi[(size_t)n * V + v] * psi[(size_t)n * V + v];
+            if (dsig_t_g) dsig_t_g[(size_t)g * V + v] = gst;
+            dL_dscale_t[v] += p->sigma_t[m * G + g] * gst;
+            for (k = 0; k < K; ++k) {
+                const double uk = u[(size_t)k * V + v];
+                l = ora_l_of_k(k);
+                for (gp = 0; gp <= g; ++gp) {
+                    const double tab = p->sigma_s[(((size_t)m * (L + 1) + l) * G + gp) * G + g];
+                    double src = phic[((size_t)gp * K + k) * V + v];
+                    if (s->kind == 1) {
+                        src += phiu[(size_t)gp * V + v] * Yu[(size_t)k * V + v];
+                        dphiu[(size_t)gp * V + v] += uk * tab * ss * Yu[(size_t)k * V + v];
+                    }
+                    gss += tab * uk * src;
+                }
+                /* adjoint downscatter into the lower groups */
+                for (gp = 0; gp < g; ++gp)
+                    sadj[((size_t)gp * K + k) * V + v] += ora_sigs(p, v, l, gp, g) * uk;
+            }
+            dL_dscale_s[v] += gss;
+        }
+    }
+    /* uncollided fluence: back through the ray trace */
+    if (s->kind == 1) {
+        int na = ora_max_alphas(p), ns, t;
+        double *alpha = (double *)malloc(sizeof(double) * na), *sl = (double *)malloc(sizeof(double) * na);
+        int *sv = (int *)malloc(sizeof(int) * na);
+        for (v = 0; v < V; ++v) {
+            int i = v % p->nx, j = (v / p->nx) % p->ny, kz = v / (p->nx * p->ny);
+            double C[3] = {p->x0 + (i + 0.5) * p->dx, p->y0 + (j + 0.5) * p->dy, p->z0 + (kz + 0.5) * p->dz};
+            int any = 0;
+            for (g = 0; g < G; ++g) any |= phiu[(size_t)g * V + v] != 0.0;
+            if (!any) continue;
+            ns = ora_segments(p, s->pos, C, alpha, sv, sl);
+            for (t = 0; t < ns; ++t) {
+                const int vp = sv[t], m = p->mat[vp];
+                double acc = 0.0;
+                for (g = 0; g < G; ++g) {
+                    const double e = -phiu[(size_t)g * V + v] *
+                                     (dL_dphi[(size_t)g * V + v] + dphiu[(size_t)g * V + v]);
+                    acc += e * sl[t] * p->sigma_t[m * G + g];
+                }
+                dL_dscale_t[vp] += acc;
+            }
+        }
+        free(alpha); free(sl); free(sv);
+    }
+    free(Y); free(D); free(M); free(phic); free(phiu); free(omu); free(Yu); free(T); free(sigt);
+    free(psi); free(fix); free(u); free(unew); free(wv); free(y); free(chi); free(sadj); free(dphiu);
     return 0;
 }
 

@@ -79,6 +79,8 @@ def load():
         lib.ora_solve.argtypes = [C.POINTER(_Problem), C.POINTER(_Source), C.POINTER(_Result)]
         lib.ora_solve.restype = C.c_int
         lib.ora_has_openmp.restype = C.c_int
+        lib.ora_adjoint.argtypes = [C.POINTER(_Problem), C.POINTER(_Source), _dp, _dp, _dp, _dp]
+        lib.ora_adjoint.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -227,6 +229,20 @@ def solve(w, source_index: int = 0, tol=None, max_iters=None, n_threads=1,
     if rc != 0:
         raise RuntimeError(f"oracle solve failed ({rc})")
     return r
+
+
+def adjoint(w, dL_dphi, source_index: int = 0, tol=None, max_iters=None, n_threads=1):
+    """Gradient of L = sum a * phi_total (a = dL_dphi [G][V]) with respect to the
+    per-voxel multipliers of sigma_t and sigma_s, by the discrete adjoint of the
+    converged solve. Returns (dL/dscale_t [V], dL/dscale_s [V], dL/dsigma_t^g [G][V])."""
+    p, keep = _problem(w, tol, max_iters, n_threads)
+    s = _source(w.sources[source_index], keep)
+    a = np.ascontiguousarray(dL_dphi, dtype=np.float64).reshape(w.n_groups, w.n_voxels)
+    gt, gs = np.zeros(w.n_voxels), np.zeros(w.n_voxels)
+    gg = np.zeros((w.n_groups, w.n_voxels))
+    if load().ora_adjoint(C.byref(p), C.byref(s), _ptr(a), _ptr(gt), _ptr(gs), _ptr(gg)) != 0:
+        raise RuntimeError("oracle adjoint failed")
+    return gt, gs, gg
 
 
 def solve_workload(w, **kw):

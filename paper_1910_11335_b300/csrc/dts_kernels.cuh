@@ -9,8 +9,8 @@
 //
 //   T    [B][NT][K][TV]   R       scatter + fixed source moments (this iteration)
 //   part [8][B][NT][K][TV] R      per-octant moment partials of the last sweep
-//   phi  [B][NT][K][TV]   double  flux moments of the current group
-//   F    [W+1][B][NT][K][TV] double fixed-source ring (first-collision + downscatter)
+//   phi00 [B][NT*TV]     double  scalar flux of the current group
+//   F    [W+1][B][NT][K][TV] R    fixed-source ring (first-collision + downscatter)
 //   xf   [8][B][NTy*NTz][NDO][TY*TZ] R  x-faces in flight (likewise yf, zf)
 #pragma once
 #include <cuda_runtime.h>
@@ -289,24 +289,255 @@ k_sweep_stage(const SweepParams<R> p, const int stage)
     if (tid == 0 && leak != 0.0) atomicAdd(&p.leak[b], leak);
 }
 
+// ---------------------------------------------------------------------------
+// A3 + A4, warp-synchronous form for tiles of TY x TZ = 32 x-lines.
+// One lane owns one x-line of the tile and walks it cell by cell; the x-face
+// stays in a register, the y- and z-faces of the neighbouring lines arrive
+// through warp shuffles one step later (the i+j+k wavefront of Sec. II.B,
+// skewed across lanes), so the wavefront needs no CTA barrier. Each warp
+// chains several directions of the octant back to back so the pipeline
+// ramp is paid once per warp, not once per direction. Padding cells pass
+// every face through unchanged, so a tile's outgoing faces on the downstream
+// boundary of the grid are exactly the leakage.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R fast_div(R a, R b) { return a / b; }
+template <>
+__device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
+
+template <typename R>
+__device__ __forceinline__ R dd_cell_line(R q, R sig, R ax, R ay, R az, R ix, R iy, R iz,
+                                          R& ox, R& oy, R& oz)
+{
+    R psi = fast_div<R>(q + ax * ix + ay * iy + az * iz, sig + ax + ay + az);
+    ox = R(2) * psi - ix;
+    oy = R(2) * psi - iy;
+    oz = R(2) * psi - iz;
+    if (ox < R(0) || oy < R(0) || oz < R(0)) {
+        bool fx = false, fy = false, fz = false;
+#pragma unroll 1
+        for (int pass = 0; pass < 3; ++pass) {
+            const bool nx = !fx && ox < R(0), ny = !fy && oy < R(0), nz = !fz && oz < R(0);
+            if (!(nx || ny || nz)) break;
+            fx |= nx;
+            fy |= ny;
+            fz |= nz;
+            const R num = q + (fx ? R(0.5) * ax : ax) * ix + (fy ? R(0.5) * ay : ay) * iy +
+                          (fz ? R(0.5) * az : az) * iz;
+            const R den = sig + (fx ? R(0) : ax) + (fy ? R(0) : ay) + (fz ? R(0) : az);
+            psi = fast_div<R>(num, den);
+            ox = fx ? R(0) : R(2) * psi - ix;
+            oy = fy ? R(0) : R(2) * psi - iy;
+            oz = fz ? R(0) : R(2) * psi - iz;
+        }
+    }
+    return psi;
+}
+
+template <typename R, int NDO, int K>
+__host__ __device__ inline size_t sweep_lines_smem_bytes(int TX, int TY, int TZ)
+{
+    const int TV = TX * TY * TZ;
+    size_t n = (size_t)NDO * TV + (size_t)NDO * (TY * TZ + TX * TZ + TX * TY) + TV +
+               2 * NDO * K + 4 * NDO;
+    size_t bytes = (n * sizeof(R) + 15) & ~size_t(15);
+    return bytes + sizeof(double) * (3 * NDO + 32);
+}
+
+constexpr int kLineThreadsMax = 128;
+
+// resident CTAs per SM the register allocation must allow (FP32: 8, FP64: 4)
+template <typename R> struct LinesOcc { static constexpr int value = sizeof(R) == 4 ? 8 : 4; };
+
+template <typename R, int NDO, int K, int TY, int TZ>
+__global__ void __launch_bounds__(kLineThreadsMax, LinesOcc<R>::value)
+k_sweep_lines(const SweepParams<R> p, const int stage)
+{
+    static_assert(TY * TZ == 32, "one warp lane per x-line");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int TX = p.TX, TV = TX * TY * TZ;
+    const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
+    int bid = blockIdx.x;
+    const int tl = bid % cnt;
+    bid /= cnt;
+    const int oct = bid & 7, b = bid >> 3;
+    if (!p.active[b]) return;
+    const unsigned pk = p.stage_tiles[s0 + tl];
+    const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
+    const bool negx = oct & 1, negy = oct & 2, negz = oct & 4;
+    const int tx = negx ? p.NTx - 1 - ta : ta;
+    const int ty = negy ? p.NTy - 1 - tb : tb;
+    const int tz = negz ? p.NTz - 1 - tc : tc;
+    const int tile = (tz * p.NTy + ty) * p.NTx + tx;
+    constexpr int fxn = TY * TZ;
+    const int fyn = TX * TZ, fzn = TX * TY;
+
+    R* Qs = reinterpret_cast<R*>(smem);        // [NDO][TV]: source, then psi
+    R* fx = Qs + NDO * TV;                      // [NDO][32] indexed by line = sz*TY + sy
+    R* fy = fx + NDO * fxn;                     // [NDO][TX*TZ] indexed sz*TX + sx
+    R* fz = fy + NDO * fyn;                     // [NDO][TX*TY] indexed sy*TX + sx
+    R* sg = fz + NDO * fzn;                     // [TV]
+    R* Ms = sg + TV;                            // [NDO][K]
+    R* Ds = Ms + NDO * K;                       // [K][NDO]
+    R* As = Ds + NDO * K;                       // [NDO][4]
+    const size_t off = ((size_t)(As + 4 * NDO - Qs) * sizeof(R) + 15) & ~size_t(15);
+    double* Lw = reinterpret_cast<double*>(smem + off);    // [NDO][3]
+    double* red = Lw + 3 * NDO;                             // [32]
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int n0 = oct * NDO;
+    for (int i = tid; i < NDO * K; i += nth) {
+        Ms[i] = p.M[n0 * K + i];
+        Ds[(i % K) * NDO + i / K] = p.Dt[n0 * K + i];
+    }
+    for (int i = tid; i < NDO * 3; i += nth) {
+        As[(i / 3) * 4 + i % 3] = p.A[n0 * 3 + i];
+        Lw[i] = p.Lw[n0 * 3 + i];
+    }
+    const size_t BB = p.B;
+    R* gx = p.xf + (((size_t)oct * BB + b) * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * (size_t)(NDO * fxn);
+    R* gy = p.yf + (((size_t)oct * BB + b) * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * (size_t)(NDO * fyn);
+    R* gz = p.zf + (((size_t)oct * BB + b) * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * (size_t)(NDO * fzn);
+    for (int i = tid; i < NDO * fxn; i += nth) fx[i] = ta > 0 ? gx[i] : R(0);
+    for (int i = tid; i < NDO * fyn; i += nth) fy[i] = tb > 0 ? gy[i] : R(0);
+    for (int i = tid; i < NDO * fzn; i += nth) fz[i] = tc > 0 ? gz[i] : R(0);
+    __syncthreads();
+
+    // phase A: scatter-source contraction Q_n = sum_k M[n][k] T_k
+    const R* Tt = p.T + ((size_t)b * p.NT + tile) * (size_t)(K * TV);
+    const R* st = p.sigt + (size_t)tile * TV;
+#pragma unroll 1
+    for (int c = tid; c < TV; c += nth) {
+        R t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] = Tt[k * TV + c];
+        sg[c] = st[c];
+#pragma unroll 1
+        for (int d = 0; d < NDO; ++d) {
+            R q = R(0);
+#pragma unroll
+            for (int k = 0; k < K; ++k) q = fma(Ms[d * K + k], t[k], q);
+            Qs[d * TV + c] = q;
+        }
+    }
+    __syncthreads();
+
+    // phase B: lane = x-line, warp = a run of directions, wavefront by shuffles
+    {
+        const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+        const int d0 = warp * NDO / nw, d1 = (warp + 1) * NDO / nw;
+        const int ly = lane % TY, lz = lane / TY;
+        const int sy = negy ? TY - 1 - ly : ly, sz = negz ? TZ - 1 - lz : lz;
+        const int line = sz * TY + sy;
+        const bool line_ok = (ty * TY + sy) < p.ny && (tz * TZ + sz) < p.nz;
+        const int nvx = p.nx - tx * TX;             // valid cells along x in this tile
+        const int total = (d1 - d0) * TX, ls = ly + lz;
+        int j = 0, lx = 0, d = d0;
+        R ax = R(0), ay = R(0), az = R(0), xin = R(0), ycur = R(0), zcur = R(0), ysh = R(0), zsh = R(0);
+        const int nsteps = total + TY + TZ - 2;
+        for (int t = 0; t < nsteps; ++t) {
+            const int u = t - ls;
+            if (u >= 0 && u < total) {
+                if (lx == 0) {
+                    d = d0 + j;
+                    ax = As[d * 4];
+                    ay = As[d * 4 + 1];
+                    az = As[d * 4 + 2];
+                    xin = fx[d * fxn + line];
+                }
+                const int sx = negx ? TX - 1 - lx : lx;
+                const int c = line * TX + sx;
+                R* pq = Qs + d * TV + c;
+                R* py = fy + d * fyn + sz * TX + sx;
+                R* pz = fz + d * fzn + sy * TX + sx;
+                const R yin = ly ? ysh : *py;
+                const R zin = lz ? zsh : *pz;
+                R ox, oy, oz, psi;
+                if (line_ok && sx < nvx) {
+                    psi = dd_cell_line<R>(*pq, sg[c], ax, ay, az, xin, yin, zin, ox, oy, oz);
+                } else {
+                    psi = R(0);
+                    ox = xin;
+                    oy = yin;
+                    oz = zin;
+                }
+                *pq = psi;
+                if (ly == TY - 1) *py = oy;
+                if (lz == TZ - 1) *pz = oz;
+                xin = ox;
+                ycur = oy;
+                zcur = oz;
+                if (++lx == TX) {
+                    fx[d * fxn + line] = ox;
+                    lx = 0;
+                    ++j;
+                }
+            }
+            ysh = __shfl_up_sync(0xffffffffu, ycur, 1);
+            zsh = __shfl_up_sync(0xffffffffu, zcur, TY);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+
+    // phase C: per-octant moment partial P_o[k] = sum_n D[k][n] psi_n
+    R* out = p.part + (((size_t)oct * BB + b) * p.NT + tile) * (size_t)(K * TV);
+#pragma unroll 1
+    for (int c = tid; c < TV; c += nth) {
+        R ps[NDO];
+#pragma unroll
+        for (int d = 0; d < NDO; ++d) ps[d] = Qs[d * TV + c];
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            R acc = R(0);
+#pragma unroll
+            for (int d = 0; d < NDO; ++d) acc = fma(Ds[k * NDO + d], ps[d], acc);
+            out[k * TV + c] = acc;
+        }
+    }
+    // outgoing faces; on the downstream boundary of the grid they leave it
+    const bool lbx = negx ? tx == 0 : tx == p.NTx - 1;
+    const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
+    const bool lbz = negz ? tz == 0 : tz == p.NTz - 1;
+    double leak = 0.0;
+    for (int i = tid; i < NDO * fxn; i += nth) {
+        gx[i] = fx[i];
+        if (lbx) leak += Lw[(i / fxn) * 3] * (double)fx[i];
+    }
+    for (int i = tid; i < NDO * fyn; i += nth) {
+        gy[i] = fy[i];
+        if (lby) leak += Lw[(i / fyn) * 3 + 1] * (double)fy[i];
+    }
+    for (int i = tid; i < NDO * fzn; i += nth) {
+        gz[i] = fz[i];
+        if (lbz) leak += Lw[(i / fzn) * 3 + 2] * (double)fz[i];
+    }
+    if (lbx || lby || lbz) {
+        leak = block_sum(leak, red);
+        if (tid == 0 && leak != 0.0) atomicAdd(&p.leak[b], leak);
+    }
+}
+
 // Translation units that only launch the sweep define DTS_SWEEP_KERNEL_ONLY so
 // that the solver's other (non-template) kernels are defined once per library.
 #ifndef DTS_SWEEP_KERNEL_ONLY
 
 // ---------------------------------------------------------------------------
-// A5 + A6 (+ A10 terms): Eq. 3 octant sum in FP64 (fixed order 0..7), next
-// source T = F + sigma_s^{gg} phi, residual and balance partial sums.
+// A5 + A6 (+ A10 terms): Eq. 3 octant sum of the scalar flux in FP64 (fixed
+// order 0..7), the higher moments in the sweep precision R, the next source
+// T = F + sigma_s^{gg} phi, and the residual and balance partial sums (FP64).
 // ---------------------------------------------------------------------------
 template <typename R>
 struct RedParams {
     int B, NT, TV, NC;
     const R* part;
-    double* phi;
+    double* phi00;             // [B][NC] scalar flux of the current group
     R* T;
-    const double* F;
+    const R* F;
     size_t Fstride;
     const int* ctl;            // [0] group, [1] fixed-source slot
-    const double* sigs;        // [L+1][NC] in-group scatter per cell
+    const R* sigs;             // [L+1][NC] in-group scatter per cell
+    const double* sigs0;       // [NC] l = 0 in-group scatter, FP64
     const double* sigt64;      // [NC]
     const int* mat_t;          // [NC], -1 = padding
     const int* active;
@@ -326,32 +557,33 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedParams<R> p)
         const int tile = ct / p.TV, c = ct - tile * p.TV;
         const size_t base = ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
         const size_t ostride = (size_t)p.B * p.NT * K * p.TV;
+        const R* __restrict__ pp = p.part + base;
+        R* __restrict__ T = p.T + base;
+        double* __restrict__ ph = p.phi00 + (size_t)b * p.NC + ct;
         if (p.mat_t[ct] >= 0) {
-            const double* F = p.F + (size_t)p.ctl[1] * p.Fstride + base;
+            const R* __restrict__ F = p.F + (size_t)p.ctl[1] * p.Fstride + base;
+            double s0 = 0.0;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const size_t ik = base + (size_t)k * p.TV;
-                double s = 0.0;
+            for (int o = 0; o < 8; ++o) s0 += (double)pp[o * ostride];
+            const double old = *ph, sl0 = p.sigs0[ct], f0 = (double)F[0];
+            const double dd = s0 - old;
+            ds = dd * dd;
+            ns = s0 * s0;
+            ab = p.vol * p.sigt64[ct] * s0;
+            sr = p.vol * (f0 + sl0 * old);
+            *ph = s0;
+            T[0] = (R)(f0 + sl0 * s0);
 #pragma unroll
-                for (int o = 0; o < 8; ++o) s += (double)p.part[o * ostride + ik];
-                const double sl = p.sigs[(size_t)l_of_k(k) * p.NC + ct];
-                if (k == 0) {
-                    const double old = p.phi[ik];
-                    const double dd = s - old;
-                    ds += dd * dd;
-                    ns += s * s;
-                    ab += p.vol * p.sigt64[ct] * s;
-                    sr += p.vol * (F[0] + sl * old);
-                }
-                p.phi[ik] = s;
-                p.T[ik] = (R)(F[(size_t)k * p.TV] + sl * s);
+            for (int k = 1; k < K; ++k) {
+                R s = R(0);
+#pragma unroll
+                for (int o = 0; o < 8; ++o) s += pp[o * ostride + (size_t)k * p.TV];
+                T[(size_t)k * p.TV] = F[(size_t)k * p.TV] + p.sigs[(size_t)l_of_k(k) * p.NC + ct] * s;
             }
         } else {
+            *ph = 0.0;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                p.phi[base + (size_t)k * p.TV] = 0.0;
-                p.T[base + (size_t)k * p.TV] = R(0);
-            }
+            for (int k = 0; k < K; ++k) T[(size_t)k * p.TV] = R(0);
         }
     }
     ds = block_sum(ds, red);
@@ -420,7 +652,7 @@ __device__ inline int tiled_to_natural(const CellParams& p, int ct, double* C)
 }
 
 template <typename R>
-__global__ void k_group_xs(const CellParams p, int g, R* sigt_r, double* sigt64, double* sigs)
+__global__ void k_group_xs(const CellParams p, int g, R* sigt_r, double* sigt64, R* sigs, double* sigs0)
 {
     const int ct = blockIdx.x * blockDim.x + threadIdx.x;
     if (ct >= p.NC) return;
@@ -428,7 +660,8 @@ __global__ void k_group_xs(const CellParams p, int g, R* sigt_r, double* sigt64,
     if (m < 0) {
         sigt_r[ct] = R(1);
         sigt64[ct] = 0.0;
-        for (int l = 0; l <= p.L; ++l) sigs[(size_t)l * p.NC + ct] = 0.0;
+        sigs0[ct] = 0.0;
+        for (int l = 0; l <= p.L; ++l) sigs[(size_t)l * p.NC + ct] = R(0);
         return;
     }
     double st = p.sigma_t[(size_t)m * p.G + g];
@@ -436,19 +669,19 @@ __global__ void k_group_xs(const CellParams p, int g, R* sigt_r, double* sigt64,
     sigt_r[ct] = (R)st;
     sigt64[ct] = st;
     const double ss = p.scale_s_t ? p.scale_s_t[ct] : 1.0;
-    for (int l = 0; l <= p.L; ++l)
-        sigs[(size_t)l * p.NC + ct] =
-            p.sigma_s[(((size_t)m * (p.L + 1) + l) * p.G + g) * p.G + g] * ss;
+    for (int l = 0; l <= p.L; ++l) {
+        const double v = p.sigma_s[(((size_t)m * (p.L + 1) + l) * p.G + g) * p.G + g] * ss;
+        sigs[(size_t)l * p.NC + ct] = (R)v;
+        if (l == 0) sigs0[ct] = v;
+    }
 }
 
-// phi = 0 and T = F[slot] at the start of a group (phi^(0) = 0)
+// T = F[slot] at the start of a group (phi^(0) = 0)
 template <typename R>
-__global__ void k_group_init(int total, const double* F, double* phi, R* T)
+__global__ void k_group_init(size_t total, const R* F, R* T)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)total) return;
-    phi[i] = 0.0;
-    T[i] = (R)F[i];
+    if (i < total) T[i] = F[i];
 }
 
 __global__ void k_set_ctl(int* ctl, int g, int slot)
@@ -560,35 +793,37 @@ __global__ void k_raytrace(const RayParams p, int g0)
 //   q_lm = sum_{g'<=gt} sigma_{s,l}^{g'->gt} phi_u^{g'} Y_lm(Omega_u)
 // or the volumetric source (l = 0 only).
 // ---------------------------------------------------------------------------
+template <typename R>
 struct SrcParams {
     CellParams c;
     const double* src;     // [B][8]
     const double* unc;     // [B][G][V]
     const double* q;       // [B][G][V] or null
-    double* F;
+    R* F;
     size_t Fstride;
     int V;
 };
 
-__global__ void k_fixed_source(const SrcParams p, int gt, int slot)
+template <typename R>
+__global__ void k_fixed_source(const SrcParams<R> p, int gt, int slot)
 {
     const int ct = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     const CellParams& c = p.c;
     if (ct >= c.NC) return;
     const int tile = ct / c.TV, cc = ct - tile * c.TV;
-    double* F = p.F + (size_t)slot * p.Fstride + ((size_t)b * c.NT + tile) * (size_t)(c.K * c.TV) + cc;
+    R* F = p.F + (size_t)slot * p.Fstride + ((size_t)b * c.NT + tile) * (size_t)(c.K * c.TV) + cc;
     const int m = c.mat_t[ct];
     const int kind = (int)p.src[(size_t)b * 8];
     if (m < 0 || kind < 0) {
-        for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = 0.0;
+        for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = R(0);
         return;
     }
     double C[3];
     const int v = tiled_to_natural(c, ct, C);
     if (kind == 0) {
-        F[0] = p.q[((size_t)b * c.G + gt) * p.V + v];
-        for (int k = 1; k < c.K; ++k) F[(size_t)k * c.TV] = 0.0;
+        F[0] = (R)p.q[((size_t)b * c.G + gt) * p.V + v];
+        for (int k = 1; k < c.K; ++k) F[(size_t)k * c.TV] = R(0);
         return;
     }
     const double* s = p.src + (size_t)b * 8;
@@ -603,25 +838,29 @@ __global__ void k_fixed_source(const SrcParams p, int gt, int slot)
         for (int l = 0; l <= c.L; ++l)
             acc[l] += c.sigma_s[(((size_t)m * (c.L + 1) + l) * c.G + gp) * c.G + gt] * ss * phu;
     }
-    for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = acc[l_of_k(k)] * Y[k];
+    for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = (R)(acc[l_of_k(k)] * Y[k]);
 }
 
 // ---------------------------------------------------------------------------
 // A2 / A7 at the end of group g: downscatter of the converged moments into
 // the fixed sources of groups g+1 .. g+W, and the outputs.
 // ---------------------------------------------------------------------------
+template <typename R>
 struct PushParams {
     CellParams c;
-    const double* phi;
-    double* F;
+    const R* part;         // octant partials of the group's last sweep
+    R* F;
     size_t Fstride;
     int W, V;
     double* col;           // [B][G][V]
     double* mom;           // [B][G][K][V] or null
-    const int* has_src;    // [B]
 };
 
-__global__ void k_push(const PushParams p, int g)
+// the converged moments are the octant sums of the last sweep's partials
+// (scalar flux in FP64, higher moments in the sweep precision, as the
+// reduction formed them)
+template <typename R>
+__global__ void k_push(const PushParams<R> p, int g)
 {
     const int ct = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
@@ -631,19 +870,31 @@ __global__ void k_push(const PushParams p, int g)
     if (m < 0) return;
     const int tile = ct / c.TV, cc = ct - tile * c.TV;
     const size_t base = ((size_t)b * c.NT + tile) * (size_t)(c.K * c.TV) + cc;
+    const size_t ostride = (size_t)c.B * c.NT * c.K * c.TV;
     const int v = tiled_to_natural(c, ct, nullptr);
     const double ss = c.scale_s_t ? c.scale_s_t[ct] : 1.0;
     const int W1 = p.W + 1;
     const int gmax = min(c.G - 1, g + p.W);
     for (int k = 0; k < c.K; ++k) {
-        const double ph = p.phi[base + (size_t)k * c.TV];
+        const R* pp = p.part + base + (size_t)k * c.TV;
+        double ph;
+        if (k == 0) {
+            ph = 0.0;
+            for (int o = 0; o < 8; ++o) ph += (double)pp[o * ostride];
+        } else {
+            R s = R(0);
+            for (int o = 0; o < 8; ++o) s += pp[o * ostride];
+            ph = (double)s;
+        }
         const int l = l_of_k(k);
         if (k == 0) p.col[((size_t)b * c.G + g) * p.V + v] = ph;
         if (p.mom) p.mom[(((size_t)b * c.G + g) * c.K + k) * p.V + v] = ph;
         for (int g2 = g + 1; g2 <= gmax; ++g2) {
             const double sgm = c.sigma_s[(((size_t)m * (c.L + 1) + l) * c.G + g) * c.G + g2];
-            if (sgm != 0.0)
-                p.F[(size_t)(g2 % W1) * p.Fstride + base + (size_t)k * c.TV] += sgm * ss * ph;
+            if (sgm != 0.0) {
+                R* f = p.F + (size_t)(g2 % W1) * p.Fstride + base + (size_t)k * c.TV;
+                *f = (R)((double)*f + sgm * ss * ph);
+            }
         }
     }
 }

@@ -51,6 +51,7 @@ struct dts_problem {
     int V = 0, G = 0, L = 0, K = 0, nd = 0, ndo = 0, B = 0;
     int TX = 0, TY = 0, TZ = 0, TV = 0, NTx = 0, NTy = 0, NTz = 0, NT = 0, NC = 0;
     int n_stages = 0, nsub = 0, n_mat = 0, W = 0, nblk = 0;
+    int line_warps = 2;               // warps per CTA of the line sweep kernel
     bool fp64 = true;
     size_t rsz = 8;                   // sizeof(R)
     std::vector<int> stage_off_h;     // [n_stages+1]
@@ -65,11 +66,13 @@ struct dts_problem {
     double *sigma_t = nullptr, *sigma_s = nullptr;
     int *mat_t = nullptr, *mat_nat = nullptr;
     double *scale_t_t = nullptr, *scale_s_t = nullptr, *scale_t_nat = nullptr;
-    double *F = nullptr, *phi = nullptr, *sigt64 = nullptr, *sigs = nullptr;
+    void* F = nullptr;                // fixed-source ring, sweep precision
+    double *phi00 = nullptr, *sigt64 = nullptr, *sigs0 = nullptr;
+    void* sigs = nullptr;             // [L+1][NC] in-group scatter, sweep precision
     void *T = nullptr, *part = nullptr, *xf = nullptr, *yf = nullptr, *zf = nullptr, *sigt_r = nullptr;
     double *unc = nullptr, *col = nullptr, *mom = nullptr, *q = nullptr, *tmp = nullptr;
     double *src = nullptr, *spec = nullptr, *leak = nullptr, *blk = nullptr, *status = nullptr;
-    int *active = nullptr, *ctl = nullptr, *has_src = nullptr;
+    int *active = nullptr, *ctl = nullptr;
     size_t Fstride = 0;
     int F_W = -1;
     // host state
@@ -272,7 +275,7 @@ SweepFn<R> sweep_fn_k(int K)
 }
 
 template <typename R>
-SweepFn<R> sweep_fn(int ndo, int K)
+SweepFn<R> sweep_fn_generic(int ndo, int K)
 {
     switch (ndo) {
     case 1: return sweep_fn_k<R, 1>(K);
@@ -281,6 +284,45 @@ SweepFn<R> sweep_fn(int ndo, int K)
     case 10: return sweep_fn_k<R, 10>(K);
     }
     return nullptr;
+}
+
+template <typename R, int NDO, int TY, int TZ>
+SweepFn<R> lines_fn_k(int K)
+{
+    switch (K) {
+    case 1: return k_sweep_lines<R, NDO, 1, TY, TZ>;
+    case 4: return k_sweep_lines<R, NDO, 4, TY, TZ>;
+    case 9: return k_sweep_lines<R, NDO, 9, TY, TZ>;
+    case 16: return k_sweep_lines<R, NDO, 16, TY, TZ>;
+    }
+    return nullptr;
+}
+
+template <typename R, int TY, int TZ>
+SweepFn<R> lines_fn(int ndo, int K)
+{
+    switch (ndo) {
+    case 1: return lines_fn_k<R, 1, TY, TZ>(K);
+    case 3: return lines_fn_k<R, 3, TY, TZ>(K);
+    case 6: return lines_fn_k<R, 6, TY, TZ>(K);
+    case 10: return lines_fn_k<R, 10, TY, TZ>(K);
+    }
+    return nullptr;
+}
+
+// tiles of exactly 32 x-lines (4 x 8 or 8 x 4) take the warp-synchronous
+// kernel; every other tile shape the generic sub-sweep kernel
+bool line_tile(const dts_problem* p)
+{
+    return (p->TY == 4 && p->TZ == 8) || (p->TY == 8 && p->TZ == 4);
+}
+
+template <typename R>
+SweepFn<R> sweep_fn(const dts_problem* p)
+{
+    if (line_tile(p))
+        return p->TY == 4 ? lines_fn<R, 4, 8>(p->ndo, p->K) : lines_fn<R, 8, 4>(p->ndo, p->K);
+    return sweep_fn_generic<R>(p->ndo, p->K);
 }
 
 template <typename R>
@@ -297,11 +339,21 @@ RedFn<R> reduce_fn(int K)
 
 size_t sweep_smem(const dts_problem* p)
 {
+    const int xfaces = line_tile(p) ? 32 : p->TY * p->TZ;
     const size_t n = (size_t)p->ndo * p->TV +
-                     (size_t)p->ndo * (p->TY * p->TZ + p->TX * p->TZ + p->TX * p->TY) + p->TV +
+                     (size_t)p->ndo * (xfaces + p->TX * p->TZ + p->TX * p->TY) + p->TV +
                      2 * p->ndo * p->K + 4 * p->ndo;
     size_t bytes = (n * p->rsz + 15) & ~size_t(15);
     return bytes + sizeof(double) * (3 * p->ndo + 32);
+}
+
+// threads per sweep CTA: the generic kernel uses 256; the line kernel one
+// warp per run of directions (2 warps unless the octant has fewer directions)
+int sweep_threads(const dts_problem* p)
+{
+    if (!line_tile(p)) return kSweepThreads;
+    const int nw = std::max(1, std::min(p->line_warps, p->ndo));
+    return 32 * nw;
 }
 
 CellParams cell_params(const dts_problem* p)
@@ -331,13 +383,14 @@ dts_status record_sweep(dts_problem* p)
     sp.T = (const R*)p->T; sp.sigt = (const R*)p->sigt_r; sp.part = (R*)p->part;
     sp.xf = (R*)p->xf; sp.yf = (R*)p->yf; sp.zf = (R*)p->zf;
     sp.active = p->active; sp.leak = p->leak;
-    SweepFn<R> sf = sweep_fn<R>(p->ndo, p->K);
+    SweepFn<R> sf = sweep_fn<R>(p);
     if (!sf) return fail(p, DTS_ERR_INTERNAL, "no sweep kernel for this (S_N, P_L)");
     const size_t smem = sweep_smem(p);
+    const int nthr = sweep_threads(p);
     for (int s = 0; s < p->n_stages; ++s) {
         const int cnt = p->stage_off_h[s + 1] - p->stage_off_h[s];
         const unsigned grid = (unsigned)cnt * 8u * (unsigned)p->B;
-        sf<<<grid, kSweepThreads, smem, p->stream>>>(sp, s);
+        sf<<<grid, nthr, smem, p->stream>>>(sp, s);
     }
     return DTS_OK;
 }
@@ -347,8 +400,9 @@ dts_status record_reduce(dts_problem* p)
 {
     RedParams<R> rp;
     rp.B = p->B; rp.NT = p->NT; rp.TV = p->TV; rp.NC = p->NC;
-    rp.part = (const R*)p->part; rp.phi = p->phi; rp.T = (R*)p->T; rp.F = p->F;
-    rp.Fstride = p->Fstride; rp.ctl = p->ctl; rp.sigs = p->sigs; rp.sigt64 = p->sigt64;
+    rp.part = (const R*)p->part; rp.phi00 = p->phi00; rp.T = (R*)p->T; rp.F = (const R*)p->F;
+    rp.Fstride = p->Fstride; rp.ctl = p->ctl; rp.sigs = (const R*)p->sigs; rp.sigs0 = p->sigs0;
+    rp.sigt64 = p->sigt64;
     rp.mat_t = p->mat_t; rp.active = p->active; rp.vol = p->d.dx * p->d.dy * p->d.dz;
     rp.blk = p->blk;
     RedFn<R> rf = reduce_fn<R>(p->K);
@@ -386,9 +440,9 @@ dts_status build_graph(dts_problem* p)
     // kernels with more than 48 KB of dynamic shared memory need the opt-in
     const size_t smem = sweep_smem(p);
     cudaError_t e;
-    if (p->fp64) e = cudaFuncSetAttribute(sweep_fn<double>(p->ndo, p->K),
+    if (p->fp64) e = cudaFuncSetAttribute(sweep_fn<double>(p),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else e = cudaFuncSetAttribute(sweep_fn<float>(p->ndo, p->K),
+    else e = cudaFuncSetAttribute(sweep_fn<float>(p),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("sweep smem attribute: ") + cudaGetErrorString(e));
     TRY(capture(p, p->fp64 ? record_sweep<double> : record_sweep<float>, &p->graph));
@@ -411,7 +465,7 @@ dts_status ensure_ring(dts_problem* p)
     dfree(p, p->F);
     p->F = nullptr;
     p->Fstride = (size_t)p->B * p->NC * p->K;
-    TRY(dalloc_t(p, &p->F, p->Fstride * (p->W + 1)));
+    TRY(dalloc(p, &p->F, p->Fstride * (p->W + 1) * p->rsz));
     p->F_W = p->W;
     return DTS_OK;
 }
@@ -420,15 +474,36 @@ template <typename R>
 void launch_group_xs(dts_problem* p, int g)
 {
     const int nb = (p->NC + 255) / 256;
-    k_group_xs<R><<<nb, 256, 0, p->stream>>>(cell_params(p), g, (R*)p->sigt_r, p->sigt64, p->sigs);
+    k_group_xs<R><<<nb, 256, 0, p->stream>>>(cell_params(p), g, (R*)p->sigt_r, p->sigt64, (R*)p->sigs,
+                                             p->sigs0);
 }
 
 template <typename R>
 void launch_group_init(dts_problem* p, int slot)
 {
-    const int total = p->B * p->NC * p->K;
-    k_group_init<R><<<(total + 255) / 256, 256, 0, p->stream>>>(total, p->F + (size_t)slot * p->Fstride,
-                                                                 p->phi, (R*)p->T);
+    const size_t total = (size_t)p->B * p->NC * p->K;
+    k_group_init<R><<<(unsigned)((total + 255) / 256), 256, 0, p->stream>>>(
+        total, (const R*)p->F + (size_t)slot * p->Fstride, (R*)p->T);
+}
+
+template <typename R>
+void launch_fixed_source(dts_problem* p, int gt, int slot)
+{
+    SrcParams<R> sp;
+    sp.c = cell_params(p);
+    sp.src = p->src; sp.unc = p->unc; sp.q = p->q; sp.F = (R*)p->F; sp.Fstride = p->Fstride;
+    sp.V = p->V;
+    k_fixed_source<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(sp, gt, slot);
+}
+
+template <typename R>
+void launch_push(dts_problem* p, int g)
+{
+    PushParams<R> pp;
+    pp.c = cell_params(p);
+    pp.part = (const R*)p->part; pp.F = (R*)p->F; pp.Fstride = p->Fstride; pp.W = p->W; pp.V = p->V;
+    pp.col = p->col; pp.mom = p->d.keep_moments ? p->mom : nullptr;
+    k_push<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g);
 }
 
 dts_status run_solve(dts_problem* p, dts_solve_stats* st)
@@ -450,16 +525,10 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
             k_raytrace<<<dim3((p->V + 127) / 128, B), 128, 0, p->stream>>>(rp, g0);
         CK(cudaGetLastError());
     }
-    SrcParams sp;
-    sp.c = cell_params(p);
-    sp.src = p->src; sp.unc = p->unc; sp.q = p->q; sp.F = p->F; sp.Fstride = p->Fstride; sp.V = p->V;
-    const dim3 cgrid((p->NC + 255) / 256, B);
-    for (int g = 0; g < std::min(G, W1); ++g)
-        k_fixed_source<<<cgrid, 256, 0, p->stream>>>(sp, g, g % W1);
-    PushParams pp;
-    pp.c = cell_params(p);
-    pp.phi = p->phi; pp.F = p->F; pp.Fstride = p->Fstride; pp.W = p->W; pp.V = p->V;
-    pp.col = p->col; pp.mom = p->d.keep_moments ? p->mom : nullptr; pp.has_src = p->has_src;
+    for (int g = 0; g < std::min(G, W1); ++g) {
+        if (p->fp64) launch_fixed_source<double>(p, g, g % W1);
+        else launch_fixed_source<float>(p, g, g % W1);
+    }
 
     int64_t updates = 0, sweeps = 0;
     int64_t launches = (G + kRayGroups - 1) / kRayGroups + std::min(G, W1);
@@ -477,6 +546,7 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
             launch_group_xs<float>(p, g);
             launch_group_init<float>(p, slot);
         }
+        CK(cudaMemsetAsync(p->phi00, 0, sizeof(double) * B * p->NC, p->stream));
         for (int b = 0; b < B; ++b) {
             p->h_active[b] = 1;
             p->iters[(size_t)b * G + g] = 0;
@@ -537,10 +607,12 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
             max_res = std::max(max_res, p->resid[bg]);
             if (p->d.tol > 0.0 && !(p->resid[bg] < p->d.tol)) all_conv = false;
         }
-        k_push<<<cgrid, 256, 0, p->stream>>>(pp, g);
+        if (p->fp64) launch_push<double>(p, g);
+        else launch_push<float>(p, g);
         launches += 4;   // set_ctl, group_xs, group_init, push
         if (g + W1 < G) {
-            k_fixed_source<<<cgrid, 256, 0, p->stream>>>(sp, g + W1, slot);
+            if (p->fp64) launch_fixed_source<double>(p, g + W1, slot);
+            else launch_fixed_source<float>(p, g + W1, slot);
             ++launches;
         }
         CK(cudaGetLastError());
@@ -576,11 +648,12 @@ void choose_tile(dts_problem* p)
         p->TV = p->TX * p->TY * p->TZ;
         return;
     }
-    // default: 8^3 tiles (clipped to the grid), which keeps the FP64 S8 P3
-    // working set of a CTA near 64 KB of shared memory
-    p->TX = std::min(8, p->d.nx);
-    p->TY = std::min(8, p->d.ny);
-    p->TZ = std::min(8, p->d.nz);
+    // default: 32 x-lines (4 in y, 8 in z) per tile for the warp-synchronous
+    // kernel, 8 cells long in x (measured fastest of 4..32 on the 96^3 S8 P3
+    // batch)
+    p->TX = 8;
+    p->TY = 4;
+    p->TZ = 8;
     p->TV = p->TX * p->TY * p->TZ;
 }
 
@@ -682,9 +755,9 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     if (!(d.tol >= 0.0) || !isfin(d.tol)) return fail(p, DTS_ERR_INVALID_ARG, "tol must be finite and >= 0");
     if (d.max_iters < 1) return fail(p, DTS_ERR_INVALID_ARG, "max_iters must be >= 1");
     const bool tile_given = d.tile_x || d.tile_y || d.tile_z;
-    if (tile_given && (d.tile_x < 1 || d.tile_y < 1 || d.tile_z < 1 || d.tile_x > 16 ||
-                       d.tile_y > 16 || d.tile_z > 16))
-        return fail(p, DTS_ERR_INVALID_ARG, "tile extents must all be 0 or all in 1..16");
+    if (tile_given && (d.tile_x < 1 || d.tile_y < 1 || d.tile_z < 1 || d.tile_x > 64 ||
+                       d.tile_y > 64 || d.tile_z > 64))
+        return fail(p, DTS_ERR_INVALID_ARG, "tile extents must all be 0 or all in 1..64");
     if (!ls_set(d.sn_order, p->mu, p->eta, p->xi, p->w))
         return fail(p, DTS_ERR_INVALID_ARG, "sn_order must be 2, 4, 6 or 8");
     p->V = d.nx * d.ny * d.nz;
@@ -725,7 +798,7 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     const size_t B = p->B, NC = p->NC, K = p->K, G = p->G, V = p->V;
     TRY(dalloc_t(p, &p->mat_t, NC));
     TRY(dalloc_t(p, &p->mat_nat, V));
-    TRY(dalloc_t(p, &p->phi, B * NC * K));
+    TRY(dalloc_t(p, &p->phi00, B * NC));
     TRY(dalloc(p, &p->T, B * NC * K * p->rsz));
     TRY(dalloc(p, &p->part, 8 * B * NC * K * p->rsz));
     const size_t nf = (size_t)p->ndo;
@@ -734,7 +807,8 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     TRY(dalloc(p, &p->zf, 8 * B * (size_t)p->NTx * p->NTy * nf * p->TX * p->TY * p->rsz));
     TRY(dalloc(p, &p->sigt_r, NC * p->rsz));
     TRY(dalloc_t(p, &p->sigt64, NC));
-    TRY(dalloc_t(p, &p->sigs, NC * (p->L + 1)));
+    TRY(dalloc(p, &p->sigs, NC * (p->L + 1) * p->rsz));
+    TRY(dalloc_t(p, &p->sigs0, NC));
     TRY(dalloc_t(p, &p->unc, B * G * V));
     TRY(dalloc_t(p, &p->col, B * G * V));
     TRY(dalloc_t(p, &p->tmp, G * V));
@@ -746,7 +820,6 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     TRY(dalloc_t(p, &p->blk, B * p->nblk * 4));
     TRY(dalloc_t(p, &p->status, B * 4));
     TRY(dalloc_t(p, &p->active, B));
-    TRY(dalloc_t(p, &p->has_src, B));
     TRY(dalloc_t(p, &p->ctl, 4));
     CK(cudaMemset(p->leak, 0, sizeof(double) * B));
     CK(cudaMemset(p->col, 0, sizeof(double) * B * G * V));
@@ -947,8 +1020,6 @@ dts_status dts_solve(dts_problem* p, dts_solve_stats* stats)
     for (int b = 0; b < p->B; ++b)
         if (!p->src_set[b]) return fail(p, DTS_ERR_STATE, "a batch member has no source");
     DevGuard guard(p->d.device);
-    std::vector<int> hs(p->B, 1);
-    CK(cudaMemcpy(p->has_src, hs.data(), sizeof(int) * p->B, cudaMemcpyHostToDevice));
     return run_solve(p, stats);
 }
 

@@ -46,6 +46,13 @@ CASES = [
     ((7, 12, 5), 6, 2, 2, (3, 5, 2), 1),
     ((9, 9, 9), 2, 0, 2, (1, 1, 1), 1),
     ((17, 6, 11), 8, 1, 2, (8, 4, 8), 3),
+    # warp-synchronous line kernel (32 x-lines per tile): both line layouts,
+    # odd and long x extents, ragged tails in every axis
+    ((13, 11, 9), 8, 3, 3, (8, 4, 8), 2),
+    ((10, 9, 17), 6, 2, 2, (5, 8, 4), 1),
+    ((21, 7, 6), 4, 1, 2, (16, 4, 8), 1),
+    ((6, 5, 9), 2, 0, 2, (3, 4, 8), 1),
+    ((40, 12, 10), 8, 3, 2, (32, 8, 4), 1),
 ]
 
 
