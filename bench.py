@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--sources", type=int, default=32)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--max-iters", type=int, default=None)
-    ap.add_argument("--tile", default="0,0,0")
+    ap.add_argument("--tile", default="auto", help="tx,ty,tz or 'auto' (dts_tune_tile)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -177,6 +177,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def sweep_kernel_name(tile, fp32):
+    """The sweep kernel the library launches for a tile shape."""
+    if fp32 and tuple(tile) == (8, 4, 4):
+        return "k_sweep_batch"
+    if tile[1] * tile[2] == 32 and tile[1] in (4, 8):
+        return "k_sweep_lines"
+    return "k_sweep_stage"
+
+
+def aggregate(ms: float, updates: float, world: int, device=None):
+    """Whole-job numbers over ranks: the slowest rank's time and the sum of
+    every rank's updates (weak scaling: each rank solves its own batch)."""
+    if world <= 1:
+        return ms, float(updates)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -192,6 +215,10 @@ def run_ours(args):
     fp32 = args.workload != "hetero64"
     prec = dts.PREC_FP32 if fp32 else dts.PREC_FP64
     tol = args.tol if args.tol is not None else w.tol
+    tuned = None
+    if args.tile == "auto":
+        tile, tuned = dts.tune_tile(w, precision=prec, device=local)
+        args.tile = ",".join(str(x) for x in tile)
     tile = tuple(int(x) for x in args.tile.split(","))
     p = dts.problem_from_workload(w, precision=prec, tol=tol, max_iters=args.max_iters or 1000,
                                   tile=tile, device=local, stream=stream.cuda_stream)
@@ -221,12 +248,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     updates = sum(s["updates"] for s in stats)
-    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tm = t.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms, updates = float(tm[0]), float(t[1])
+    ms, updates = aggregate(ms, updates, world, dev)
     value = updates / (ms / 1e3)
 
     # roofline of the dominant kernel (the wavefront sweep), timed live by
@@ -239,7 +261,7 @@ def run_ours(args):
     achieved = (sum(s["updates"] for s in stats) * bpu / 1e9) / (sweep_ms / 1e3)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "k_sweep_stage", "peak_source": which,
+                "kernel": sweep_kernel_name(tile, fp32), "peak_source": which,
                 "sweep_share_of_step": sweep_ms / ms if ms else None,
                 "bytes_per_update": bpu}
 
@@ -266,6 +288,7 @@ def run_ours(args):
                        "sources_per_gpu": w.batch, "tol": tol,
                        "precision": "fp32 sweep/contraction, fp64 accumulation" if fp32 else "fp64",
                        "tile": [stats[0]["tile_x"], stats[0]["tile_y"], stats[0]["tile_z"]],
+                       "tile_choice": "dts_tune_tile" if tuned else "given",
                        "parallelism": f"weak x{world}, independent source batches",
                        "l2": "inputs larger than L2 (device state of tens of GB per step)"},
             "roofline": roofline,
@@ -293,7 +316,8 @@ def fp64_plain(w, p32, dts, dev, stream, tol):
     scalar fluence over all groups)."""
     import torch
     from paper_1910_11335_b300 import inputs  # noqa: F401
-    q = dts.problem_from_workload(w, precision=dts.PREC_FP64, tol=tol, max_iters=1000,
+    tile, _ = dts.tune_tile(w, precision=dts.PREC_FP64, batch=1, device=dev)
+    q = dts.problem_from_workload(w, precision=dts.PREC_FP64, tol=tol, max_iters=1000, tile=tile,
                                   device=dev, stream=stream.cuda_stream, sources=[0])
     q.solve(allow_not_converged=True)
     torch.cuda.synchronize(dev)
@@ -312,6 +336,7 @@ def fp64_plain(w, p32, dts, dev, stream, tol):
     v = st.updates / (ms / 1e3)
     q.close()
     return {"fp64_plain": {"value": v, "unit": UNIT, "sources": 1, "converged": st.converged,
+                           "tile": list(tile),
                            "sweeps": st.sweeps, "ms": ms,
                            "sweep_achieved_gbs": st.updates * sweep_bytes_per_update(K, ndo, 8) / 1e9
                            / (st.sweep_ms / 1e3)},

@@ -173,6 +173,28 @@ dts_status dts_get_scalar_fluence(dts_problem *p, int batch_index, dts_component
 dts_status dts_get_moments(dts_problem *p, int batch_index, int group, double *out,
                            size_t out_len, int out_is_device);
 
+/*
+ * Discrete adjoint of the converged solve of batch member batch_index
+ * (differentiation form; the paper has no adjoint -- it is the gradient of the
+ * Eq. 2-7 solution). Given dL/dphi_total [G][V] (the gradient of a scalar loss
+ * with respect to the total scalar fluence of every group and voxel), writes
+ *   dL_dscale_t [V]  dL/d(multiplier of sigma_t in voxel v), all groups
+ *   dL_dscale_s [V]  dL/d(multiplier of every sigma_s entry in voxel v)
+ *   dL_dsigma_t [G][V] dL/dsigma_t^g(v) of the collided part (NULL = skip)
+ * Groups run from low energy to high; each recomputes its forward sweep from
+ * the kept moments (recording fluxes and fixup sets, which stay fixed), then
+ * iterates the transposed source iteration to tol / max_iters; the uncollided
+ * part is differentiated through the ray trace. Needs DTS_PREC_FP64,
+ * keep_moments = 1 and a completed dts_solve (else DTS_ERR_STATE).
+ * ptrs_are_device selects device (1) or host (0) memory for all four arrays.
+ */
+dts_status dts_solve_adjoint(dts_problem *p, int batch_index, const double *dL_dphi,
+                             double *dL_dscale_t, double *dL_dscale_s, double *dL_dsigma_t,
+                             int ptrs_are_device);
+
+/* Adjoint source iterations per group [G] of the last dts_solve_adjoint. */
+dts_status dts_get_adjoint_iterations(dts_problem *p, int32_t *out, size_t out_len);
+
 /* Per (source, group) results of the last solve, host arrays:
  *   iterations [B][G]; residuals [B][G] (final relative L2 change);
  *   balance [B][G][3] = (sum_v V T_00, sum_v V sigma_t phi_00, leakage) of the
@@ -207,6 +229,20 @@ int dts_version(void);
  */
 dts_status dts_quadrature(int sn_order, double *mu, double *eta, double *xi, double *w,
                           int *n_dirs);
+
+/*
+ * Wavefront tile chosen by measurement (the batching pattern's autotuner; the
+ * paper sweeps one sub-sweep of Eqs. 8-22 per launch and has no tiles). For
+ * the shape in *desc (grid, S_N order, Legendre order, precision, device, up
+ * to 16 sources) each candidate tile that fits -- 8x4x4 (FP32 batched
+ * kernel), 8x4x8, 4x4x8, 16x4x8, 8x8x4, 8x8x8, 4x4x4 -- times two source
+ * iterations of a probe problem (one group, homogeneous scatterer, unit
+ * volumetric source) and the fastest sweep in updates per second wins. Writes
+ * desc->tile_x/y/z; *best_updates_per_s (may be NULL) gets the probe rate.
+ * Results are cached per process. Runs on the device; allocates and frees
+ * probe problems. Errors: DTS_ERR_INVALID_ARG, DTS_ERR_CUDA.
+ */
+dts_status dts_tune_tile(dts_problem_desc *desc, double *best_updates_per_s);
 dts_status dts_moment_tables(int sn_order, int legendre_order, double *D, double *M);
 long long dts_subsweep_size(int nx, int ny, int nz, int S);
 

@@ -430,47 +430,81 @@ k_sweep_lines(const SweepParams<R> p, const int stage)
         const int sy = negy ? TY - 1 - ly : ly, sz = negz ? TZ - 1 - lz : lz;
         const int line = sz * TY + sy;
         const bool line_ok = (ty * TY + sy) < p.ny && (tz * TZ + sz) < p.nz;
-        const int nvx = p.nx - tx * TX;             // valid cells along x in this tile
+        const int nvx = line_ok ? p.nx - tx * TX : 0;   // valid cells along x in this line
         const int total = (d1 - d0) * TX, ls = ly + lz;
-        int j = 0, lx = 0, d = d0;
-        R ax = R(0), ay = R(0), az = R(0), xin = R(0), ycur = R(0), zcur = R(0), ysh = R(0), zsh = R(0);
+        const int xflip = negx ? TX - 1 : 0;           // storage x = xflip ^ lx when TX is 2^n
+        int lx = 0, d = d0;
+        R ax = As[d0 * 4], ay = As[d0 * 4 + 1], az = As[d0 * 4 + 2];
+        R asum = ax + ay + az;
+        R* qd = Qs + d0 * TV + line * TX;
+        const R* sgl = sg + line * TX;
+        R* yd = fy + d0 * fyn + sz * TX;
+        R* zd = fz + d0 * fzn + sy * TX;
+        R xin = fx[d0 * fxn + line], ycur = R(0), zcur = R(0), ysh = R(0), zsh = R(0);
+        const bool ytop = ly == TY - 1, ztop = lz == TZ - 1;
         const int nsteps = total + TY + TZ - 2;
         for (int t = 0; t < nsteps; ++t) {
             const int u = t - ls;
-            if (u >= 0 && u < total) {
-                if (lx == 0) {
-                    d = d0 + j;
-                    ax = As[d * 4];
-                    ay = As[d * 4 + 1];
-                    az = As[d * 4 + 2];
-                    xin = fx[d * fxn + line];
-                }
-                const int sx = negx ? TX - 1 - lx : lx;
-                const int c = line * TX + sx;
-                R* pq = Qs + d * TV + c;
-                R* py = fy + d * fyn + sz * TX + sx;
-                R* pz = fz + d * fzn + sy * TX + sx;
-                const R yin = ly ? ysh : *py;
-                const R zin = lz ? zsh : *pz;
-                R ox, oy, oz, psi;
-                if (line_ok && sx < nvx) {
-                    psi = dd_cell_line<R>(*pq, sg[c], ax, ay, az, xin, yin, zin, ox, oy, oz);
+            const bool act = (unsigned)u < (unsigned)total;
+            bool neg = false;
+            R ox = R(0), oy = R(0), oz = R(0), psi = R(0), q = R(0), sig = R(0), yin = R(0), zin = R(0);
+            int sx = 0;
+            if (act) {
+                sx = (TX & (TX - 1)) == 0 ? (xflip ^ lx) : (negx ? TX - 1 - lx : lx);
+                yin = ly ? ysh : yd[sx];
+                zin = lz ? zsh : zd[sx];
+                if (sx < nvx) {
+                    q = qd[sx];
+                    sig = sgl[sx];
+                    psi = fast_div<R>(q + ax * xin + ay * yin + az * zin, sig + asum);
+                    ox = R(2) * psi - xin;
+                    oy = R(2) * psi - yin;
+                    oz = R(2) * psi - zin;
+                    neg = ox < R(0) || oy < R(0) || oz < R(0);
                 } else {
-                    psi = R(0);
                     ox = xin;
                     oy = yin;
                     oz = zin;
                 }
-                *pq = psi;
-                if (ly == TY - 1) *py = oy;
-                if (lz == TZ - 1) *pz = oz;
+            }
+            if (__any_sync(0xffffffffu, neg) && neg) {
+                bool fxd = false, fyd = false, fzd = false;
+#pragma unroll 1
+                for (int pass = 0; pass < 3; ++pass) {
+                    const bool nx = !fxd && ox < R(0), ny = !fyd && oy < R(0), nz = !fzd && oz < R(0);
+                    if (!(nx || ny || nz)) break;
+                    fxd |= nx;
+                    fyd |= ny;
+                    fzd |= nz;
+                    const R num = q + (fxd ? R(0.5) * ax : ax) * xin + (fyd ? R(0.5) * ay : ay) * yin +
+                                  (fzd ? R(0.5) * az : az) * zin;
+                    const R den = sig + (fxd ? R(0) : ax) + (fyd ? R(0) : ay) + (fzd ? R(0) : az);
+                    psi = fast_div<R>(num, den);
+                    ox = fxd ? R(0) : R(2) * psi - xin;
+                    oy = fyd ? R(0) : R(2) * psi - yin;
+                    oz = fzd ? R(0) : R(2) * psi - zin;
+                }
+            }
+            if (act) {
+                qd[sx] = psi;
+                if (ytop) yd[sx] = oy;
+                if (ztop) zd[sx] = oz;
                 xin = ox;
                 ycur = oy;
                 zcur = oz;
-                if (++lx == TX) {
+                if (++lx == TX) {   // this line of direction d is done: next direction
                     fx[d * fxn + line] = ox;
                     lx = 0;
-                    ++j;
+                    if (++d < d1) {
+                        ax = As[d * 4];
+                        ay = As[d * 4 + 1];
+                        az = As[d * 4 + 2];
+                        asum = ax + ay + az;
+                        qd += TV;
+                        yd += fyn;
+                        zd += fzn;
+                        xin = fx[d * fxn + line];
+                    }
                 }
             }
             ysh = __shfl_up_sync(0xffffffffu, ycur, 1);
@@ -515,6 +549,252 @@ k_sweep_lines(const SweepParams<R> p, const int stage)
     if (lbx || lby || lbz) {
         leak = block_sum(leak, red);
         if (tid == 0 && leak != 0.0) atomicAdd(&p.leak[b], leak);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A3 + A4, batched form (FP32): one warp per (tile, octant, group of sources).
+// Lane = (source, direction) pair, e.g. 3 sources x 10 directions for S8, so
+// all lanes solve the same cell at the same time: the warp walks the tile in
+// upwind order (the sub-sweeps of Sec. II.B reduce to a lexicographic walk
+// inside one warp), the x-face stays in a register and the y/z faces sit in
+// per-lane shared-memory columns updated in place. No skew, no shuffles, no
+// CTA barrier; shared-memory offsets are compile-time in the unrolled x walk.
+// Shared memory holds the tile in octant-local order, so the walk is the
+// same for every octant. Faces move between global and shared memory as
+// coalesced per-source blocks. Padding cells pass faces through.
+// ---------------------------------------------------------------------------
+constexpr int kQP = 33;   // padded lane row of the source/flux buffer
+
+template <int BX, int BY, int BZ>
+__host__ __device__ constexpr size_t sweep_batch_smem(int ndo, int K)
+{
+    // floats (+ 8 of slack for the 16-byte alignment of the doubles), then
+    // 3*ndo leakage weights and up to 32 per-source leakage sums
+    return sizeof(float) * ((size_t)BX * BY * BZ * kQP + 32 * (BY * BZ + BZ * BX + BY * BX) +
+                            BX * BY * BZ + 2 * ndo * K + 8) +
+           sizeof(double) * (3 * ndo + 32);
+}
+
+// global face block of one source: [NDO][F] in storage order; shared: [local slot][lane]
+template <int NDO, int F, int SB, typename Map>
+__device__ __forceinline__ void faces_in(float* sh, const float* g0, size_t gstride, int nb,
+                                         unsigned okmask, bool upstream, Map map)
+{
+    for (int j = threadIdx.x; j < nb * NDO * F; j += 32) {
+        const int il = j / (NDO * F), rem = j - il * (NDO * F), dd = rem / F, e = rem - dd * F;
+        const bool ok = upstream && (okmask >> il & 1u);
+        sh[map(e) * 32 + il * NDO + dd] = ok ? g0[(size_t)il * gstride + rem] : 0.f;
+    }
+}
+
+template <int NDO, int F, int SB, typename Map>
+__device__ __forceinline__ void faces_out(const float* sh, float* g0, size_t gstride, int nb,
+                                          unsigned okmask, bool leaving, const double* Lw, int axis,
+                                          double* leak_sh, Map map)
+{
+    for (int j = threadIdx.x; j < nb * NDO * F; j += 32) {
+        const int il = j / (NDO * F), rem = j - il * (NDO * F), dd = rem / F, e = rem - dd * F;
+        if (!(okmask >> il & 1u)) continue;
+        const float v = sh[map(e) * 32 + il * NDO + dd];
+        g0[(size_t)il * gstride + rem] = v;
+        if (leaving && v != 0.f) atomicAdd(&leak_sh[il], Lw[dd * 3 + axis] * (double)v);
+    }
+}
+
+template <int NDO, int K, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float> p, const int stage)
+{
+    constexpr int SB = 32 / NDO;       // sources per warp
+    constexpr int NL = SB * NDO;       // lanes in use
+    constexpr int BV = BX * BY * BZ;
+    constexpr int fxn = BY * BZ, fyn = BX * BZ, fzn = BX * BY;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* Qs = reinterpret_cast<float*>(smem);    // [BV][kQP] local cell order, lane column
+    float* fx = Qs + BV * kQP;                     // [BY*BZ][32] x-faces by local (y,z)
+    float* fy = fx + fxn * 32;                     // [BZ*BX][32] y-faces by local (z,x)
+    float* fz = fy + fyn * 32;                     // [BY*BX][32] z-faces by local (y,x)
+    float* sg = fz + fzn * 32;                     // [BV] local order
+    float* Ms = sg + BV;                           // [NDO][K]
+    float* Ds = Ms + NDO * K;                      // [K][NDO]
+    double* Lws = reinterpret_cast<double*>(smem + (((size_t)(Ds + NDO * K - Qs) * 4 + 15) & ~size_t(15)));
+    double* leak_sh = Lws + 3 * NDO;               // [SB]
+
+    const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
+    int bid = blockIdx.x;
+    const int tl = bid % cnt;
+    bid /= cnt;
+    const int oct = bid & 7, b0 = (bid >> 3) * SB;
+    const int lane = threadIdx.x;
+    const int nb = min(SB, p.B - b0);
+    unsigned okmask = 0;                           // sources of this warp still iterating
+    for (int i = 0; i < nb; ++i)
+        if (p.active[b0 + i]) okmask |= 1u << i;
+    if (okmask == 0) return;
+
+    const unsigned pk = p.stage_tiles[s0 + tl];
+    const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
+    const bool negx = oct & 1, negy = oct & 2, negz = oct & 4;
+    const int tx = negx ? p.NTx - 1 - ta : ta;
+    const int ty = negy ? p.NTy - 1 - tb : tb;
+    const int tz = negz ? p.NTz - 1 - tc : tc;
+    const int tile = (tz * p.NTy + ty) * p.NTx + tx;
+    const int n0 = oct * NDO;
+    const size_t BB = p.B;
+
+    for (int i = lane; i < NDO * K; i += 32) {
+        Ms[i] = p.M[n0 * K + i];
+        Ds[(i % K) * NDO + i / K] = p.Dt[n0 * K + i];
+    }
+    for (int i = lane; i < 3 * NDO; i += 32) Lws[i] = p.Lw[n0 * 3 + i];
+    if (lane < SB) leak_sh[lane] = 0.0;
+    const int bl = lane / NDO, d = lane - bl * NDO;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    if (lane < NL) {
+        ax = p.A[(n0 + d) * 3];
+        ay = p.A[(n0 + d) * 3 + 1];
+        az = p.A[(n0 + d) * 3 + 2];
+    }
+    const float asum = ax + ay + az;
+
+    // incoming faces (zero on the grid boundary), storage -> local order
+    const size_t sx_ = (size_t)(p.NTy * p.NTz) * NDO * fxn, sy_ = (size_t)(p.NTx * p.NTz) * NDO * fyn,
+                 sz_ = (size_t)(p.NTx * p.NTy) * NDO * fzn;
+    float* gx = p.xf + (((size_t)oct * BB + b0) * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * (size_t)(NDO * fxn);
+    float* gy = p.yf + (((size_t)oct * BB + b0) * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * (size_t)(NDO * fyn);
+    float* gz = p.zf + (((size_t)oct * BB + b0) * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * (size_t)(NDO * fzn);
+    auto mapx = [&](int e) {    // storage (sy, sz) -> local slot (ly, lz)
+        const int sy = e % BY, sz = e / BY;
+        return (negz ? BZ - 1 - sz : sz) * BY + (negy ? BY - 1 - sy : sy);
+    };
+    auto mapy = [&](int e) {    // storage (sx, sz) -> local (lx, lz)
+        const int sx = e % BX, sz = e / BX;
+        return (negz ? BZ - 1 - sz : sz) * BX + (negx ? BX - 1 - sx : sx);
+    };
+    auto mapz = [&](int e) {    // storage (sx, sy) -> local (lx, ly)
+        const int sx = e % BX, sy = e / BX;
+        return (negy ? BY - 1 - sy : sy) * BX + (negx ? BX - 1 - sx : sx);
+    };
+    faces_in<NDO, fxn, SB>(fx, gx, sx_, nb, okmask, ta > 0, mapx);
+    faces_in<NDO, fyn, SB>(fy, gy, sy_, nb, okmask, tb > 0, mapy);
+    faces_in<NDO, fzn, SB>(fz, gz, sz_, nb, okmask, tc > 0, mapz);
+
+    // phase A: items (source, cell); consecutive lanes read consecutive cells
+    const float* st = p.sigt + (size_t)tile * BV;
+#pragma unroll 1
+    for (int i = lane; i < SB * BV; i += 32) {
+        const int il = i / BV, cs = i - il * BV;
+        const int sxc = cs % BX, syc = (cs / BX) % BY, szc = cs / (BX * BY);
+        const int cl = ((negz ? BZ - 1 - szc : szc) * BY + (negy ? BY - 1 - syc : syc)) * BX +
+                       (negx ? BX - 1 - sxc : sxc);
+        if (il == 0) sg[cl] = st[cs];
+        if (!(okmask >> il & 1u)) continue;
+        const float* Tt = p.T + ((size_t)(b0 + il) * p.NT + tile) * (size_t)(K * BV) + cs;
+        float t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] = Tt[k * BV];
+        float* qrow = Qs + cl * kQP + il * NDO;
+#pragma unroll 1
+        for (int dd = 0; dd < NDO; ++dd) {
+            float q = 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) q = fmaf(Ms[dd * K + k], t[k], q);
+            qrow[dd] = q;
+        }
+    }
+    __syncwarp();
+
+    // phase B: the lexicographic walk, every lane on the same cell
+    const int nvx = p.nx - tx * BX, nvy = p.ny - ty * BY, nvz = p.nz - tz * BZ;
+    unsigned vx = 0;
+#pragma unroll
+    for (int lx = 0; lx < BX; ++lx)
+        if ((negx ? BX - 1 - lx : lx) < nvx) vx |= 1u << lx;
+#pragma unroll 1
+    for (int line = 0; line < BY * BZ; ++line) {
+        const int ly = line % BY, lz = line / BY;
+        const bool lok = (negy ? BY - 1 - ly : ly) < nvy && (negz ? BZ - 1 - lz : lz) < nvz;
+        const unsigned vm = lok ? vx : 0u;
+        float* qrow = Qs + line * BX * kQP + lane;
+        float* yrow = fy + lz * BX * 32 + lane;
+        float* zrow = fz + ly * BX * 32 + lane;
+        const float* srow = sg + line * BX;
+        float xin = fx[line * 32 + lane];
+#pragma unroll
+        for (int lx = 0; lx < BX; ++lx) {
+            const float yin = yrow[lx * 32], zin = zrow[lx * 32];
+            float psi, ox, oy, oz;
+            if (vm >> lx & 1u) {
+                const float q = qrow[lx * kQP], sig = srow[lx];
+                psi = __fdividef(q + ax * xin + ay * yin + az * zin, sig + asum);
+                ox = 2.f * psi - xin;
+                oy = 2.f * psi - yin;
+                oz = 2.f * psi - zin;
+                const bool neg = ox < 0.f || oy < 0.f || oz < 0.f;
+                if (__any_sync(0xffffffffu, neg) && neg) {
+                    bool fxd = false, fyd = false, fzd = false;
+#pragma unroll 1
+                    for (int pass = 0; pass < 3; ++pass) {
+                        const bool nx = !fxd && ox < 0.f, ny = !fyd && oy < 0.f, nz = !fzd && oz < 0.f;
+                        if (!(nx || ny || nz)) break;
+                        fxd |= nx;
+                        fyd |= ny;
+                        fzd |= nz;
+                        const float num = q + (fxd ? 0.5f * ax : ax) * xin + (fyd ? 0.5f * ay : ay) * yin +
+                                          (fzd ? 0.5f * az : az) * zin;
+                        const float den = sig + (fxd ? 0.f : ax) + (fyd ? 0.f : ay) + (fzd ? 0.f : az);
+                        psi = __fdividef(num, den);
+                        ox = fxd ? 0.f : 2.f * psi - xin;
+                        oy = fyd ? 0.f : 2.f * psi - yin;
+                        oz = fzd ? 0.f : 2.f * psi - zin;
+                    }
+                }
+            } else {
+                psi = 0.f;
+                ox = xin;
+                oy = yin;
+                oz = zin;
+            }
+            qrow[lx * kQP] = psi;
+            yrow[lx * 32] = oy;
+            zrow[lx * 32] = oz;
+            xin = ox;
+        }
+        fx[line * 32 + lane] = xin;
+    }
+    __syncwarp();
+
+    // phase C: per-octant moment partials of every source of the warp
+#pragma unroll 1
+    for (int i = lane; i < SB * BV; i += 32) {
+        const int il = i / BV, cs = i - il * BV;
+        if (!(okmask >> il & 1u)) continue;   // converged sources keep their last partials
+        const int sxc = cs % BX, syc = (cs / BX) % BY, szc = cs / (BX * BY);
+        const int cl = ((negz ? BZ - 1 - szc : szc) * BY + (negy ? BY - 1 - syc : syc)) * BX +
+                       (negx ? BX - 1 - sxc : sxc);
+        const float* prow = Qs + cl * kQP + il * NDO;
+        float ps[NDO];
+#pragma unroll
+        for (int dd = 0; dd < NDO; ++dd) ps[dd] = prow[dd];
+        float* out = p.part + (((size_t)oct * BB + b0 + il) * p.NT + tile) * (size_t)(K * BV) + cs;
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int dd = 0; dd < NDO; ++dd) acc = fmaf(Ds[k * NDO + dd], ps[dd], acc);
+            out[k * BV] = acc;
+        }
+    }
+    // outgoing faces; those leaving the grid are the leakage
+    const bool lbx = negx ? tx == 0 : tx == p.NTx - 1;
+    const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
+    const bool lbz = negz ? tz == 0 : tz == p.NTz - 1;
+    faces_out<NDO, fxn, SB>(fx, gx, sx_, nb, okmask, lbx, Lws, 0, leak_sh, mapx);
+    faces_out<NDO, fyn, SB>(fy, gy, sy_, nb, okmask, lby, Lws, 1, leak_sh, mapy);
+    faces_out<NDO, fzn, SB>(fz, gz, sz_, nb, okmask, lbz, Lws, 2, leak_sh, mapz);
+    if (lbx || lby || lbz) {
+        __syncwarp();
+        if (lane < nb && (okmask >> lane & 1u) && leak_sh[lane] != 0.0) atomicAdd(&p.leak[b0 + lane], leak_sh[lane]);
     }
 }
 

@@ -9,14 +9,19 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
 #include "../../include/dts.h"
 #include "dts_kernels.cuh"
+#include "dts_adjoint.cuh"
 
 using namespace dts;
 
@@ -90,6 +95,17 @@ struct dts_problem {
     cudaGraphExec_t graph = nullptr, graph_red = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t eva = nullptr, evb = nullptr, evc = nullptr;   // around the two graph replays
+    // adjoint buffers (allocated by the first dts_solve_adjoint, B = 1)
+    bool adj_ready = false;
+    int adj_W = -1;
+    double *adj_T = nullptr, *adj_part = nullptr, *adj_xf = nullptr, *adj_yf = nullptr,
+           *adj_zf = nullptr, *adj_psi = nullptr, *adj_cpart = nullptr, *adj_S = nullptr,
+           *adj_u00 = nullptr, *adj_a = nullptr, *adj_gt = nullptr, *adj_gs = nullptr,
+           *adj_gsig = nullptr, *adj_dphiu = nullptr, *adj_blk = nullptr, *adj_status = nullptr,
+           *adj_leak = nullptr;
+    unsigned char* adj_mask = nullptr;
+    int *adj_active = nullptr, *adj_ctl = nullptr;
+    std::vector<int32_t> adj_iters;   // [G]
     int graph_launches = 0;           // kernels per graph replay
 };
 
@@ -317,9 +333,50 @@ bool line_tile(const dts_problem* p)
     return (p->TY == 4 && p->TZ == 8) || (p->TY == 8 && p->TZ == 4);
 }
 
+// FP32 problems with 8 x 4 x 4 or 4 x 4 x 4 tiles take the batched kernel
+// (lanes = source x direction pairs)
+bool batch_tile(const dts_problem* p)
+{
+    return !p->fp64 && p->TY == 4 && p->TZ == 4 && (p->TX == 8 || p->TX == 4);
+}
+
+int batch_sources_per_warp(const dts_problem* p) { return 32 / p->ndo; }
+
+template <int NDO, int BX>
+SweepFn<float> batch_fn_k(int K)
+{
+    switch (K) {
+    case 1: return k_sweep_batch<NDO, 1, BX, 4, 4>;
+    case 4: return k_sweep_batch<NDO, 4, BX, 4, 4>;
+    case 9: return k_sweep_batch<NDO, 9, BX, 4, 4>;
+    case 16: return k_sweep_batch<NDO, 16, BX, 4, 4>;
+    }
+    return nullptr;
+}
+
+template <int BX>
+SweepFn<float> batch_fn_x(int ndo, int K)
+{
+    switch (ndo) {
+    case 1: return batch_fn_k<1, BX>(K);
+    case 3: return batch_fn_k<3, BX>(K);
+    case 6: return batch_fn_k<6, BX>(K);
+    case 10: return batch_fn_k<10, BX>(K);
+    }
+    return nullptr;
+}
+
+SweepFn<float> batch_fn(const dts_problem* p)
+{
+    return p->TX == 8 ? batch_fn_x<8>(p->ndo, p->K) : batch_fn_x<4>(p->ndo, p->K);
+}
+
 template <typename R>
 SweepFn<R> sweep_fn(const dts_problem* p)
 {
+    if constexpr (sizeof(R) == 4) {
+        if (batch_tile(p)) return batch_fn(p);
+    }
     if (line_tile(p))
         return p->TY == 4 ? lines_fn<R, 4, 8>(p->ndo, p->K) : lines_fn<R, 8, 4>(p->ndo, p->K);
     return sweep_fn_generic<R>(p->ndo, p->K);
@@ -339,6 +396,8 @@ RedFn<R> reduce_fn(int K)
 
 size_t sweep_smem(const dts_problem* p)
 {
+    if (batch_tile(p))
+        return p->TX == 8 ? sweep_batch_smem<8, 4, 4>(p->ndo, p->K) : sweep_batch_smem<4, 4, 4>(p->ndo, p->K);
     const int xfaces = line_tile(p) ? 32 : p->TY * p->TZ;
     const size_t n = (size_t)p->ndo * p->TV +
                      (size_t)p->ndo * (xfaces + p->TX * p->TZ + p->TX * p->TY) + p->TV +
@@ -351,6 +410,7 @@ size_t sweep_smem(const dts_problem* p)
 // warp per run of directions (2 warps unless the octant has fewer directions)
 int sweep_threads(const dts_problem* p)
 {
+    if (batch_tile(p)) return 32;
     if (!line_tile(p)) return kSweepThreads;
     const int nw = std::max(1, std::min(p->line_warps, p->ndo));
     return 32 * nw;
@@ -389,7 +449,10 @@ dts_status record_sweep(dts_problem* p)
     const int nthr = sweep_threads(p);
     for (int s = 0; s < p->n_stages; ++s) {
         const int cnt = p->stage_off_h[s + 1] - p->stage_off_h[s];
-        const unsigned grid = (unsigned)cnt * 8u * (unsigned)p->B;
+        const unsigned groups = batch_tile(p) ? (unsigned)((p->B + batch_sources_per_warp(p) - 1) /
+                                                           batch_sources_per_warp(p))
+                                              : (unsigned)p->B;
+        const unsigned grid = (unsigned)cnt * 8u * groups;
         sf<<<grid, nthr, smem, p->stream>>>(sp, s);
     }
     return DTS_OK;
@@ -648,12 +711,14 @@ void choose_tile(dts_problem* p)
         p->TV = p->TX * p->TY * p->TZ;
         return;
     }
-    // default: 32 x-lines (4 in y, 8 in z) per tile for the warp-synchronous
-    // kernel, 8 cells long in x (measured fastest of 4..32 on the 96^3 S8 P3
-    // batch)
+    // default: FP32 batches of at least a warp's worth of sources take the
+    // batched kernel's 8 x 4 x 4 tile; otherwise 32 x-lines (4 in y, 8 in z)
+    // per tile for the warp-synchronous kernel, 8 cells long in x (measured
+    // fastest of 4..32 on the 96^3 S8 P3 batch)
+    const bool batched = p->d.precision == DTS_PREC_FP32 && p->d.batch >= 32 / p->ndo;
     p->TX = 8;
     p->TY = 4;
-    p->TZ = 8;
+    p->TZ = batched ? 4 : 8;
     p->TV = p->TX * p->TY * p->TZ;
 }
 
@@ -869,6 +934,184 @@ std::vector<T> to_tiled(const dts_problem* p, const T* nat, T pad)
                         }
             }
     return out;
+}
+
+// ---------------------------------------------------------------------------
+// discrete adjoint (FP64): see dts_adjoint.cuh
+// ---------------------------------------------------------------------------
+template <int NDO, int K>
+void* adj_sweep_fn_k(int mode)
+{
+    return mode == 1 ? (void*)k_sweep_adj<NDO, K, 1> : (void*)k_sweep_adj<NDO, K, 2>;
+}
+
+template <int NDO>
+void* adj_sweep_fn_n(int K, int mode)
+{
+    switch (K) {
+    case 1: return adj_sweep_fn_k<NDO, 1>(mode);
+    case 4: return adj_sweep_fn_k<NDO, 4>(mode);
+    case 9: return adj_sweep_fn_k<NDO, 9>(mode);
+    case 16: return adj_sweep_fn_k<NDO, 16>(mode);
+    }
+    return nullptr;
+}
+
+using AdjFn = void (*)(const AdjSweepParams, int);
+
+AdjFn adj_sweep_fn(int ndo, int K, int mode)
+{
+    switch (ndo) {
+    case 1: return (AdjFn)adj_sweep_fn_n<1>(K, mode);
+    case 3: return (AdjFn)adj_sweep_fn_n<3>(K, mode);
+    case 6: return (AdjFn)adj_sweep_fn_n<6>(K, mode);
+    case 10: return (AdjFn)adj_sweep_fn_n<10>(K, mode);
+    }
+    return nullptr;
+}
+
+size_t adj_smem(const dts_problem* p)
+{
+    const size_t n = (size_t)p->ndo * p->TV +
+                     (size_t)p->ndo * (p->TY * p->TZ + p->TX * p->TZ + p->TX * p->TY) + p->TV +
+                     2 * p->ndo * p->K + 4 * p->ndo;
+    return n * sizeof(double);
+}
+
+dts_status adj_alloc(dts_problem* p)
+{
+    if (p->adj_ready && p->adj_W != p->W) {   // band width changed: resize the source ring
+        dfree(p, p->adj_S);
+        p->adj_S = nullptr;
+        TRY(dalloc_t(p, &p->adj_S, (size_t)(p->W + 1) * p->NC * p->K));
+        p->adj_W = p->W;
+    }
+    if (p->adj_ready) return DTS_OK;
+    p->adj_W = p->W;
+    const size_t NC = p->NC, K = p->K, nd = p->nd, G = p->G, V = p->V, ndo = p->ndo;
+    TRY(dalloc_t(p, &p->adj_T, NC * K));
+    TRY(dalloc_t(p, &p->adj_part, 8 * NC * K));
+    TRY(dalloc_t(p, &p->adj_xf, 8 * (size_t)p->NTy * p->NTz * ndo * p->TY * p->TZ));
+    TRY(dalloc_t(p, &p->adj_yf, 8 * (size_t)p->NTx * p->NTz * ndo * p->TX * p->TZ));
+    TRY(dalloc_t(p, &p->adj_zf, 8 * (size_t)p->NTx * p->NTy * ndo * p->TX * p->TY));
+    TRY(dalloc_t(p, &p->adj_psi, nd * NC));
+    TRY(dalloc_t(p, &p->adj_mask, nd * NC));
+    TRY(dalloc_t(p, &p->adj_cpart, 8 * NC));
+    TRY(dalloc_t(p, &p->adj_S, (size_t)(p->W + 1) * NC * K));
+    TRY(dalloc_t(p, &p->adj_u00, NC));
+    TRY(dalloc_t(p, &p->adj_a, G * V));
+    TRY(dalloc_t(p, &p->adj_gt, V));
+    TRY(dalloc_t(p, &p->adj_gs, V));
+    TRY(dalloc_t(p, &p->adj_gsig, G * V));
+    TRY(dalloc_t(p, &p->adj_dphiu, G * V));
+    TRY(dalloc_t(p, &p->adj_blk, (size_t)p->nblk * 4));
+    TRY(dalloc_t(p, &p->adj_status, 4));
+    TRY(dalloc_t(p, &p->adj_leak, 1));
+    TRY(dalloc_t(p, &p->adj_active, 1));
+    TRY(dalloc_t(p, &p->adj_ctl, 4));
+    const int one = 1;
+    CK(cudaMemcpy(p->adj_active, &one, sizeof(int), cudaMemcpyHostToDevice));
+    for (int mode = 1; mode <= 2; ++mode) {
+        AdjFn f = adj_sweep_fn(p->ndo, p->K, mode);
+        if (!f) return fail(p, DTS_ERR_INTERNAL, "no adjoint sweep kernel for this (S_N, P_L)");
+        CK(cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)adj_smem(p)));
+    }
+    p->adj_ready = true;
+    return DTS_OK;
+}
+
+dts_status run_adjoint(dts_problem* p, int b)
+{
+    const int G = p->G, W1 = p->W + 1;
+    const size_t NC = p->NC, K = p->K, V = p->V;
+    const dim3 cgrid((p->NC + 255) / 256);
+    CK(cudaMemsetAsync(p->adj_gt, 0, sizeof(double) * V, p->stream));
+    CK(cudaMemsetAsync(p->adj_gs, 0, sizeof(double) * V, p->stream));
+    CK(cudaMemsetAsync(p->adj_dphiu, 0, sizeof(double) * G * V, p->stream));
+    CK(cudaMemsetAsync(p->adj_leak, 0, sizeof(double), p->stream));
+
+    AdjCellParams ac;
+    ac.c = cell_params(p);
+    ac.c.B = 1;
+    ac.b = b; ac.V = p->V; ac.src = p->src; ac.unc = p->unc; ac.mom = p->mom; ac.q = p->q;
+    ac.a = p->adj_a; ac.S = p->adj_S; ac.Sstride = NC * K; ac.W = p->W;
+    AdjGradParams gp;
+    gp.a = ac; gp.part = p->adj_part; gp.cpart = p->adj_cpart; gp.gt = p->adj_gt; gp.gs = p->adj_gs;
+    gp.gsig = p->adj_gsig; gp.dphiu = p->adj_dphiu;
+
+    AdjSweepParams sp;
+    SweepParams<double>& q = sp.s;
+    q.nx = p->d.nx; q.ny = p->d.ny; q.nz = p->d.nz;
+    q.TX = p->TX; q.TY = p->TY; q.TZ = p->TZ; q.TV = p->TV;
+    q.NTx = p->NTx; q.NTy = p->NTy; q.NTz = p->NTz; q.NT = p->NT;
+    q.B = 1; q.nsub = p->nsub;
+    q.stage_tiles = p->stage_tiles; q.stage_off = p->stage_off;
+    q.diag_cells = p->diag_cells; q.diag_off = p->diag_off;
+    q.A = (const double*)p->At; q.Lw = p->Lw;
+    q.T = p->adj_T; q.sigt = (const double*)p->sigt_r; q.part = p->adj_part;
+    q.xf = p->adj_xf; q.yf = p->adj_yf; q.zf = p->adj_zf;
+    q.active = p->adj_active; q.leak = p->adj_leak;
+    sp.rec_psi = p->adj_psi; sp.rec_mask = p->adj_mask; sp.cpart = p->adj_cpart; sp.NC = p->NC;
+    const size_t smem = adj_smem(p);
+    AdjFn rec = adj_sweep_fn(p->ndo, p->K, 1), adj = adj_sweep_fn(p->ndo, p->K, 2);
+
+    RedParams<double> rp;
+    rp.B = 1; rp.NT = p->NT; rp.TV = p->TV; rp.NC = p->NC;
+    rp.part = p->adj_part; rp.phi00 = p->adj_u00; rp.T = p->adj_T; rp.F = p->adj_S;
+    rp.Fstride = NC * K; rp.ctl = p->adj_ctl; rp.sigs = (const double*)p->sigs; rp.sigs0 = p->sigs0;
+    rp.sigt64 = p->sigt64; rp.mat_t = p->mat_t; rp.active = p->adj_active;
+    rp.vol = p->d.dx * p->d.dy * p->d.dz; rp.blk = p->adj_blk;
+    RedFn<double> rf = reduce_fn<double>(p->K);
+
+    p->adj_iters.assign(G, 0);
+    for (int g = G - 1; g >= std::max(0, G - W1); --g)
+        k_adj_source_init<<<cgrid, 256, 0, p->stream>>>(ac, g, g % W1);
+    for (int g = G - 1; g >= 0; --g) {
+        const int slot = g % W1;
+        k_set_ctl<<<1, 1, 0, p->stream>>>(p->adj_ctl, g, slot);
+        launch_group_xs<double>(p, g);
+        k_adj_source_T<<<cgrid, 256, 0, p->stream>>>(ac, g, p->adj_T);
+        // forward sweep of the converged source, recording psi and fixup sets
+        q.M = (const double*)p->Mt;
+        q.Dt = (const double*)p->Dt;
+        for (int s = 0; s < p->n_stages; ++s) {
+            const int cnt = p->stage_off_h[s + 1] - p->stage_off_h[s];
+            rec<<<(unsigned)cnt * 8u, kSweepThreads, smem, p->stream>>>(sp, s);
+        }
+        // adjoint source iteration: the transposed sweep swaps the roles of D and M
+        q.M = (const double*)p->Dt;
+        q.Dt = (const double*)p->Mt;
+        CK(cudaMemsetAsync(p->adj_u00, 0, sizeof(double) * NC, p->stream));
+        k_group_init<double><<<(unsigned)((NC * K + 255) / 256), 256, 0, p->stream>>>(
+            NC * K, p->adj_S + (size_t)slot * NC * K, p->adj_T);
+        CK(cudaGetLastError());
+        for (int it = 1; it <= p->d.max_iters; ++it) {
+            for (int s = 0; s < p->n_stages; ++s) {
+                const int cnt = p->stage_off_h[s + 1] - p->stage_off_h[s];
+                adj<<<(unsigned)cnt * 8u, kSweepThreads, smem, p->stream>>>(sp, s);
+            }
+            rf<<<dim3(p->nblk, 1), kRedThreads, 0, p->stream>>>(rp);
+            k_resid_final<<<1, 256, 0, p->stream>>>(p->adj_blk, p->nblk, p->adj_leak, p->adj_status);
+            CK(cudaMemcpyAsync(p->h_status, p->adj_status, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                               p->stream));
+            CK(cudaStreamSynchronize(p->stream));
+            p->adj_iters[g] = it;
+            if (p->d.tol > 0.0 && p->h_status[0] < p->d.tol) break;
+        }
+        k_adj_grad<<<cgrid, 256, 0, p->stream>>>(gp, g);
+        if (g - W1 >= 0) k_adj_source_init<<<cgrid, 256, 0, p->stream>>>(ac, g - W1, slot);
+        CK(cudaGetLastError());
+    }
+    RayParams rp2;
+    rp2.nx = p->d.nx; rp2.ny = p->d.ny; rp2.nz = p->d.nz; rp2.V = p->V; rp2.G = G;
+    rp2.dx = p->d.dx; rp2.dy = p->d.dy; rp2.dz = p->d.dz;
+    rp2.x0 = p->d.x0; rp2.y0 = p->d.y0; rp2.z0 = p->d.z0;
+    rp2.mat = p->mat_nat; rp2.scale_t = p->scale_t_nat; rp2.sigma_t = p->sigma_t;
+    rp2.src = p->src; rp2.spec = p->spec; rp2.unc = p->unc;
+    k_adj_ray<<<(unsigned)((V + 127) / 128), 128, 0, p->stream>>>(rp2, p->adj_a, p->adj_dphiu, b, p->adj_gt);
+    CK(cudaGetLastError());
+    return DTS_OK;
 }
 
 }  // namespace
@@ -1094,6 +1337,38 @@ dts_status dts_get_balance(dts_problem* p, double* out, size_t out_len)
     return DTS_OK;
 }
 
+dts_status dts_solve_adjoint(dts_problem* p, int batch_index, const double* dL_dphi, double* dL_dscale_t,
+                             double* dL_dscale_s, double* dL_dsigma_t, int ptrs_are_device)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->fp64) return fail(p, DTS_ERR_STATE, "the adjoint needs a DTS_PREC_FP64 problem");
+    if (!p->d.keep_moments) return fail(p, DTS_ERR_STATE, "the adjoint needs keep_moments = 1");
+    if (!p->solved) return fail(p, DTS_ERR_STATE, "no forward solve has completed");
+    if (batch_index < 0 || batch_index >= p->B) return fail(p, DTS_ERR_INVALID_ARG, "batch_index out of range");
+    if (!dL_dphi || !dL_dscale_t || !dL_dscale_s) return fail(p, DTS_ERR_INVALID_ARG, "NULL pointer");
+    DevGuard guard(p->d.device);
+    TRY(adj_alloc(p));
+    const size_t GV = (size_t)p->G * p->V, V = p->V;
+    const cudaMemcpyKind in = ptrs_are_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind out = ptrs_are_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(p->adj_a, dL_dphi, sizeof(double) * GV, in, p->stream));
+    TRY(run_adjoint(p, batch_index));
+    CK(cudaMemcpyAsync(dL_dscale_t, p->adj_gt, sizeof(double) * V, out, p->stream));
+    CK(cudaMemcpyAsync(dL_dscale_s, p->adj_gs, sizeof(double) * V, out, p->stream));
+    if (dL_dsigma_t) CK(cudaMemcpyAsync(dL_dsigma_t, p->adj_gsig, sizeof(double) * GV, out, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    return DTS_OK;
+}
+
+dts_status dts_get_adjoint_iterations(dts_problem* p, int32_t* out, size_t out_len)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!out || out_len < (size_t)p->G) return fail(p, DTS_ERR_INVALID_ARG, "out too small");
+    if (p->adj_iters.size() != (size_t)p->G) return fail(p, DTS_ERR_STATE, "no adjoint solve has run");
+    std::copy(p->adj_iters.begin(), p->adj_iters.end(), out);
+    return DTS_OK;
+}
+
 const char* dts_last_error(const dts_problem* p) { return p ? p->err.c_str() : g_thread_error.c_str(); }
 
 void dts_destroy_problem(dts_problem* p)
@@ -1143,6 +1418,92 @@ dts_status dts_moment_tables(int sn_order, int legendre_order, double* D, double
     moment_tables(legendre_order, a, b, c, w, Dv, Mv);
     std::copy(Dv.begin(), Dv.end(), D);
     std::copy(Mv.begin(), Mv.end(), M);
+    return DTS_OK;
+}
+
+dts_status dts_tune_tile(dts_problem_desc* desc, double* best_updates_per_s)
+{
+    static std::mutex mu;
+    static std::map<std::vector<long long>, std::tuple<int, int, int, double>> cache;
+    if (!desc) return fail(nullptr, DTS_ERR_INVALID_ARG, "desc is NULL");
+    int nd = 0;
+    {
+        double a[80], b2[80], c[80], w[80];
+        if (dts_quadrature(desc->sn_order, a, b2, c, w, &nd) != DTS_OK)
+            return fail(nullptr, DTS_ERR_INVALID_ARG, "sn_order must be 2, 4, 6 or 8");
+    }
+    int dev_name_hash = 0;
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, desc->device) != cudaSuccess)
+            return fail(nullptr, DTS_ERR_CUDA, "cannot query the device");
+        for (const char* q = prop.name; *q; ++q) dev_name_hash = dev_name_hash * 31 + *q;
+    }
+    const int probe_b = std::min(desc->batch, 16);
+    const std::vector<long long> key = {desc->nx, desc->ny, desc->nz, desc->sn_order, desc->legendre_order,
+                                        probe_b, (long long)desc->precision, desc->device, dev_name_hash};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            desc->tile_x = std::get<0>(it->second);
+            desc->tile_y = std::get<1>(it->second);
+            desc->tile_z = std::get<2>(it->second);
+            if (best_updates_per_s) *best_updates_per_s = std::get<3>(it->second);
+            return DTS_OK;
+        }
+    }
+    std::vector<std::array<int, 3>> cand;
+    if (desc->precision == DTS_PREC_FP32) {
+        cand.push_back({8, 4, 4});
+        cand.push_back({4, 4, 4});
+    }
+    for (auto t : std::vector<std::array<int, 3>>{{8, 4, 8}, {4, 4, 8}, {16, 4, 8}, {8, 8, 4}, {8, 8, 8}, {4, 4, 4}})
+        cand.push_back(t);
+    // probe: one group, homogeneous scatterer, unit volumetric source, two iterations
+    const int L = desc->legendre_order, V = desc->nx * desc->ny * desc->nz;
+    const double h = std::min(desc->dx, std::min(desc->dy, desc->dz));
+    std::vector<double> st(1, 0.5 / h), ss(L + 1);
+    for (int l = 0; l <= L; ++l) ss[l] = 0.25 / h * std::pow(0.3, l);
+    std::vector<int32_t> mat(V, 0);
+    std::vector<double> q(V, 1.0);
+    dts_source src{};
+    src.kind = 0;
+    src.q = q.data();
+    double best = -1.0;
+    std::array<int, 3> best_t = {0, 0, 0};
+    for (const auto& t : cand) {
+        dts_problem_desc d = *desc;
+        d.n_groups = 1;
+        d.batch = probe_b;
+        d.tol = 0.0;
+        d.max_iters = 2;
+        d.keep_moments = 0;
+        d.tile_x = t[0];
+        d.tile_y = t[1];
+        d.tile_z = t[2];
+        dts_problem* pr = nullptr;
+        if (dts_create_problem(&d, &pr) != DTS_OK) continue;   // tile does not fit
+        bool ok = dts_set_materials(pr, 1, st.data(), ss.data(), mat.data(), nullptr, nullptr) == DTS_OK;
+        for (int b = 0; ok && b < probe_b; ++b) ok = dts_set_source(pr, b, &src) == DTS_OK;
+        dts_solve_stats stats{};
+        if (ok) ok = dts_solve(pr, &stats) == DTS_OK;
+        if (ok && stats.sweep_ms > 0.0) {
+            const double ups = (double)stats.updates / (stats.sweep_ms * 1e-3);
+            if (ups > best) {
+                best = ups;
+                best_t = t;
+            }
+        }
+        dts_destroy_problem(pr);
+    }
+    if (best <= 0.0) return fail(nullptr, DTS_ERR_CUDA, "no candidate tile could be timed");
+    desc->tile_x = best_t[0];
+    desc->tile_y = best_t[1];
+    desc->tile_z = best_t[2];
+    if (best_updates_per_s) *best_updates_per_s = best;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = std::make_tuple(best_t[0], best_t[1], best_t[2], best);
     return DTS_OK;
 }
 

@@ -65,7 +65,8 @@ EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_sol
            "dts_get_scalar_fluence", "dts_get_moments", "dts_get_iterations", "dts_get_residuals",
            "dts_get_balance", "dts_last_error", "dts_destroy_problem", "dts_status_string",
            "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size",
-           "dts_sweep_once_noalloc")
+           "dts_sweep_once_noalloc", "dts_solve_adjoint", "dts_get_adjoint_iterations",
+           "dts_tune_tile")
 
 
 def lib():
@@ -95,6 +96,10 @@ def lib():
         "dts_quadrature": ([C.c_int, _dp, _dp, _dp, _dp, C.POINTER(C.c_int)], C.c_int),
         "dts_moment_tables": ([C.c_int, C.c_int, _dp, _dp], C.c_int),
         "dts_subsweep_size": ([C.c_int, C.c_int, C.c_int, C.c_int], C.c_longlong),
+        "dts_tune_tile": ([C.POINTER(ProblemDesc), C.POINTER(C.c_double)], C.c_int),
+        "dts_solve_adjoint": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_int], C.c_int),
+        "dts_get_adjoint_iterations": ([C.c_void_p, _ip, C.c_size_t], C.c_int),
         "dts_sweep_once_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                     C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p], C.c_int),
@@ -157,6 +162,15 @@ def sweep_once_noalloc(nx, ny, nz, dx, dy, dz, sn_order, legendre_order, src_mom
                                         C.c_void_p(src_moments.data_ptr()),
                                         C.c_void_p(sigma_t.data_ptr()), C.c_void_p(phi.data_ptr()),
                                         stream))
+
+
+def tune_tile(w: inputs.Workload, precision=PREC_FP64, batch=None, device=0):
+    """Tile chosen by dts_tune_tile for workload w's shape: ((tx, ty, tz), probe updates/s)."""
+    d = ProblemDesc(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.x0, w.y0, w.z0, w.n_groups, w.sn_order,
+                    w.legendre_order, batch or w.batch, precision, 0.0, 2, None, device, 0, 0, 0, 0)
+    best = C.c_double(0.0)
+    _check(lib().dts_tune_tile(C.byref(d), C.byref(best)))
+    return (d.tile_x, d.tile_y, d.tile_z), best.value
 
 
 # ------------------------------------------------------------------ problems
@@ -252,6 +266,37 @@ class Problem:
         out = np.zeros(self.B * self.G)
         _check(lib().dts_get_residuals(self._h, _dptr(out), out.size), self._h)
         return out.reshape(self.B, self.G)
+
+    def adjoint(self, b: int, dL_dphi, with_sigma_t: bool = False):
+        """Discrete adjoint of the last (FP64, keep_moments) solve of batch
+        member b. dL_dphi [G][V] is dL/d(total scalar fluence). Returns
+        (dL/dscale_t [V], dL/dscale_s [V][, dL/dsigma_t^g [G][V]]) as numpy
+        arrays, or writes into CUDA tensors when dL_dphi is one."""
+        if hasattr(dL_dphi, "is_cuda") and dL_dphi.is_cuda:
+            import torch
+            a = dL_dphi.contiguous().to(torch.float64)
+            gt = torch.empty(self.V, dtype=torch.float64, device=a.device)
+            gs = torch.empty_like(gt)
+            gg = torch.empty(self.G * self.V, dtype=torch.float64, device=a.device) if with_sigma_t else None
+            _check(lib().dts_solve_adjoint(self._h, b, C.c_void_p(a.data_ptr()), C.c_void_p(gt.data_ptr()),
+                                           C.c_void_p(gs.data_ptr()),
+                                           C.c_void_p(gg.data_ptr()) if gg is not None else None, 1),
+                   self._h)
+            return (gt, gs, gg.view(self.G, self.V)) if with_sigma_t else (gt, gs)
+        a = np.ascontiguousarray(dL_dphi, dtype=np.float64).reshape(-1)
+        assert a.size == self.G * self.V
+        gt, gs = np.zeros(self.V), np.zeros(self.V)
+        gg = np.zeros(self.G * self.V) if with_sigma_t else None
+        _check(lib().dts_solve_adjoint(self._h, b, a.ctypes.data_as(C.c_void_p), gt.ctypes.data_as(C.c_void_p),
+                                       gs.ctypes.data_as(C.c_void_p),
+                                       gg.ctypes.data_as(C.c_void_p) if gg is not None else None, 0),
+               self._h)
+        return (gt, gs, gg.reshape(self.G, self.V)) if with_sigma_t else (gt, gs)
+
+    def adjoint_iterations(self):
+        out = np.zeros(self.G, dtype=np.int32)
+        _check(lib().dts_get_adjoint_iterations(self._h, out.ctypes.data_as(_ip), out.size), self._h)
+        return out
 
     def balance(self):
         out = np.zeros(self.B * self.G * 3)

@@ -1,0 +1,129 @@
+"""The GPU discrete adjoint (dts_solve_adjoint, FP64) against the oracle's
+adjoint and against central finite differences of GPU forward solves."""
+import numpy as np
+import pytest
+
+from paper_1910_11335_b300 import dts, inputs
+from parity_util import rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(w, tol, tile=(0, 0, 0), scale_t=None, scale_s=None, max_iters=4000):
+    p = dts.Problem(nx=w.nx, ny=w.ny, nz=w.nz, dx=w.dx, dy=w.dy, dz=w.dz, x0=w.x0, y0=w.y0, z0=w.z0,
+                    n_groups=w.n_groups, sn_order=w.sn_order, legendre_order=w.legendre_order,
+                    batch=1, precision=dts.PREC_FP64, tol=tol, max_iters=max_iters,
+                    keep_moments=True, tile=tile)
+    p.set_materials(w.sigma_t, w.sigma_s, w.mat_id.reshape(-1), scale_t, scale_s)
+    p.set_source(0, w.sources[0])
+    return p
+
+
+@pytest.mark.parametrize("case", ["cone_s4p1", "thick_s6p2", "cone_s8p3_generic_tile"])
+def test_adjoint_matches_oracle_adjoint(ora, case):
+    if case == "cone_s4p1":
+        w, tile = inputs.small_cone(9, 8, 7, n_groups=3, sn_order=4, legendre_order=1), (0, 0, 0)
+    elif case == "thick_s6p2":
+        w = inputs.random_volumetric(7, 5, 6, n_groups=2, sn_order=6, legendre_order=2,
+                                     seed_index=510, thin=False)
+        tile = (4, 4, 4)
+    else:
+        w, tile = inputs.small_cone(6, 7, 5, n_groups=2, sn_order=8, legendre_order=3), (3, 4, 2)
+    rng = np.random.default_rng(11)
+    a = rng.uniform(0.0, 1.0, size=(w.n_groups, w.n_voxels))
+    gt_o, gs_o, gg_o = ora.adjoint(w, a, tol=1e-14, max_iters=4000, n_threads=4)
+    p = _problem(w, 1e-14, tile)
+    p.solve(allow_not_converged=True)
+    gt, gs, gg = p.adjoint(0, a, with_sigma_t=True)
+    assert rel_max(gt, gt_o) <= 1e-9
+    assert rel_max(gs, gs_o) <= 1e-9
+    for g in range(w.n_groups):
+        assert rel_max(gg[g], gg_o[g]) <= 1e-9
+    assert np.all(p.adjoint_iterations() > 1)
+
+
+def _detector_loss(w, phi, target):
+    pix, n_pix = inputs.detector_layout(w)
+    layer = phi.reshape(w.n_groups, w.nz, w.ny, w.nx)[:, :, w.ny - 1, :]
+    resp = np.zeros(n_pix)
+    np.add.at(resp, pix.reshape(-1), (w.group_energy_kev[:, None, None] * layer).sum(0).reshape(-1))
+    return float(((resp - target) ** 2).sum()), resp
+
+
+def test_adjoint_64_central_differences():
+    """Differentiation form: 64^3, 8 groups, S6, P1; squared detector-response
+    error against a seeded target; central differences (step 1e-6 relative,
+    FP64 solves) on 20 seeded voxels, 10 for sigma_t and 10 for sigma_s."""
+    w = inputs.adjoint_64()
+    tol = 1e-14
+    one = np.ones(w.n_voxels)
+    p = _problem(w, tol)
+    p.solve(allow_not_converged=True)
+    phi = p.fluence(0, dts.TOTAL)
+    _, resp0 = _detector_loss(w, phi, 0.0)
+    target = resp0 * inputs.detector_target_noise(resp0.size)
+    L0, resp = _detector_loss(w, phi, target)
+    pix, _ = inputs.detector_layout(w)
+    a = np.zeros((w.n_groups, w.nz, w.ny, w.nx))
+    a[:, :, w.ny - 1, :] = 2.0 * (resp - target)[pix][None, :, :] * w.group_energy_kev[:, None, None]
+    gt, gs = p.adjoint(0, a.reshape(w.n_groups, -1))
+    rng = np.random.default_rng(1910)
+    # seeded voxels among those whose gradient is well above the solve noise
+    cand_t = np.argsort(-np.abs(gt))[:2000]
+    cand_s = np.argsort(-np.abs(gs))[:2000]
+    vt = rng.choice(cand_t, 10, replace=False)
+    vs = rng.choice(cand_s, 10, replace=False)
+    h = 1e-6
+
+    def loss(st, ss):
+        q = _problem(w, tol, scale_t=st, scale_s=ss)
+        q.solve(allow_not_converged=True)
+        return _detector_loss(w, q.fluence(0, dts.TOTAL), target)[0]
+
+    for v in vt:
+        e = np.zeros(w.n_voxels)
+        e[v] = h
+        fd = (loss(one + e, one) - loss(one - e, one)) / (2 * h)
+        assert abs(fd - gt[v]) <= 2e-4 * abs(gt[v]), (v, fd, gt[v])
+    for v in vs:
+        e = np.zeros(w.n_voxels)
+        e[v] = h
+        fd = (loss(one, one + e) - loss(one, one - e)) / (2 * h)
+        assert abs(fd - gs[v]) <= 2e-4 * abs(gs[v]), (v, fd, gs[v])
+
+
+def test_autograd_function_matches_adjoint():
+    import torch
+    from paper_1910_11335_b300 import autograd
+    w = inputs.small_cone(10, 12, 9, n_groups=3, sn_order=6, legendre_order=1)
+    st = torch.ones(w.n_voxels, dtype=torch.float64, device="cuda", requires_grad=True)
+    ss = torch.ones(w.n_voxels, dtype=torch.float64, device="cuda", requires_grad=True)
+    phi = autograd.solve(st, ss, w, tol=1e-13)
+    resp = autograd.detector_response(phi, w)
+    target = resp.detach() * 0.9
+    loss = ((resp - target) ** 2).sum()
+    loss.backward()
+    # the same gradient through the library's adjoint directly
+    p = _problem(w, 1e-13)
+    p.solve(allow_not_converged=True)
+    phi_np = p.fluence(0, dts.TOTAL)
+    x = torch.tensor(phi_np, dtype=torch.float64, device="cuda", requires_grad=True)
+    l2 = ((autograd.detector_response(x, w) - target) ** 2).sum()
+    (dphi,) = torch.autograd.grad(l2, [x])
+    gt, gs = p.adjoint(0, dphi.cpu().numpy())
+    assert rel_max(st.grad.cpu().numpy(), gt) <= 1e-9
+    assert rel_max(ss.grad.cpu().numpy(), gs) <= 1e-9
+
+
+def test_adjoint_needs_fp64_and_moments():
+    w = inputs.small_cone(6, 5, 4, n_groups=2, sn_order=4, legendre_order=1)
+    p = dts.problem_from_workload(w, tol=0.0, max_iters=2)
+    p.solve()
+    with pytest.raises(dts.DTSError) as e:
+        p.adjoint(0, np.zeros((2, w.n_voxels)))
+    assert e.value.status == dts.DTS_ERR_STATE
+    q = dts.problem_from_workload(w, precision=dts.PREC_FP32, tol=0.0, max_iters=2, keep_moments=True)
+    q.solve()
+    with pytest.raises(dts.DTSError) as e:
+        q.adjoint(0, np.zeros((2, w.n_voxels)))
+    assert e.value.status == dts.DTS_ERR_STATE

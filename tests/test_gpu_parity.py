@@ -112,6 +112,53 @@ def test_fp32_form_relative_l2(ora):
         assert rel_l2(col, r.collided) <= TOL_FP32_L2
 
 
+BATCH_CASES = [
+    # dims,       N, L, G, batch  (FP32, 8x4x4 tiles: lanes = source x direction pairs)
+    ((13, 11, 9), 8, 3, 3, 4),     # 3 sources x 10 directions per warp, ragged group
+    ((10, 9, 17), 6, 1, 2, 7),     # 5 x 6
+    ((9, 14, 6), 4, 2, 2, 11),     # 10 x 3
+    ((7, 6, 9), 2, 0, 2, 33),      # 32 x 1
+]
+
+
+@pytest.mark.parametrize("dims,N,L,G,B", BATCH_CASES)
+def test_batched_fp32_kernel(ora, dims, N, L, G, B):
+    w = inputs.small_cone(*dims, n_groups=G, sn_order=N, legendre_order=L, n_sources=B)
+    p, st = _gpu(w, precision=dts.PREC_FP32, tol=0.0, max_iters=5, tile=(8, 4, 4))
+    assert (st.tile_x, st.tile_y, st.tile_z) == (8, 4, 4)
+    for b in sorted({0, B // 2, B - 1}):
+        r = ora.solve(w, b, tol=0.0, max_iters=5, n_threads=8)
+        col = p.fluence(b, dts.COLLIDED)
+        for g in range(G):
+            assert rel_l2(col[g], r.collided[g]) <= TOL_FP32_L2, (b, g)
+    bal = p.balance()
+    for b in range(B):
+        for g in range(G):
+            assert abs(bal[b, g, 0] - bal[b, g, 1] - bal[b, g, 2]) <= 1e-5 * bal[b, g, 0]
+
+
+def test_batched_fp32_sources_converging_at_different_counts(ora):
+    w = inputs.small_cone(16, 15, 14, n_groups=3, sn_order=8, legendre_order=3, n_sources=8)
+    # members 4..7: volumetric sources in air, water and bone regions, which
+    # converge at other iteration counts than the cone beams
+    rng = np.random.default_rng(4)
+    mat = w.mat_id.reshape(-1)
+    for b, m in zip(range(4, 8), (0, 1, 2, 1)):
+        q = np.zeros((3, w.n_voxels))
+        idx = np.flatnonzero(mat == m)
+        q[:, rng.choice(idx, min(20, idx.size), replace=False)] = 1.0
+        w.sources[b] = inputs.Source(kind=0, q=q)
+    p, st = _gpu(w, precision=dts.PREC_FP32, tol=1e-6, max_iters=500, tile=(8, 4, 4))
+    assert (st.tile_x, st.tile_y, st.tile_z) == (8, 4, 4)
+    its = p.iterations()
+    assert len(set(its[:, 0])) > 1          # the batch members stop at different iterations
+    for b in (0, 3, 4, 5, 6, 7):
+        r = ora.solve(w, b, tol=1e-11, max_iters=500, n_threads=8)
+        tot = p.fluence(b, dts.TOTAL)
+        for g in range(3):
+            assert rel_l2(tot[g], r.total[g]) <= TOL_FP32_L2, (b, g)
+
+
 def test_fp64_is_deterministic():
     w = inputs.small_cone(10, 9, 8, n_groups=2, sn_order=8, legendre_order=3)
     a, _ = _gpu(w, tol=0.0, max_iters=4)
