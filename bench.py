@@ -179,7 +179,7 @@ def run_reference(args):
 
 def sweep_kernel_name(tile, fp32):
     """The sweep kernel the library launches for a tile shape."""
-    if fp32 and tuple(tile) == (8, 4, 4):
+    if fp32 and tuple(tile) in ((8, 4, 4), (4, 4, 4)):
         return "k_sweep_batch"
     if tile[1] * tile[2] == 32 and tile[1] in (4, 8):
         return "k_sweep_lines"

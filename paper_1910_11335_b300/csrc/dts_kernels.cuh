@@ -558,67 +558,82 @@ k_sweep_lines(const SweepParams<R> p, const int stage)
 // all lanes solve the same cell at the same time: the warp walks the tile in
 // upwind order (the sub-sweeps of Sec. II.B reduce to a lexicographic walk
 // inside one warp), the x-face stays in a register and the y/z faces sit in
-// per-lane shared-memory columns updated in place. No skew, no shuffles, no
-// CTA barrier; shared-memory offsets are compile-time in the unrolled x walk.
-// Shared memory holds the tile in octant-local order, so the walk is the
-// same for every octant. Faces move between global and shared memory as
-// coalesced per-source blocks. Padding cells pass faces through.
+// per-lane shared-memory columns updated in place. The tile is processed one
+// x-line at a time: the line's source moments arrive by cp.async one line
+// ahead, are contracted to the lanes' directions, swept, and reduced to
+// octant moment partials, so shared memory holds one line of sources and
+// fluxes rather than the whole tile. The contractions use packed FP32x2 FMA
+// (two directions, or two moments, per instruction; each half rounds like
+// fmaf). Padding cells pass faces through.
 // ---------------------------------------------------------------------------
-constexpr int kQP = 33;   // padded lane row of the source/flux buffer
-
-template <int BX, int BY, int BZ>
-__host__ __device__ constexpr size_t sweep_batch_smem(int ndo, int K)
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi)
 {
-    // floats (+ 8 of slack for the 16-byte alignment of the doubles), then
-    // 3*ndo leakage weights and up to 32 per-source leakage sums
-    return sizeof(float) * ((size_t)BX * BY * BZ * kQP + 32 * (BY * BZ + BZ * BX + BY * BX) +
-                            BX * BY * BZ + 2 * ndo * K + 8) +
-           sizeof(double) * (3 * ndo + 32);
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
 
-// global face block of one source: [NDO][F] in storage order; shared: [local slot][lane]
-template <int NDO, int F, int SB, typename Map>
-__device__ __forceinline__ void faces_in(float* sh, const float* g0, size_t gstride, int nb,
-                                         unsigned okmask, bool upstream, Map map)
+__device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi)
 {
-    for (int j = threadIdx.x; j < nb * NDO * F; j += 32) {
-        const int il = j / (NDO * F), rem = j - il * (NDO * F), dd = rem / F, e = rem - dd * F;
-        const bool ok = upstream && (okmask >> il & 1u);
-        sh[map(e) * 32 + il * NDO + dd] = ok ? g0[(size_t)il * gstride + rem] : 0.f;
-    }
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-template <int NDO, int F, int SB, typename Map>
-__device__ __forceinline__ void faces_out(const float* sh, float* g0, size_t gstride, int nb,
-                                          unsigned okmask, bool leaving, const double* Lw, int axis,
-                                          double* leak_sh, Map map)
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c)
 {
-    for (int j = threadIdx.x; j < nb * NDO * F; j += 32) {
-        const int il = j / (NDO * F), rem = j - il * (NDO * F), dd = rem / F, e = rem - dd * F;
-        if (!(okmask >> il & 1u)) continue;
-        const float v = sh[map(e) * 32 + il * NDO + dd];
-        g0[(size_t)il * gstride + rem] = v;
-        if (leaving && v != 0.f) atomicAdd(&leak_sh[il], Lw[dd * 3 + axis] * (double)v);
-    }
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
-template <int NDO, int K, int BX, int BY, int BZ>
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <int NDO, int K, int BX>
+struct BatchShape {
+    static constexpr int BY = 4, BZ = 4, BV = BX * BY * BZ;
+    static constexpr int SB = 32 / NDO, NL = SB * NDO;
+    static constexpr int FS = 33;                       // odd lane stride >= 32: every lane owns a column
+    static constexpr int TSTR = K * BX + 8;             // staged source row per source (16-byte multiple)
+    static constexpr int PSTR = NDO * BX + 8;           // line fluxes per source, [NDO][BX] + pad
+    static constexpr int NC_ = SB * K;                  // (source, moment) pairs of phase C
+    static constexpr int fxn = BY * BZ, fyn = BX * BZ, fzn = BX * BY;
+    // float offsets
+    static constexpr int oT = 0;                        // [2][SB][TSTR] staged source moments
+    static constexpr int oP = oT + 2 * SB * TSTR;       // [SB][PSTR] line fluxes (storage x order)
+    static constexpr int oX = oP + SB * PSTR;           // [fxn][FS]
+    static constexpr int oY = oX + fxn * FS;            // [fyn][FS]
+    static constexpr int oZ = oY + fyn * FS;            // [fzn][FS]
+    static constexpr int oS = oZ + fzn * FS;            // [BV] sigma_t, local order
+    static constexpr int nF = (oS + BV + 3) & ~3;
+    static constexpr size_t bytes = sizeof(float) * nF + sizeof(double) * (3 * NDO + SB);
+};
+
+template <int NDO, int K, int BX>
+__host__ __device__ constexpr size_t sweep_batch_smem() { return BatchShape<NDO, K, BX>::bytes; }
+
+template <int NDO, int K, int BX>
 __global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float> p, const int stage)
 {
-    constexpr int SB = 32 / NDO;       // sources per warp
-    constexpr int NL = SB * NDO;       // lanes in use
-    constexpr int BV = BX * BY * BZ;
-    constexpr int fxn = BY * BZ, fyn = BX * BZ, fzn = BX * BY;
-    extern __shared__ __align__(16) unsigned char smem[];
-    float* Qs = reinterpret_cast<float*>(smem);    // [BV][kQP] local cell order, lane column
-    float* fx = Qs + BV * kQP;                     // [BY*BZ][32] x-faces by local (y,z)
-    float* fy = fx + fxn * 32;                     // [BZ*BX][32] y-faces by local (z,x)
-    float* fz = fy + fyn * 32;                     // [BY*BX][32] z-faces by local (y,x)
-    float* sg = fz + fzn * 32;                     // [BV] local order
-    float* Ms = sg + BV;                           // [NDO][K]
-    float* Ds = Ms + NDO * K;                      // [K][NDO]
-    double* Lws = reinterpret_cast<double*>(smem + (((size_t)(Ds + NDO * K - Qs) * 4 + 15) & ~size_t(15)));
-    double* leak_sh = Lws + 3 * NDO;               // [SB]
+    using S = BatchShape<NDO, K, BX>;
+    constexpr int BY = S::BY, BZ = S::BZ, BV = S::BV, SB = S::SB, NL = S::NL, FS = S::FS;
+    constexpr int TSTR = S::TSTR, PSTR = S::PSTR, NCP = S::NC_;
+    constexpr int fxn = S::fxn, fyn = S::fyn, fzn = S::fzn;
+    constexpr int CR = (NCP + 31) / 32;                 // rounds of phase C
+    extern __shared__ __align__(16) float smf[];
+    float* Tst = smf + S::oT;
+    float* Ps = smf + S::oP;
+    float* fx = smf + S::oX;
+    float* fy = smf + S::oY;
+    float* fz = smf + S::oZ;
+    float* sg = smf + S::oS;
+    double* Lws = reinterpret_cast<double*>(smf + S::nF);
+    double* leak_sh = Lws + 3 * NDO;
 
     const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
     int bid = blockIdx.x;
@@ -641,157 +656,219 @@ __global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float>
     const int tile = (tz * p.NTy + ty) * p.NTx + tx;
     const int n0 = oct * NDO;
     const size_t BB = p.B;
+    const float* Tbase = p.T + ((size_t)b0 * p.NT + tile) * (size_t)(K * BV);
+    const size_t Tsrc = (size_t)p.NT * K * BV;     // stride between sources
 
-    for (int i = lane; i < NDO * K; i += 32) {
-        Ms[i] = p.M[n0 * K + i];
-        Ds[(i % K) * NDO + i / K] = p.Dt[n0 * K + i];
-    }
-    for (int i = lane; i < 3 * NDO; i += 32) Lws[i] = p.Lw[n0 * 3 + i];
-    if (lane < SB) leak_sh[lane] = 0.0;
+    auto stage_line = [&](int line, int buf) {
+        const int ly = line % BY, lz = line / BY;
+        const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
+        const int lbase = (sz * BY + sy) * BX;
+        constexpr int CH = BX / 4;                 // 16-byte chunks per (source, moment) row
+        for (int u = lane; u < nb * K * CH; u += 32) {
+            const int il = u / (K * CH), r = u - il * (K * CH), k = r / CH, h = r - k * CH;
+            if (!(okmask >> il & 1u)) continue;
+            cp_async16(Tst + (buf * SB + il) * TSTR + k * BX + h * 4,
+                       Tbase + il * Tsrc + (size_t)k * BV + lbase + h * 4);
+        }
+        cp_async_commit();
+    };
+    stage_line(0, 0);
+
+    // phase-B / phase-A lane: (source bl, direction d); its contraction row of M in registers
     const int bl = lane / NDO, d = lane - bl * NDO;
+    const bool dlane = lane < NL;
     float ax = 0.f, ay = 0.f, az = 0.f;
-    if (lane < NL) {
+    unsigned long long m2[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float m = dlane ? p.M[(n0 + d) * K + k] : 0.f;
+        m2[k] = f2pack(m, m);
+    }
+    if (dlane) {
         ax = p.A[(n0 + d) * 3];
         ay = p.A[(n0 + d) * 3 + 1];
         az = p.A[(n0 + d) * 3 + 2];
     }
     const float asum = ax + ay + az;
+    // phase-C lanes: (source, moment) pairs; their row of D in registers
+    unsigned long long dc[CR][NDO];
+#pragma unroll
+    for (int r = 0; r < CR; ++r) {
+        const int lc = lane + 32 * r, kc = lc % K;
+        const bool ok = lc < NCP;
+#pragma unroll
+        for (int dd = 0; dd < NDO; ++dd) {
+            const float v = ok ? p.Dt[(n0 + dd) * K + kc] : 0.f;
+            dc[r][dd] = f2pack(v, v);
+        }
+    }
+    for (int i = lane; i < 3 * NDO; i += 32) Lws[i] = p.Lw[n0 * 3 + i];
+    if (lane < SB) leak_sh[lane] = 0.0;
+    const float* st = p.sigt + (size_t)tile * BV;
+    for (int cs = lane; cs < BV; cs += 32) {
+        const int sx = cs % BX, sy = (cs / BX) % BY, sz = cs / (BX * BY);
+        sg[((negz ? BZ - 1 - sz : sz) * BY + (negy ? BY - 1 - sy : sy)) * BX + (negx ? BX - 1 - sx : sx)] = st[cs];
+    }
 
-    // incoming faces (zero on the grid boundary), storage -> local order
-    const size_t sx_ = (size_t)(p.NTy * p.NTz) * NDO * fxn, sy_ = (size_t)(p.NTx * p.NTz) * NDO * fyn,
-                 sz_ = (size_t)(p.NTx * p.NTy) * NDO * fzn;
+    // incoming faces (zero on the grid boundary), storage -> local order, coalesced per source
+    const size_t sxs = (size_t)(p.NTy * p.NTz) * NDO * fxn, sys = (size_t)(p.NTx * p.NTz) * NDO * fyn,
+                 szs = (size_t)(p.NTx * p.NTy) * NDO * fzn;
     float* gx = p.xf + (((size_t)oct * BB + b0) * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * (size_t)(NDO * fxn);
     float* gy = p.yf + (((size_t)oct * BB + b0) * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * (size_t)(NDO * fyn);
     float* gz = p.zf + (((size_t)oct * BB + b0) * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * (size_t)(NDO * fzn);
-    auto mapx = [&](int e) {    // storage (sy, sz) -> local slot (ly, lz)
+    auto mapx = [&](int e) {
         const int sy = e % BY, sz = e / BY;
         return (negz ? BZ - 1 - sz : sz) * BY + (negy ? BY - 1 - sy : sy);
     };
-    auto mapy = [&](int e) {    // storage (sx, sz) -> local (lx, lz)
+    auto mapy = [&](int e) {
         const int sx = e % BX, sz = e / BX;
         return (negz ? BZ - 1 - sz : sz) * BX + (negx ? BX - 1 - sx : sx);
     };
-    auto mapz = [&](int e) {    // storage (sx, sy) -> local (lx, ly)
+    auto mapz = [&](int e) {
         const int sx = e % BX, sy = e / BX;
         return (negy ? BY - 1 - sy : sy) * BX + (negx ? BX - 1 - sx : sx);
     };
-    faces_in<NDO, fxn, SB>(fx, gx, sx_, nb, okmask, ta > 0, mapx);
-    faces_in<NDO, fyn, SB>(fy, gy, sy_, nb, okmask, tb > 0, mapy);
-    faces_in<NDO, fzn, SB>(fz, gz, sz_, nb, okmask, tc > 0, mapz);
-
-    // phase A: items (source, cell); consecutive lanes read consecutive cells
-    const float* st = p.sigt + (size_t)tile * BV;
-#pragma unroll 1
-    for (int i = lane; i < SB * BV; i += 32) {
-        const int il = i / BV, cs = i - il * BV;
-        const int sxc = cs % BX, syc = (cs / BX) % BY, szc = cs / (BX * BY);
-        const int cl = ((negz ? BZ - 1 - szc : szc) * BY + (negy ? BY - 1 - syc : syc)) * BX +
-                       (negx ? BX - 1 - sxc : sxc);
-        if (il == 0) sg[cl] = st[cs];
-        if (!(okmask >> il & 1u)) continue;
-        const float* Tt = p.T + ((size_t)(b0 + il) * p.NT + tile) * (size_t)(K * BV) + cs;
-        float t[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) t[k] = Tt[k * BV];
-        float* qrow = Qs + cl * kQP + il * NDO;
-#pragma unroll 1
-        for (int dd = 0; dd < NDO; ++dd) {
-            float q = 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) q = fmaf(Ms[dd * K + k], t[k], q);
-            qrow[dd] = q;
-        }
+#define DTS_FACES_IN(SH, G, STR, F, UP, MAP)                                                       \
+    for (int j = lane; j < nb * NDO * F; j += 32) {                                               \
+        const int il = j / (NDO * F), rem = j - il * (NDO * F), dd = rem / F, e = rem - dd * F;  \
+        const bool ok = (UP) && (okmask >> il & 1u);                                              \
+        SH[MAP(e) * FS + il * NDO + dd] = ok ? G[(size_t)il * STR + rem] : 0.f;                   \
     }
-    __syncwarp();
+    DTS_FACES_IN(fx, gx, sxs, fxn, ta > 0, mapx)
+    DTS_FACES_IN(fy, gy, sys, fyn, tb > 0, mapy)
+    DTS_FACES_IN(fz, gz, szs, fzn, tc > 0, mapz)
+#undef DTS_FACES_IN
 
-    // phase B: the lexicographic walk, every lane on the same cell
     const int nvx = p.nx - tx * BX, nvy = p.ny - ty * BY, nvz = p.nz - tz * BZ;
     unsigned vx = 0;
 #pragma unroll
     for (int lx = 0; lx < BX; ++lx)
         if ((negx ? BX - 1 - lx : lx) < nvx) vx |= 1u << lx;
+    const bool srcok = dlane && (okmask >> bl & 1u);
+
 #pragma unroll 1
     for (int line = 0; line < BY * BZ; ++line) {
+        const int buf = line & 1;
+        if (line + 1 < BY * BZ) stage_line(line + 1, buf ^ 1);
+        else cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
         const int ly = line % BY, lz = line / BY;
-        const bool lok = (negy ? BY - 1 - ly : ly) < nvy && (negz ? BZ - 1 - lz : lz) < nvz;
-        const unsigned vm = lok ? vx : 0u;
-        float* qrow = Qs + line * BX * kQP + lane;
-        float* yrow = fy + lz * BX * 32 + lane;
-        float* zrow = fz + ly * BX * 32 + lane;
-        const float* srow = sg + line * BX;
-        float xin = fx[line * 32 + lane];
-#pragma unroll
-        for (int lx = 0; lx < BX; ++lx) {
-            const float yin = yrow[lx * 32], zin = zrow[lx * 32];
-            float psi, ox, oy, oz;
-            if (vm >> lx & 1u) {
-                const float q = qrow[lx * kQP], sig = srow[lx];
-                psi = __fdividef(q + ax * xin + ay * yin + az * zin, sig + asum);
-                ox = 2.f * psi - xin;
-                oy = 2.f * psi - yin;
-                oz = 2.f * psi - zin;
-                const bool neg = ox < 0.f || oy < 0.f || oz < 0.f;
-                if (__any_sync(0xffffffffu, neg) && neg) {
-                    bool fxd = false, fyd = false, fzd = false;
-#pragma unroll 1
-                    for (int pass = 0; pass < 3; ++pass) {
-                        const bool nx = !fxd && ox < 0.f, ny = !fyd && oy < 0.f, nz = !fzd && oz < 0.f;
-                        if (!(nx || ny || nz)) break;
-                        fxd |= nx;
-                        fyd |= ny;
-                        fzd |= nz;
-                        const float num = q + (fxd ? 0.5f * ax : ax) * xin + (fyd ? 0.5f * ay : ay) * yin +
-                                          (fzd ? 0.5f * az : az) * zin;
-                        const float den = sig + (fxd ? 0.f : ax) + (fyd ? 0.f : ay) + (fzd ? 0.f : az);
-                        psi = __fdividef(num, den);
-                        ox = fxd ? 0.f : 2.f * psi - xin;
-                        oy = fyd ? 0.f : 2.f * psi - yin;
-                        oz = fzd ? 0.f : 2.f * psi - zin;
-                    }
-                }
-            } else {
-                psi = 0.f;
-                ox = xin;
-                oy = yin;
-                oz = zin;
-            }
-            qrow[lx * kQP] = psi;
-            yrow[lx * 32] = oy;
-            zrow[lx * 32] = oz;
-            xin = ox;
-        }
-        fx[line * 32 + lane] = xin;
-    }
-    __syncwarp();
+        const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
 
-    // phase C: per-octant moment partials of every source of the warp
-#pragma unroll 1
-    for (int i = lane; i < SB * BV; i += 32) {
-        const int il = i / BV, cs = i - il * BV;
-        if (!(okmask >> il & 1u)) continue;   // converged sources keep their last partials
-        const int sxc = cs % BX, syc = (cs / BX) % BY, szc = cs / (BX * BY);
-        const int cl = ((negz ? BZ - 1 - szc : szc) * BY + (negy ? BY - 1 - syc : syc)) * BX +
-                       (negx ? BX - 1 - sxc : sxc);
-        const float* prow = Qs + cl * kQP + il * NDO;
-        float ps[NDO];
+        // A: this lane's sources for the line's cells, two cells per FMA, in local x order
+        float q[BX];
+        {
+            const float* tr = Tst + (buf * SB + (srcok ? bl : 0)) * TSTR;
 #pragma unroll
-        for (int dd = 0; dd < NDO; ++dd) ps[dd] = prow[dd];
-        float* out = p.part + (((size_t)oct * BB + b0 + il) * p.NT + tile) * (size_t)(K * BV) + cs;
-#pragma unroll 1
-        for (int k = 0; k < K; ++k) {
-            float acc = 0.f;
+            for (int pp = 0; pp < BX / 2; ++pp) {
+                const int spair = negx ? BX - 2 - 2 * pp : 2 * pp;   // storage pair of local (2pp, 2pp+1)
+                unsigned long long acc = 0ull;
 #pragma unroll
-            for (int dd = 0; dd < NDO; ++dd) acc = fmaf(Ds[k * NDO + dd], ps[dd], acc);
-            out[k * BV] = acc;
+                for (int k = 0; k < K; ++k) {
+                    const unsigned long long t2 = *reinterpret_cast<const unsigned long long*>(tr + k * BX + spair);
+                    acc = ffma2(m2[k], t2, acc);
+                }
+                float lo, hi;
+                f2unpack(acc, lo, hi);
+                q[2 * pp] = negx ? hi : lo;
+                q[2 * pp + 1] = negx ? lo : hi;
+            }
         }
+
+        // B: walk the line, every lane on the same cell; fluxes to Ps in storage x order
+        {
+            const bool lok = sy < nvy && sz < nvz;
+            const unsigned vm = lok ? vx : 0u;
+            float* yrow = fy + lz * BX * FS + lane;
+            float* zrow = fz + ly * BX * FS + lane;
+            const float* srow = sg + line * BX;
+            float* prow = Ps + (srcok ? bl : 0) * PSTR + d * BX;
+            float xin = fx[line * FS + lane];
+#pragma unroll
+            for (int lx = 0; lx < BX; ++lx) {
+                const float yin = yrow[lx * FS], zin = zrow[lx * FS];
+                float psi, ox, oy, oz;
+                if (vm >> lx & 1u) {
+                    const float qv = q[lx], sig = srow[lx];
+                    psi = __fdividef(qv + ax * xin + ay * yin + az * zin, sig + asum);
+                    ox = 2.f * psi - xin;
+                    oy = 2.f * psi - yin;
+                    oz = 2.f * psi - zin;
+                    const bool neg = ox < 0.f || oy < 0.f || oz < 0.f;
+                    if (__any_sync(0xffffffffu, neg) && neg) {
+                        bool fxd = false, fyd = false, fzd = false;
+#pragma unroll 1
+                        for (int pass = 0; pass < 3; ++pass) {
+                            const bool nx = !fxd && ox < 0.f, ny = !fyd && oy < 0.f, nz = !fzd && oz < 0.f;
+                            if (!(nx || ny || nz)) break;
+                            fxd |= nx;
+                            fyd |= ny;
+                            fzd |= nz;
+                            const float num = qv + (fxd ? 0.5f * ax : ax) * xin + (fyd ? 0.5f * ay : ay) * yin +
+                                              (fzd ? 0.5f * az : az) * zin;
+                            const float den = sig + (fxd ? 0.f : ax) + (fyd ? 0.f : ay) + (fzd ? 0.f : az);
+                            psi = __fdividef(num, den);
+                            ox = fxd ? 0.f : 2.f * psi - xin;
+                            oy = fyd ? 0.f : 2.f * psi - yin;
+                            oz = fzd ? 0.f : 2.f * psi - zin;
+                        }
+                    }
+                } else {
+                    psi = 0.f;
+                    ox = xin;
+                    oy = yin;
+                    oz = zin;
+                }
+                if (srcok) prow[negx ? BX - 1 - lx : lx] = psi;
+                yrow[lx * FS] = oy;
+                zrow[lx * FS] = oz;
+                xin = ox;
+            }
+            fx[line * FS + lane] = xin;
+        }
+        __syncwarp();
+
+        // C: lane = (source, moment): octant moment partial of the line, two cells per FMA
+#pragma unroll
+        for (int r = 0; r < CR; ++r) {
+            const int lc = lane + 32 * r;
+            const int il = lc / K, kc = lc - il * K;
+            if (lc < NCP && il < nb && (okmask >> il & 1u)) {
+                const float* pr = Ps + il * PSTR;
+                float* out = p.part + (((size_t)oct * BB + b0 + il) * p.NT + tile) * (size_t)(K * BV) +
+                             (size_t)kc * BV + (sz * BY + sy) * BX;
+#pragma unroll
+                for (int pp = 0; pp < BX / 2; ++pp) {
+                    unsigned long long acc = 0ull;
+#pragma unroll
+                    for (int dd = 0; dd < NDO; ++dd) {
+                        const unsigned long long s2 = *reinterpret_cast<const unsigned long long*>(pr + dd * BX + 2 * pp);
+                        acc = ffma2(dc[r][dd], s2, acc);
+                    }
+                    *reinterpret_cast<unsigned long long*>(out + 2 * pp) = acc;
+                }
+            }
+        }
+        __syncwarp();
     }
+
     // outgoing faces; those leaving the grid are the leakage
     const bool lbx = negx ? tx == 0 : tx == p.NTx - 1;
     const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
     const bool lbz = negz ? tz == 0 : tz == p.NTz - 1;
-    faces_out<NDO, fxn, SB>(fx, gx, sx_, nb, okmask, lbx, Lws, 0, leak_sh, mapx);
-    faces_out<NDO, fyn, SB>(fy, gy, sy_, nb, okmask, lby, Lws, 1, leak_sh, mapy);
-    faces_out<NDO, fzn, SB>(fz, gz, sz_, nb, okmask, lbz, Lws, 2, leak_sh, mapz);
+#define DTS_FACES_OUT(SH, G, STR, F, LEAVE, AXIS, MAP)                                             \
+    for (int j = lane; j < nb * NDO * F; j += 32) {                                               \
+        const int il = j / (NDO * F), rem = j - il * (NDO * F), dd = rem / F, e = rem - dd * F;  \
+        if (!(okmask >> il & 1u)) continue;                                                       \
+        const float v = SH[MAP(e) * FS + il * NDO + dd];                                          \
+        G[(size_t)il * STR + rem] = v;                                                            \
+        if ((LEAVE) && v != 0.f) atomicAdd(&leak_sh[il], Lws[dd * 3 + AXIS] * (double)v);        \
+    }
+    DTS_FACES_OUT(fx, gx, sxs, fxn, lbx, 0, mapx)
+    DTS_FACES_OUT(fy, gy, sys, fyn, lby, 1, mapy)
+    DTS_FACES_OUT(fz, gz, szs, fzn, lbz, 2, mapz)
+#undef DTS_FACES_OUT
     if (lbx || lby || lbz) {
         __syncwarp();
         if (lane < nb && (okmask >> lane & 1u) && leak_sh[lane] != 0.0) atomicAdd(&p.leak[b0 + lane], leak_sh[lane]);
@@ -864,6 +941,85 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedParams<R> p)
             *ph = 0.0;
 #pragma unroll
             for (int k = 0; k < K; ++k) T[(size_t)k * p.TV] = R(0);
+        }
+    }
+    ds = block_sum(ds, red);
+    ns = block_sum(ns, red);
+    sr = block_sum(sr, red);
+    ab = block_sum(ab, red);
+    if (threadIdx.x == 0) {
+        double* o = p.blk + ((size_t)b * gridDim.x + blockIdx.x) * 4;
+        o[0] = ds;
+        o[1] = ns;
+        o[2] = sr;
+        o[3] = ab;
+    }
+}
+
+// The same reduction for FP32 sweeps, four consecutive cells per thread with
+// 16-byte loads and stores (tile volumes that are multiples of 4).
+template <int K>
+__global__ void __launch_bounds__(kRedThreads) k_reduce4(const RedParams<float> p)
+{
+    __shared__ double red[32];
+    const int b = blockIdx.y;
+    const int c4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    double ds = 0.0, ns = 0.0, sr = 0.0, ab = 0.0;
+    if (p.active[b] != 0 && c4 < p.NC) {
+        const int tile = c4 / p.TV, c = c4 - tile * p.TV;
+        const size_t base = ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
+        const size_t ostride = (size_t)p.B * p.NT * K * p.TV;
+        const float* __restrict__ pp = p.part + base;
+        float* __restrict__ T = p.T + base;
+        const float* __restrict__ F = p.F + (size_t)p.ctl[1] * p.Fstride + base;
+        double* __restrict__ ph = p.phi00 + (size_t)b * p.NC + c4;
+        const int4 m4 = *reinterpret_cast<const int4*>(p.mat_t + c4);
+        const int mm[4] = {m4.x, m4.y, m4.z, m4.w};
+        double s0[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            const float4 v = *reinterpret_cast<const float4*>(pp + o * ostride);
+            s0[0] += (double)v.x;
+            s0[1] += (double)v.y;
+            s0[2] += (double)v.z;
+            s0[3] += (double)v.w;
+        }
+        const float4 f0 = *reinterpret_cast<const float4*>(F);
+        const float ff[4] = {f0.x, f0.y, f0.z, f0.w};
+        float t0[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (mm[j] < 0) {
+                s0[j] = 0.0;
+                t0[j] = 0.f;
+                continue;
+            }
+            const double old = ph[j], sl0 = p.sigs0[c4 + j], fj = (double)ff[j];
+            const double dd = s0[j] - old;
+            ds += dd * dd;
+            ns += s0[j] * s0[j];
+            ab += p.vol * p.sigt64[c4 + j] * s0[j];
+            sr += p.vol * (fj + sl0 * old);
+            t0[j] = (float)(fj + sl0 * s0[j]);
+        }
+        *reinterpret_cast<double2*>(ph) = make_double2(s0[0], s0[1]);
+        *reinterpret_cast<double2*>(ph + 2) = make_double2(s0[2], s0[3]);
+        *reinterpret_cast<float4*>(T) = make_float4(t0[0], t0[1], t0[2], t0[3]);
+#pragma unroll
+        for (int k = 1; k < K; ++k) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const float4 v = *reinterpret_cast<const float4*>(pp + o * ostride + (size_t)k * p.TV);
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+            }
+            const float4 f = *reinterpret_cast<const float4*>(F + (size_t)k * p.TV);
+            const float4 sl = *reinterpret_cast<const float4*>(p.sigs + (size_t)l_of_k(k) * p.NC + c4);
+            *reinterpret_cast<float4*>(T + (size_t)k * p.TV) =
+                make_float4(f.x + sl.x * acc.x, f.y + sl.y * acc.y, f.z + sl.z * acc.z, f.w + sl.w * acc.w);
         }
     }
     ds = block_sum(ds, red);

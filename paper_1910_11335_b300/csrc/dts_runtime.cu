@@ -346,12 +346,36 @@ template <int NDO, int BX>
 SweepFn<float> batch_fn_k(int K)
 {
     switch (K) {
-    case 1: return k_sweep_batch<NDO, 1, BX, 4, 4>;
-    case 4: return k_sweep_batch<NDO, 4, BX, 4, 4>;
-    case 9: return k_sweep_batch<NDO, 9, BX, 4, 4>;
-    case 16: return k_sweep_batch<NDO, 16, BX, 4, 4>;
+    case 1: return k_sweep_batch<NDO, 1, BX>;
+    case 4: return k_sweep_batch<NDO, 4, BX>;
+    case 9: return k_sweep_batch<NDO, 9, BX>;
+    case 16: return k_sweep_batch<NDO, 16, BX>;
     }
     return nullptr;
+}
+
+template <int NDO, int BX>
+size_t batch_smem_k(int K)
+{
+    switch (K) {
+    case 1: return sweep_batch_smem<NDO, 1, BX>();
+    case 4: return sweep_batch_smem<NDO, 4, BX>();
+    case 9: return sweep_batch_smem<NDO, 9, BX>();
+    case 16: return sweep_batch_smem<NDO, 16, BX>();
+    }
+    return 0;
+}
+
+template <int BX>
+size_t batch_smem_x(int ndo, int K)
+{
+    switch (ndo) {
+    case 1: return batch_smem_k<1, BX>(K);
+    case 3: return batch_smem_k<3, BX>(K);
+    case 6: return batch_smem_k<6, BX>(K);
+    case 10: return batch_smem_k<10, BX>(K);
+    }
+    return 0;
 }
 
 template <int BX>
@@ -394,10 +418,20 @@ RedFn<R> reduce_fn(int K)
     return nullptr;
 }
 
+RedFn<float> reduce4_fn(int K)
+{
+    switch (K) {
+    case 1: return k_reduce4<1>;
+    case 4: return k_reduce4<4>;
+    case 9: return k_reduce4<9>;
+    case 16: return k_reduce4<16>;
+    }
+    return nullptr;
+}
+
 size_t sweep_smem(const dts_problem* p)
 {
-    if (batch_tile(p))
-        return p->TX == 8 ? sweep_batch_smem<8, 4, 4>(p->ndo, p->K) : sweep_batch_smem<4, 4, 4>(p->ndo, p->K);
+    if (batch_tile(p)) return p->TX == 8 ? batch_smem_x<8>(p->ndo, p->K) : batch_smem_x<4>(p->ndo, p->K);
     const int xfaces = line_tile(p) ? 32 : p->TY * p->TZ;
     const size_t n = (size_t)p->ndo * p->TV +
                      (size_t)p->ndo * (xfaces + p->TX * p->TZ + p->TX * p->TY) + p->TV +
@@ -468,9 +502,19 @@ dts_status record_reduce(dts_problem* p)
     rp.sigt64 = p->sigt64;
     rp.mat_t = p->mat_t; rp.active = p->active; rp.vol = p->d.dx * p->d.dy * p->d.dz;
     rp.blk = p->blk;
-    RedFn<R> rf = reduce_fn<R>(p->K);
-    rf<<<dim3(p->nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
-    k_resid_final<<<p->B, 256, 0, p->stream>>>(p->blk, p->nblk, p->leak, p->status);
+    int nblk = p->nblk;
+    if constexpr (sizeof(R) == 4) {
+        if (p->TV % 4 == 0) {   // four cells per thread
+            nblk = (p->NC / 4 + kRedThreads - 1) / kRedThreads;
+            RedFn<float> rf4 = reduce4_fn(p->K);
+            rf4<<<dim3(nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
+        } else {
+            reduce_fn<R>(p->K)<<<dim3(nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
+        }
+    } else {
+        reduce_fn<R>(p->K)<<<dim3(nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
+    }
+    k_resid_final<<<p->B, 256, 0, p->stream>>>(p->blk, nblk, p->leak, p->status);
     p->graph_launches = p->n_stages + 2;
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(double) * 4 * p->B, cudaMemcpyDeviceToHost,
                        p->stream));
