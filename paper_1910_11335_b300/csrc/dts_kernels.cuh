@@ -557,14 +557,17 @@ k_sweep_lines(const SweepParams<R> p, const int stage)
 // Lane = (source, direction) pair, e.g. 3 sources x 10 directions for S8, so
 // all lanes solve the same cell at the same time: the warp walks the tile in
 // upwind order (the sub-sweeps of Sec. II.B reduce to a lexicographic walk
-// inside one warp), the x-face stays in a register and the y/z faces sit in
-// per-lane shared-memory columns updated in place. The tile is processed one
-// x-line at a time: the line's source moments arrive by cp.async one line
-// ahead, are contracted to the lanes' directions, swept, and reduced to
-// octant moment partials, so shared memory holds one line of sources and
-// fluxes rather than the whole tile. The contractions use packed FP32x2 FMA
-// (two directions, or two moments, per instruction; each half rounds like
-// fmaf). Padding cells pass faces through.
+// inside one warp). Each lane's sweep is independent of the others; the x-face
+// stays in a register, the y-faces of a z-column of lines stay in registers,
+// and the z-faces sit in per-lane shared-memory slots. The tile is processed
+// one x-line at a time: the line's source moments arrive by cp.async one line
+// ahead, are contracted to the lanes' directions (A3), swept (A4), and reduced
+// to octant moment partials by lanes re-assigned to (moment, cell quad) pairs,
+// so shared memory holds one line of sources and fluxes rather than the whole
+// tile. Both contractions use packed FP32x2 FMA over pairs of cells fed by
+// 16-byte shared loads (each half rounds like fmaf). Padding cells pass faces
+// through. Faces between tiles live in octant-local lane-major blocks, so a
+// tile's incoming faces are a flat copy of what its upstream neighbour wrote.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long f2pack(float lo, float hi)
 {
@@ -596,35 +599,120 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 
 template <int NDO, int K, int BX>
 struct BatchShape {
-    static constexpr int BY = 4, BZ = 4, BV = BX * BY * BZ;
-    static constexpr int SB = 32 / NDO, NL = SB * NDO;
-    static constexpr int FS = 33;                       // odd lane stride >= 32: every lane owns a column
-    static constexpr int TSTR = K * BX + 8;             // staged source row per source (16-byte multiple)
-    static constexpr int PSTR = NDO * BX + 8;           // line fluxes per source, [NDO][BX] + pad
-    static constexpr int NC_ = SB * K;                  // (source, moment) pairs of phase C
+    static constexpr int BY = 4, BZ = 4, BV = BX * BY * BZ, NLINE = BY * BZ;
+    static constexpr int SB = 32 / NDO, NL = SB * NDO;  // sources per warp, busy lanes
+    static constexpr int NQ = BX / 4;                   // 4-cell quads per line
+    static constexpr int TSTR = K * BX + 4;             // staged moments of a source, [K][BX] + pad
+    static constexpr int PSTR = NDO * BX + 4;           // line fluxes of a source, [NDO][BX] + pad
+    static constexpr int NH = 32 / K;                   // phase-C lane groups (lane = moment + K * group)
+    static constexpr int NITEM = SB * NQ;               // phase-C (source, quad) items per line
+    static constexpr int NJ = (NITEM + NH - 1) / NH;    // items per lane group
+    static constexpr int NCP = (SB * K * NQ + 31) / 32; // 16-byte cp.async chunks per lane per line
+    static constexpr bool PRE_CP = NCP <= 4, PRE_C = NJ <= 4;   // keep per-lane offsets in registers
     static constexpr int fxn = BY * BZ, fyn = BX * BZ, fzn = BX * BY;
     // float offsets
-    static constexpr int oT = 0;                        // [2][SB][TSTR] staged source moments
-    static constexpr int oP = oT + 2 * SB * TSTR;       // [SB][PSTR] line fluxes (storage x order)
-    static constexpr int oX = oP + SB * PSTR;           // [fxn][FS]
-    static constexpr int oY = oX + fxn * FS;            // [fyn][FS]
-    static constexpr int oZ = oY + fyn * FS;            // [fzn][FS]
-    static constexpr int oS = oZ + fzn * FS;            // [BV] sigma_t, local order
+    static constexpr int oT = 0;                        // [2][SB][TSTR]
+    static constexpr int oP = oT + 2 * SB * TSTR;       // [SB][PSTR]
+    static constexpr int oX = oP + SB * PSTR;           // [fxn][32] x faces, slot = local line
+    static constexpr int oY = oX + fxn * 32;            // [fyn][32] y faces, slot = lz * BX + lx
+    static constexpr int oZ = oY + fyn * 32;            // [fzn][32] z faces, slot = ly * BX + lx
+    static constexpr int oS = oZ + fzn * 32;            // [NLINE][BX] sigma_t, local line, storage x
     static constexpr int nF = (oS + BV + 3) & ~3;
-    static constexpr size_t bytes = sizeof(float) * nF + sizeof(double) * (3 * NDO + SB);
+    static constexpr size_t bytes = sizeof(float) * nF + sizeof(double) * SB;
 };
 
 template <int NDO, int K, int BX>
 __host__ __device__ constexpr size_t sweep_batch_smem() { return BatchShape<NDO, K, BX>::bytes; }
 
-template <int NDO, int K, int BX>
-__global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float> p, const int stage)
+// Face buffers of the batched kernel: per (octant, source group, tile column)
+// one block of F slots x 32 lanes, in the octant-local frame of the sweep.
+__host__ __device__ inline size_t batch_face_floats(int n_groups, int columns, int F)
+{
+    return (size_t)8 * n_groups * columns * F * 32;
+}
+
+template <int F>
+__device__ __forceinline__ void batch_faces_in(float* sh, const float* g, bool upstream)
+{
+    for (int j = threadIdx.x; j < F * 8; j += 32) {
+        const float4 v = upstream ? *reinterpret_cast<const float4*>(g + 4 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(sh + 4 * j) = v;
+    }
+}
+
+template <int F>
+__device__ __forceinline__ void batch_faces_out(const float* sh, float* g)
+{
+    for (int j = threadIdx.x; j < F * 8; j += 32)
+        *reinterpret_cast<float4*>(g + 4 * j) = *reinterpret_cast<const float4*>(sh + 4 * j);
+}
+
+// Set-to-zero fixup of one cell (FP32), entered with the plain diamond-
+// difference result: faces found negative are fixed at zero and enter the
+// balance with half weight; at most three passes.
+__device__ __forceinline__ void batch_fixup(float qv, float sig, float ax, float ay, float az, float xin,
+                                            float yin, float zin, float& psi, float& ox, float& oy, float& oz)
+{
+    bool fxd = false, fyd = false, fzd = false;
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+        const bool nx = !fxd && ox < 0.f, ny = !fyd && oy < 0.f, nz = !fzd && oz < 0.f;
+        if (!(nx || ny || nz)) break;
+        fxd |= nx;
+        fyd |= ny;
+        fzd |= nz;
+        const float num = qv + (fxd ? 0.5f * ax : ax) * xin + (fyd ? 0.5f * ay : ay) * yin +
+                          (fzd ? 0.5f * az : az) * zin;
+        const float den = sig + (fxd ? 0.f : ax) + (fyd ? 0.f : ay) + (fzd ? 0.f : az);
+        psi = __fdividef(num, den);
+        ox = fxd ? 0.f : 2.f * psi - xin;
+        oy = fyd ? 0.f : 2.f * psi - yin;
+        oz = fzd ? 0.f : 2.f * psi - zin;
+    }
+}
+
+// One x-line of phase B. Cells in upwind (local) order lx; q and psi in
+// storage x order sx. CHECK: the line has padding cells (mask vm over sx).
+template <int BX, bool NX, bool CHECK>
+__device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], float* zrow, const float* srow,
+                                           float& xin, unsigned vm, float ax, float ay, float az, float asum)
+{
+#pragma unroll
+    for (int lx = 0; lx < BX; ++lx) {
+        const int sx = NX ? BX - 1 - lx : lx;
+        const float yin = yv[lx], zin = zrow[lx * 32];
+        float psi, ox, oy, oz;
+        if (!CHECK || (vm >> sx & 1u)) {
+            const float q = qv[sx], sig = srow[sx];
+            psi = __fdividef(fmaf(ax, xin, fmaf(ay, yin, fmaf(az, zin, q))), sig + asum);
+            ox = fmaf(2.f, psi, -xin);
+            oy = fmaf(2.f, psi, -yin);
+            oz = fmaf(2.f, psi, -zin);
+            const bool neg = fminf(ox, fminf(oy, oz)) < 0.f;
+            if (__any_sync(0xffffffffu, neg)) {
+                if (neg) batch_fixup(q, sig, ax, ay, az, xin, yin, zin, psi, ox, oy, oz);
+            }
+        } else {
+            psi = 0.f;
+            ox = xin;
+            oy = yin;
+            oz = zin;
+        }
+        qv[sx] = psi;
+        yv[lx] = oy;
+        zrow[lx * 32] = oz;
+        xin = ox;
+    }
+}
+
+template <int NDO, int K, int BX, bool NX>
+__device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, const int oct, const int grp,
+                                                 const int ta, const int tb, const int tc, const unsigned okmask)
 {
     using S = BatchShape<NDO, K, BX>;
-    constexpr int BY = S::BY, BZ = S::BZ, BV = S::BV, SB = S::SB, NL = S::NL, FS = S::FS;
-    constexpr int TSTR = S::TSTR, PSTR = S::PSTR, NCP = S::NC_;
+    constexpr int BY = S::BY, BZ = S::BZ, BV = S::BV, SB = S::SB, NL = S::NL, NQ = S::NQ;
+    constexpr int TSTR = S::TSTR, PSTR = S::PSTR, NH = S::NH, NJ = S::NJ, NCP = S::NCP;
     constexpr int fxn = S::fxn, fyn = S::fyn, fzn = S::fzn;
-    constexpr int CR = (NCP + 31) / 32;                 // rounds of phase C
     extern __shared__ __align__(16) float smf[];
     float* Tst = smf + S::oT;
     float* Ps = smf + S::oP;
@@ -632,247 +720,243 @@ __global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float>
     float* fy = smf + S::oY;
     float* fz = smf + S::oZ;
     float* sg = smf + S::oS;
-    double* Lws = reinterpret_cast<double*>(smf + S::nF);
-    double* leak_sh = Lws + 3 * NDO;
+    double* leak_sh = reinterpret_cast<double*>(smf + S::nF);
 
-    const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
-    int bid = blockIdx.x;
-    const int tl = bid % cnt;
-    bid /= cnt;
-    const int oct = bid & 7, b0 = (bid >> 3) * SB;
     const int lane = threadIdx.x;
-    const int nb = min(SB, p.B - b0);
-    unsigned okmask = 0;                           // sources of this warp still iterating
-    for (int i = 0; i < nb; ++i)
-        if (p.active[b0 + i]) okmask |= 1u << i;
-    if (okmask == 0) return;
-
-    const unsigned pk = p.stage_tiles[s0 + tl];
-    const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
-    const bool negx = oct & 1, negy = oct & 2, negz = oct & 4;
-    const int tx = negx ? p.NTx - 1 - ta : ta;
+    const int b0 = grp * SB, nb = min(SB, p.B - b0);
+    const int ngrp = (p.B + SB - 1) / SB;
+    const bool negy = oct & 2, negz = oct & 4;
+    const int tx = NX ? p.NTx - 1 - ta : ta;
     const int ty = negy ? p.NTy - 1 - tb : tb;
     const int tz = negz ? p.NTz - 1 - tc : tc;
     const int tile = (tz * p.NTy + ty) * p.NTx + tx;
     const int n0 = oct * NDO;
-    const size_t BB = p.B;
+    const int NTKB = p.NT * K * BV;                 // stride between sources (fits: checked on the host)
     const float* Tbase = p.T + ((size_t)b0 * p.NT + tile) * (size_t)(K * BV);
-    const size_t Tsrc = (size_t)p.NT * K * BV;     // stride between sources
+    float* obase = p.part + (((size_t)oct * p.B + b0) * p.NT + tile) * (size_t)(K * BV);
 
+    // cp.async chunks of one line: u -> (source il, moment k, quad h)
+    auto chunk = [&](int c, int& src, int& dst) {
+        const int u = lane + 32 * c;
+        const int il = u / (K * NQ), r = u - il * (K * NQ), k = r / NQ, h = r - k * NQ;
+        const bool ok = u < SB * K * NQ && il < nb && (okmask >> il & 1u);
+        src = ok ? il * NTKB + k * BV + 4 * h : -1;
+        dst = il * TSTR + k * BX + 4 * h;
+    };
+    int csrc[S::PRE_CP ? NCP : 1], cdst[S::PRE_CP ? NCP : 1];
+    if constexpr (S::PRE_CP) {
+#pragma unroll
+        for (int c = 0; c < NCP; ++c) chunk(c, csrc[c], cdst[c]);
+    }
     auto stage_line = [&](int line, int buf) {
         const int ly = line % BY, lz = line / BY;
         const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
         const int lbase = (sz * BY + sy) * BX;
-        constexpr int CH = BX / 4;                 // 16-byte chunks per (source, moment) row
-        for (int u = lane; u < nb * K * CH; u += 32) {
-            const int il = u / (K * CH), r = u - il * (K * CH), k = r / CH, h = r - k * CH;
-            if (!(okmask >> il & 1u)) continue;
-            cp_async16(Tst + (buf * SB + il) * TSTR + k * BX + h * 4,
-                       Tbase + il * Tsrc + (size_t)k * BV + lbase + h * 4);
+        float* dbase = Tst + buf * SB * TSTR;
+#pragma unroll
+        for (int c = 0; c < NCP; ++c) {
+            int src, dst;
+            if constexpr (S::PRE_CP) {
+                src = csrc[c];
+                dst = cdst[c];
+            } else {
+                chunk(c, src, dst);
+            }
+            if (src >= 0) cp_async16(dbase + dst, Tbase + src + lbase);
         }
         cp_async_commit();
     };
     stage_line(0, 0);
 
-    // phase-B / phase-A lane: (source bl, direction d); its contraction row of M in registers
+    // phase A/B lane: (source bl, direction d)
     const int bl = lane / NDO, d = lane - bl * NDO;
-    const bool dlane = lane < NL;
+    const bool srcok = lane < NL && (okmask >> bl & 1u);
     float ax = 0.f, ay = 0.f, az = 0.f;
     unsigned long long m2[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float m = dlane ? p.M[(n0 + d) * K + k] : 0.f;
+        const float m = srcok ? p.M[(n0 + d) * K + k] : 0.f;
         m2[k] = f2pack(m, m);
     }
-    if (dlane) {
+    if (srcok) {
         ax = p.A[(n0 + d) * 3];
         ay = p.A[(n0 + d) * 3 + 1];
         az = p.A[(n0 + d) * 3 + 2];
     }
     const float asum = ax + ay + az;
-    // phase-C lanes: (source, moment) pairs; their row of D in registers
-    unsigned long long dc[CR][NDO];
+    const float* trow = Tst + (srcok ? bl : 0) * TSTR;
+    float* prow = Ps + (srcok ? bl : 0) * PSTR + d * BX;
+
+    // phase C lane: (moment kc, group h); items (source il, quad qd) = h + NH * j
+    const int kc = lane % K, hc = lane / K;
+    unsigned long long dk[NDO];
 #pragma unroll
-    for (int r = 0; r < CR; ++r) {
-        const int lc = lane + 32 * r, kc = lc % K;
-        const bool ok = lc < NCP;
+    for (int dd = 0; dd < NDO; ++dd) {
+        const float v = hc < NH ? p.Dt[(n0 + dd) * K + kc] : 0.f;
+        dk[dd] = f2pack(v, v);
+    }
+    auto citem = [&](int j, int& pofs, int& oofs) {
+        const int item = hc + NH * j;
+        const int il = item / NQ, qd = item - il * NQ;
+        const bool ok = hc < NH && item < S::NITEM && il < nb && (okmask >> il & 1u);
+        pofs = il * PSTR + 4 * qd;
+        oofs = ok ? il * NTKB + kc * BV + 4 * qd : -1;
+    };
+    int cp_[S::PRE_C ? NJ : 1], co_[S::PRE_C ? NJ : 1];
+    if constexpr (S::PRE_C) {
 #pragma unroll
-        for (int dd = 0; dd < NDO; ++dd) {
-            const float v = ok ? p.Dt[(n0 + dd) * K + kc] : 0.f;
-            dc[r][dd] = f2pack(v, v);
+        for (int j = 0; j < NJ; ++j) citem(j, cp_[j], co_[j]);
+    }
+
+    if (lane < SB) leak_sh[lane] = 0.0;
+    {
+        const float* st = p.sigt + (size_t)tile * BV;
+        for (int i = lane; i < BV / 4; i += 32) {
+            const int srow = i / NQ, h = i - srow * NQ;
+            const int sy = srow % BY, sz = srow / BY;
+            const int ly = negy ? BY - 1 - sy : sy, lz = negz ? BZ - 1 - sz : sz;
+            *reinterpret_cast<float4*>(sg + (lz * BY + ly) * BX + 4 * h) =
+                *reinterpret_cast<const float4*>(st + srow * BX + 4 * h);
         }
     }
-    for (int i = lane; i < 3 * NDO; i += 32) Lws[i] = p.Lw[n0 * 3 + i];
-    if (lane < SB) leak_sh[lane] = 0.0;
-    const float* st = p.sigt + (size_t)tile * BV;
-    for (int cs = lane; cs < BV; cs += 32) {
-        const int sx = cs % BX, sy = (cs / BX) % BY, sz = cs / (BX * BY);
-        sg[((negz ? BZ - 1 - sz : sz) * BY + (negy ? BY - 1 - sy : sy)) * BX + (negx ? BX - 1 - sx : sx)] = st[cs];
-    }
-
-    // incoming faces (zero on the grid boundary), storage -> local order, coalesced per source
-    const size_t sxs = (size_t)(p.NTy * p.NTz) * NDO * fxn, sys = (size_t)(p.NTx * p.NTz) * NDO * fyn,
-                 szs = (size_t)(p.NTx * p.NTy) * NDO * fzn;
-    float* gx = p.xf + (((size_t)oct * BB + b0) * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * (size_t)(NDO * fxn);
-    float* gy = p.yf + (((size_t)oct * BB + b0) * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * (size_t)(NDO * fyn);
-    float* gz = p.zf + (((size_t)oct * BB + b0) * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * (size_t)(NDO * fzn);
-    auto mapx = [&](int e) {
-        const int sy = e % BY, sz = e / BY;
-        return (negz ? BZ - 1 - sz : sz) * BY + (negy ? BY - 1 - sy : sy);
-    };
-    auto mapy = [&](int e) {
-        const int sx = e % BX, sz = e / BX;
-        return (negz ? BZ - 1 - sz : sz) * BX + (negx ? BX - 1 - sx : sx);
-    };
-    auto mapz = [&](int e) {
-        const int sx = e % BX, sy = e / BX;
-        return (negy ? BY - 1 - sy : sy) * BX + (negx ? BX - 1 - sx : sx);
-    };
-#define DTS_FACES_IN(SH, G, STR, F, UP, MAP)                                                       \
-    for (int j = lane; j < nb * NDO * F; j += 32) {                                               \
-        const int il = j / (NDO * F), rem = j - il * (NDO * F), dd = rem / F, e = rem - dd * F;  \
-        const bool ok = (UP) && (okmask >> il & 1u);                                              \
-        SH[MAP(e) * FS + il * NDO + dd] = ok ? G[(size_t)il * STR + rem] : 0.f;                   \
-    }
-    DTS_FACES_IN(fx, gx, sxs, fxn, ta > 0, mapx)
-    DTS_FACES_IN(fy, gy, sys, fyn, tb > 0, mapy)
-    DTS_FACES_IN(fz, gz, szs, fzn, tc > 0, mapz)
-#undef DTS_FACES_IN
+    const size_t og = (size_t)oct * ngrp + grp;
+    float* gx = p.xf + ((og * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * fxn) * 32;
+    float* gy = p.yf + ((og * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * fyn) * 32;
+    float* gz = p.zf + ((og * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * fzn) * 32;
+    batch_faces_in<fxn>(fx, gx, ta > 0);
+    batch_faces_in<fyn>(fy, gy, tb > 0);
+    batch_faces_in<fzn>(fz, gz, tc > 0);
 
     const int nvx = p.nx - tx * BX, nvy = p.ny - ty * BY, nvz = p.nz - tz * BZ;
-    unsigned vx = 0;
-#pragma unroll
-    for (int lx = 0; lx < BX; ++lx)
-        if ((negx ? BX - 1 - lx : lx) < nvx) vx |= 1u << lx;
-    const bool srcok = dlane && (okmask >> bl & 1u);
+    constexpr unsigned FULL = (1u << BX) - 1u;
+    const unsigned vxs = nvx >= BX ? FULL : (1u << nvx) - 1u;   // valid cells, storage x bits
+    float yv[BX];
 
 #pragma unroll 1
-    for (int line = 0; line < BY * BZ; ++line) {
+    for (int line = 0; line < S::NLINE; ++line) {
         const int buf = line & 1;
-        if (line + 1 < BY * BZ) stage_line(line + 1, buf ^ 1);
+        if (line + 1 < S::NLINE) stage_line(line + 1, buf ^ 1);
         else cp_async_commit();
         cp_async_wait1();
         __syncwarp();
         const int ly = line % BY, lz = line / BY;
         const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
 
-        // A: this lane's sources for the line's cells, two cells per FMA, in local x order
-        float q[BX];
+        // A: Q for the line's cells, two cells per packed FMA, storage x order
+        float qv[BX];
         {
-            const float* tr = Tst + (buf * SB + (srcok ? bl : 0)) * TSTR;
+            const float* tr = trow + buf * SB * TSTR;
 #pragma unroll
-            for (int pp = 0; pp < BX / 2; ++pp) {
-                const int spair = negx ? BX - 2 - 2 * pp : 2 * pp;   // storage pair of local (2pp, 2pp+1)
-                unsigned long long acc = 0ull;
+            for (int qd = 0; qd < NQ; ++qd) {
+                unsigned long long a0 = 0ull, a1 = 0ull;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    const unsigned long long t2 = *reinterpret_cast<const unsigned long long*>(tr + k * BX + spair);
-                    acc = ffma2(m2[k], t2, acc);
+                    const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(tr + k * BX + 4 * qd);
+                    a0 = ffma2(m2[k], t.x, a0);
+                    a1 = ffma2(m2[k], t.y, a1);
                 }
-                float lo, hi;
-                f2unpack(acc, lo, hi);
-                q[2 * pp] = negx ? hi : lo;
-                q[2 * pp + 1] = negx ? lo : hi;
+                f2unpack(a0, qv[4 * qd], qv[4 * qd + 1]);
+                f2unpack(a1, qv[4 * qd + 2], qv[4 * qd + 3]);
             }
         }
 
-        // B: walk the line, every lane on the same cell; fluxes to Ps in storage x order
-        {
-            const bool lok = sy < nvy && sz < nvz;
-            const unsigned vm = lok ? vx : 0u;
-            float* yrow = fy + lz * BX * FS + lane;
-            float* zrow = fz + ly * BX * FS + lane;
-            const float* srow = sg + line * BX;
-            float* prow = Ps + (srcok ? bl : 0) * PSTR + d * BX;
-            float xin = fx[line * FS + lane];
+        // B: walk the line
+        if (ly == 0) {
 #pragma unroll
-            for (int lx = 0; lx < BX; ++lx) {
-                const float yin = yrow[lx * FS], zin = zrow[lx * FS];
-                float psi, ox, oy, oz;
-                if (vm >> lx & 1u) {
-                    const float qv = q[lx], sig = srow[lx];
-                    psi = __fdividef(qv + ax * xin + ay * yin + az * zin, sig + asum);
-                    ox = 2.f * psi - xin;
-                    oy = 2.f * psi - yin;
-                    oz = 2.f * psi - zin;
-                    const bool neg = ox < 0.f || oy < 0.f || oz < 0.f;
-                    if (__any_sync(0xffffffffu, neg) && neg) {
-                        bool fxd = false, fyd = false, fzd = false;
-#pragma unroll 1
-                        for (int pass = 0; pass < 3; ++pass) {
-                            const bool nx = !fxd && ox < 0.f, ny = !fyd && oy < 0.f, nz = !fzd && oz < 0.f;
-                            if (!(nx || ny || nz)) break;
-                            fxd |= nx;
-                            fyd |= ny;
-                            fzd |= nz;
-                            const float num = qv + (fxd ? 0.5f * ax : ax) * xin + (fyd ? 0.5f * ay : ay) * yin +
-                                              (fzd ? 0.5f * az : az) * zin;
-                            const float den = sig + (fxd ? 0.f : ax) + (fyd ? 0.f : ay) + (fzd ? 0.f : az);
-                            psi = __fdividef(num, den);
-                            ox = fxd ? 0.f : 2.f * psi - xin;
-                            oy = fyd ? 0.f : 2.f * psi - yin;
-                            oz = fzd ? 0.f : 2.f * psi - zin;
-                        }
-                    }
-                } else {
-                    psi = 0.f;
-                    ox = xin;
-                    oy = yin;
-                    oz = zin;
-                }
-                if (srcok) prow[negx ? BX - 1 - lx : lx] = psi;
-                yrow[lx * FS] = oy;
-                zrow[lx * FS] = oz;
-                xin = ox;
-            }
-            fx[line * FS + lane] = xin;
+            for (int lx = 0; lx < BX; ++lx) yv[lx] = fy[(lz * BX + lx) * 32 + lane];
+        }
+        {
+            const unsigned vm = (sy < nvy && sz < nvz) ? vxs : 0u;
+            float* zrow = fz + ly * BX * 32 + lane;
+            const float* srow = sg + line * BX;
+            float xin = fx[line * 32 + lane];
+            if (vm == FULL) batch_line<BX, NX, false>(qv, yv, zrow, srow, xin, vm, ax, ay, az, asum);
+            else batch_line<BX, NX, true>(qv, yv, zrow, srow, xin, vm, ax, ay, az, asum);
+            fx[line * 32 + lane] = xin;
+        }
+        if (ly == BY - 1) {
+#pragma unroll
+            for (int lx = 0; lx < BX; ++lx) fy[(lz * BX + lx) * 32 + lane] = yv[lx];
+        }
+        if (srcok) {
+#pragma unroll
+            for (int qd = 0; qd < NQ; ++qd)
+                *reinterpret_cast<float4*>(prow + 4 * qd) =
+                    make_float4(qv[4 * qd], qv[4 * qd + 1], qv[4 * qd + 2], qv[4 * qd + 3]);
         }
         __syncwarp();
 
-        // C: lane = (source, moment): octant moment partial of the line, two cells per FMA
+        // C: lane = (moment, item): octant moment partial of four cells, two per packed FMA
+        {
+            const int lofs = (sz * BY + sy) * BX;
 #pragma unroll
-        for (int r = 0; r < CR; ++r) {
-            const int lc = lane + 32 * r;
-            const int il = lc / K, kc = lc - il * K;
-            if (lc < NCP && il < nb && (okmask >> il & 1u)) {
-                const float* pr = Ps + il * PSTR;
-                float* out = p.part + (((size_t)oct * BB + b0 + il) * p.NT + tile) * (size_t)(K * BV) +
-                             (size_t)kc * BV + (sz * BY + sy) * BX;
-#pragma unroll
-                for (int pp = 0; pp < BX / 2; ++pp) {
-                    unsigned long long acc = 0ull;
+            for (int j = 0; j < NJ; ++j) {
+                int pofs, oofs;
+                if constexpr (S::PRE_C) {
+                    pofs = cp_[j];
+                    oofs = co_[j];
+                } else {
+                    citem(j, pofs, oofs);
+                }
+                if (oofs >= 0) {
+                    const float* pr = Ps + pofs;
+                    unsigned long long a0 = 0ull, a1 = 0ull;
 #pragma unroll
                     for (int dd = 0; dd < NDO; ++dd) {
-                        const unsigned long long s2 = *reinterpret_cast<const unsigned long long*>(pr + dd * BX + 2 * pp);
-                        acc = ffma2(dc[r][dd], s2, acc);
+                        const ulonglong2 s2 = *reinterpret_cast<const ulonglong2*>(pr + dd * BX);
+                        a0 = ffma2(dk[dd], s2.x, a0);
+                        a1 = ffma2(dk[dd], s2.y, a1);
                     }
-                    *reinterpret_cast<unsigned long long*>(out + 2 * pp) = acc;
+                    *reinterpret_cast<ulonglong2*>(obase + oofs + lofs) = make_ulonglong2(a0, a1);
                 }
             }
         }
         __syncwarp();
     }
 
-    // outgoing faces; those leaving the grid are the leakage
-    const bool lbx = negx ? tx == 0 : tx == p.NTx - 1;
+    // outgoing faces; the lane's own faces leaving the grid are its leakage
+    batch_faces_out<fxn>(fx, gx);
+    batch_faces_out<fyn>(fy, gy);
+    batch_faces_out<fzn>(fz, gz);
+    const bool lbx = NX ? tx == 0 : tx == p.NTx - 1;
     const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
     const bool lbz = negz ? tz == 0 : tz == p.NTz - 1;
-#define DTS_FACES_OUT(SH, G, STR, F, LEAVE, AXIS, MAP)                                             \
-    for (int j = lane; j < nb * NDO * F; j += 32) {                                               \
-        const int il = j / (NDO * F), rem = j - il * (NDO * F), dd = rem / F, e = rem - dd * F;  \
-        if (!(okmask >> il & 1u)) continue;                                                       \
-        const float v = SH[MAP(e) * FS + il * NDO + dd];                                          \
-        G[(size_t)il * STR + rem] = v;                                                            \
-        if ((LEAVE) && v != 0.f) atomicAdd(&leak_sh[il], Lws[dd * 3 + AXIS] * (double)v);        \
-    }
-    DTS_FACES_OUT(fx, gx, sxs, fxn, lbx, 0, mapx)
-    DTS_FACES_OUT(fy, gy, sys, fyn, lby, 1, mapy)
-    DTS_FACES_OUT(fz, gz, szs, fzn, lbz, 2, mapz)
-#undef DTS_FACES_OUT
     if (lbx || lby || lbz) {
+        if (srcok) {
+            float sx_ = 0.f, sy_ = 0.f, sz_ = 0.f;
+            if (lbx)
+                for (int e = 0; e < fxn; ++e) sx_ += fx[e * 32 + lane];
+            if (lby)
+                for (int e = 0; e < fyn; ++e) sy_ += fy[e * 32 + lane];
+            if (lbz)
+                for (int e = 0; e < fzn; ++e) sz_ += fz[e * 32 + lane];
+            const double lk = p.Lw[(n0 + d) * 3] * (double)sx_ + p.Lw[(n0 + d) * 3 + 1] * (double)sy_ +
+                              p.Lw[(n0 + d) * 3 + 2] * (double)sz_;
+            if (lk != 0.0) atomicAdd(&leak_sh[bl], lk);
+        }
         __syncwarp();
         if (lane < nb && (okmask >> lane & 1u) && leak_sh[lane] != 0.0) atomicAdd(&p.leak[b0 + lane], leak_sh[lane]);
     }
+}
+
+template <int NDO, int K, int BX>
+__global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float> p, const int stage)
+{
+    constexpr int SB = BatchShape<NDO, K, BX>::SB;
+    const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
+    int bid = blockIdx.x;
+    const int tl = bid % cnt;
+    bid /= cnt;
+    const int oct = bid & 7, grp = bid >> 3, b0 = grp * SB;
+    const int nb = min(SB, p.B - b0);
+    unsigned okmask = 0;                           // sources of this warp still iterating
+    for (int i = 0; i < nb; ++i)
+        if (p.active[b0 + i]) okmask |= 1u << i;
+    if (okmask == 0) return;
+    const unsigned pk = p.stage_tiles[s0 + tl];
+    const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
+    if (oct & 1) sweep_batch_body<NDO, K, BX, true>(p, oct, grp, ta, tb, tc, okmask);
+    else sweep_batch_body<NDO, K, BX, false>(p, oct, grp, ta, tb, tc, okmask);
 }
 
 // Translation units that only launch the sweep define DTS_SWEEP_KERNEL_ONLY so

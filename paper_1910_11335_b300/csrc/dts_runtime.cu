@@ -746,6 +746,14 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
     return DTS_OK;
 }
 
+// the batched kernel addresses one warp's sources with 32-bit offsets
+bool batch_offsets_fit(const dts_problem* p, int tx, int ty, int tz)
+{
+    const size_t padded = (size_t)((p->d.nx + tx - 1) / tx * tx) * ((p->d.ny + ty - 1) / ty * ty) *
+                          ((p->d.nz + tz - 1) / tz * tz);
+    return (size_t)(32 / p->ndo) * padded * p->K < (size_t)INT_MAX;
+}
+
 void choose_tile(dts_problem* p)
 {
     if (p->d.tile_x > 0) {
@@ -759,7 +767,8 @@ void choose_tile(dts_problem* p)
     // batched kernel's 8 x 4 x 4 tile; otherwise 32 x-lines (4 in y, 8 in z)
     // per tile for the warp-synchronous kernel, 8 cells long in x (measured
     // fastest of 4..32 on the 96^3 S8 P3 batch)
-    const bool batched = p->d.precision == DTS_PREC_FP32 && p->d.batch >= 32 / p->ndo;
+    const bool batched = p->d.precision == DTS_PREC_FP32 && p->d.batch >= 32 / p->ndo &&
+                         batch_offsets_fit(p, 8, 4, 4);
     p->TX = 8;
     p->TY = 4;
     p->TZ = batched ? 4 : 8;
@@ -772,6 +781,8 @@ dts_status setup_schedule(dts_problem* p)
     p->NTx = (p->d.nx + p->TX - 1) / p->TX;
     p->NTy = (p->d.ny + p->TY - 1) / p->TY;
     p->NTz = (p->d.nz + p->TZ - 1) / p->TZ;
+    if (batch_tile(p) && !batch_offsets_fit(p, p->TX, p->TY, p->TZ))
+        return fail(p, DTS_ERR_INVALID_ARG, "grid too large for the batched 4 x 4 tiles; take an 8 x 4 x 8 tile");
     if (p->NTx > 1023 || p->NTy > 1023 || p->NTz > 1023)
         return fail(p, DTS_ERR_INVALID_ARG, "too many tiles along an axis (max 1023)");
     p->NT = p->NTx * p->NTy * p->NTz;
@@ -911,9 +922,18 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     TRY(dalloc(p, &p->T, B * NC * K * p->rsz));
     TRY(dalloc(p, &p->part, 8 * B * NC * K * p->rsz));
     const size_t nf = (size_t)p->ndo;
-    TRY(dalloc(p, &p->xf, 8 * B * (size_t)p->NTy * p->NTz * nf * p->TY * p->TZ * p->rsz));
-    TRY(dalloc(p, &p->yf, 8 * B * (size_t)p->NTx * p->NTz * nf * p->TX * p->TZ * p->rsz));
-    TRY(dalloc(p, &p->zf, 8 * B * (size_t)p->NTx * p->NTy * nf * p->TX * p->TY * p->rsz));
+    size_t fxs = 8 * B * (size_t)p->NTy * p->NTz * nf * p->TY * p->TZ * p->rsz;
+    size_t fys = 8 * B * (size_t)p->NTx * p->NTz * nf * p->TX * p->TZ * p->rsz;
+    size_t fzs = 8 * B * (size_t)p->NTx * p->NTy * nf * p->TX * p->TY * p->rsz;
+    if (batch_tile(p)) {   // lane-major blocks per source group
+        const int ngrp = (p->B + batch_sources_per_warp(p) - 1) / batch_sources_per_warp(p);
+        fxs = std::max(fxs, sizeof(float) * batch_face_floats(ngrp, p->NTy * p->NTz, p->TY * p->TZ));
+        fys = std::max(fys, sizeof(float) * batch_face_floats(ngrp, p->NTx * p->NTz, p->TX * p->TZ));
+        fzs = std::max(fzs, sizeof(float) * batch_face_floats(ngrp, p->NTx * p->NTy, p->TX * p->TY));
+    }
+    TRY(dalloc(p, &p->xf, fxs));
+    TRY(dalloc(p, &p->yf, fys));
+    TRY(dalloc(p, &p->zf, fzs));
     TRY(dalloc(p, &p->sigt_r, NC * p->rsz));
     TRY(dalloc_t(p, &p->sigt64, NC));
     TRY(dalloc(p, &p->sigs, NC * (p->L + 1) * p->rsz));
