@@ -1216,7 +1216,7 @@ __global__ void k_set_ctl(int* ctl, int g, int slot)
 // src rows: kind, pos[3], axis[3], half_angle.
 // ---------------------------------------------------------------------------
 struct RayParams {
-    int nx, ny, nz, V, G;
+    int nx, ny, nz, V, G, n_mat;
     double dx, dy, dz, x0, y0, z0;
     const int* mat;                // natural [V]
     const double* scale_t;         // natural [V] or null
@@ -1305,6 +1305,113 @@ __global__ void k_raytrace(const RayParams p, int g0)
     const double inv = 1.0 / (4.0 * kPi * r2);
     for (int gg = 0; gg < ng; ++gg)
         out[(size_t)gg * p.V] = p.spec[(size_t)b * p.G + g0 + gg] * exp(-tau[gg]) * inv;
+}
+
+// The same traversal for problems with at most kRayMats materials: each
+// thread accumulates the path length through every material (weighted by the
+// voxel's sigma_t scale) in shared memory, and every group's optical depth is
+// sum_m L_m sigma_t[m][g], so one pass serves all groups. The next crossing
+// parameter is formed with the reciprocal of the ray's direction component.
+constexpr int kRayMats = 8;
+constexpr int kRayThreads = 128;
+
+__global__ void __launch_bounds__(kRayThreads) k_raytrace_mat(const RayParams p)
+{
+    __shared__ double Ls[kRayMats][kRayThreads];
+    const int tid = threadIdx.x;
+    const int v = blockIdx.x * blockDim.x + tid;
+    const int b = blockIdx.y;
+    if (v >= p.V) return;
+#pragma unroll
+    for (int m = 0; m < kRayMats; ++m) Ls[m][tid] = 0.0;
+    const double* s = p.src + (size_t)b * 8;
+    double* out = p.unc + (size_t)b * p.G * p.V + v;
+    if (s[0] != 1.0) {
+        for (int g = 0; g < p.G; ++g) out[(size_t)g * p.V] = 0.0;
+        return;
+    }
+    const int cx = v % p.nx, cy = (v / p.nx) % p.ny, cz = v / (p.nx * p.ny);
+    const double Px = s[1], Py = s[2], Pz = s[3];
+    const double dx = p.x0 + (cx + 0.5) * p.dx - Px, dy = p.y0 + (cy + 0.5) * p.dy - Py,
+                 dz = p.z0 + (cz + 0.5) * p.dz - Pz;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double r = sqrt(r2);
+    const double an = sqrt(s[4] * s[4] + s[5] * s[5] + s[6] * s[6]);
+    const double cosang = (dx * s[4] + dy * s[5] + dz * s[6]) / (r * an);
+    if (s[7] < kPi && cosang < cos(s[7])) {
+        for (int g = 0; g < p.G; ++g) out[(size_t)g * p.V] = 0.0;
+        return;
+    }
+    // parameter where the segment P -> C enters the grid box
+    double a_in = 0.0;
+    auto enter = [&](double lo, int n, double h, double P, double d) {
+        if (d != 0.0) {
+            const double t0 = (lo - P) / d, t1 = (lo + n * h - P) / d;
+            a_in = fmax(a_in, fmin(t0, t1));
+        }
+    };
+    enter(p.x0, p.nx, p.dx, Px, dx);
+    enter(p.y0, p.ny, p.dy, Py, dy);
+    enter(p.z0, p.nz, p.dz, Pz, dz);
+    // per axis: voxel index, step, reciprocal direction and next crossing parameter
+    auto init = [&](double lo, int n, double h, double P, double d, int c, int& id, int& st, double& inv,
+                    double& tn) {
+        if (d == 0.0) {
+            id = c;
+            st = 0;
+            inv = 0.0;
+            tn = 2.0;
+            return;
+        }
+        int i0 = (int)floor((P + a_in * d - lo) / h);
+        id = i0 < 0 ? 0 : (i0 >= n ? n - 1 : i0);
+        st = d > 0.0 ? 1 : -1;
+        inv = 1.0 / d;
+        tn = (lo + (id + (d > 0.0 ? 1 : 0)) * h - P) * inv;
+    };
+    int ix, iy, iz, sx, sy, sz;
+    double ivx, ivy, ivz, tx, ty, tz;
+    init(p.x0, p.nx, p.dx, Px, dx, cx, ix, sx, ivx, tx);
+    init(p.y0, p.ny, p.dy, Py, dy, cy, iy, sy, ivy, ty);
+    init(p.z0, p.nz, p.dz, Pz, dz, cz, iz, sz, ivz, tz);
+    double acur = a_in;
+    const int max_steps = p.nx + p.ny + p.nz + 3;
+    for (int it = 0; it < max_steps; ++it) {
+        const int ax = (ty < tx) ? ((tz < ty) ? 2 : 1) : ((tz < tx) ? 2 : 0);
+        const double a1 = fmin(ax == 0 ? tx : ax == 1 ? ty : tz, 1.0);
+        const double seg = (a1 - acur) * r;
+        if (seg > 0.0) {
+            const int vv = (iz * p.ny + iy) * p.nx + ix;
+            const int m = p.mat[vv];
+            Ls[m][tid] += p.scale_t ? p.scale_t[vv] * seg : seg;
+        }
+        if (a1 >= 1.0) break;
+        acur = a1;
+        if (ax == 0) {
+            ix += sx;
+            if (ix < 0 || ix >= p.nx) break;
+            tx = (p.x0 + (ix + (sx > 0 ? 1 : 0)) * p.dx - Px) * ivx;
+        } else if (ax == 1) {
+            iy += sy;
+            if (iy < 0 || iy >= p.ny) break;
+            ty = (p.y0 + (iy + (sy > 0 ? 1 : 0)) * p.dy - Py) * ivy;
+        } else {
+            iz += sz;
+            if (iz < 0 || iz >= p.nz) break;
+            tz = (p.z0 + (iz + (sz > 0 ? 1 : 0)) * p.dz - Pz) * ivz;
+        }
+    }
+    double Lm[kRayMats];
+#pragma unroll
+    for (int m = 0; m < kRayMats; ++m) Lm[m] = Ls[m][tid];
+    const double inv = 1.0 / (4.0 * kPi * r2);
+    for (int g = 0; g < p.G; ++g) {
+        double tau = 0.0;
+#pragma unroll
+        for (int m = 0; m < kRayMats; ++m)
+            if (m < p.n_mat) tau += Lm[m] * p.sigma_t[(size_t)m * p.G + g];
+        out[(size_t)g * p.V] = p.spec[(size_t)b * p.G + g] * exp(-tau) * inv;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1415,6 +1522,97 @@ __global__ void k_push(const PushParams<R> p, int g)
                 R* f = p.F + (size_t)(g2 % W1) * p.Fstride + base + (size_t)k * c.TV;
                 *f = (R)((double)*f + sgm * ss * ph);
             }
+        }
+    }
+}
+
+// FP32 form with tiles a multiple of 4 cells long in x: one thread per
+// (4 consecutive cells, source), 16-byte loads and stores. The scalar flux is
+// summed in FP64 as above; each later group's fixed source takes the product
+// sigma_s * scale_s rounded to FP32 once per (cell, l, group) and an FP32 FMA
+// per moment.
+template <int K>
+__global__ void __launch_bounds__(256) k_push4(const PushParams<float> p, int g)
+{
+    const int c4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int b = blockIdx.y;
+    const CellParams& c = p.c;
+    if (c4 >= c.NC) return;
+    const int4 m4 = *reinterpret_cast<const int4*>(c.mat_t + c4);
+    const int mm[4] = {m4.x, m4.y, m4.z, m4.w};
+    if ((mm[0] & mm[1] & mm[2] & mm[3]) < 0) return;            // four padding cells
+    const int tile = c4 / c.TV, cc = c4 - tile * c.TV;
+    const size_t base = ((size_t)b * c.NT + tile) * (size_t)(K * c.TV) + cc;
+    const size_t ostride = (size_t)c.B * c.NT * K * c.TV;
+    const int v0 = tiled_to_natural(c, c4, nullptr);            // the 4 cells are x-consecutive
+    const int x0 = v0 % c.nx;
+    const int W1 = p.W + 1;
+    const int gmax = min(c.G - 1, g + p.W);
+    const int L1 = c.L + 1;
+    constexpr int LK = K == 1 ? 1 : K == 4 ? 2 : K == 9 ? 3 : 4;  // Legendre orders present
+    const int nw = gmax - g;
+    double ss[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ss[j] = c.scale_s_t ? c.scale_s_t[c4 + j] : 1.0;
+    float sc[4][LK][4];                                         // [g2 - g - 1][l][cell], W <= 4
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+        for (int l = 0; l < LK; ++l)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                sc[w][l][j] = (w >= nw || mm[j] < 0)
+                                  ? 0.f
+                                  : (float)(c.sigma_s[(((size_t)mm[j] * L1 + l) * c.G + g) * c.G + g + 1 + w] * ss[j]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float* pp = p.part + base + (size_t)k * c.TV;
+        double ph[4];
+        float4 s4;
+        if (k == 0) {
+            ph[0] = ph[1] = ph[2] = ph[3] = 0.0;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const float4 v = *reinterpret_cast<const float4*>(pp + o * ostride);
+                ph[0] += (double)v.x;
+                ph[1] += (double)v.y;
+                ph[2] += (double)v.z;
+                ph[3] += (double)v.w;
+            }
+            s4 = make_float4((float)ph[0], (float)ph[1], (float)ph[2], (float)ph[3]);
+        } else {
+            s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const float4 v = *reinterpret_cast<const float4*>(pp + o * ostride);
+                s4.x += v.x;
+                s4.y += v.y;
+                s4.z += v.z;
+                s4.w += v.w;
+            }
+            ph[0] = s4.x;
+            ph[1] = s4.y;
+            ph[2] = s4.z;
+            ph[3] = s4.w;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (mm[j] < 0 || x0 + j >= c.nx) continue;
+            if (k == 0) p.col[((size_t)b * c.G + g) * p.V + v0 + j] = ph[j];
+            if (p.mom) p.mom[(((size_t)b * c.G + g) * K + k) * p.V + v0 + j] = ph[j];
+        }
+        const int l = l_of_k(k);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            if (w >= nw) break;
+            float4* f = reinterpret_cast<float4*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base +
+                                                  (size_t)k * c.TV);
+            float4 fv = *f;
+            fv.x = fmaf(sc[w][l][0], s4.x, fv.x);
+            fv.y = fmaf(sc[w][l][1], s4.y, fv.y);
+            fv.z = fmaf(sc[w][l][2], s4.z, fv.z);
+            fv.w = fmaf(sc[w][l][3], s4.w, fv.w);
+            *f = fv;
         }
     }
 }

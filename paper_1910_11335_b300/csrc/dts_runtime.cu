@@ -610,6 +610,14 @@ void launch_push(dts_problem* p, int g)
     pp.c = cell_params(p);
     pp.part = (const R*)p->part; pp.F = (R*)p->F; pp.Fstride = p->Fstride; pp.W = p->W; pp.V = p->V;
     pp.col = p->col; pp.mom = p->d.keep_moments ? p->mom : nullptr;
+    if constexpr (sizeof(R) == 4) {
+        if (p->TX % 4 == 0 && p->W <= 4) {
+            using PushFn = void (*)(const PushParams<float>, int);
+            const PushFn f = p->K == 1 ? k_push4<1> : p->K == 4 ? k_push4<4> : p->K == 9 ? k_push4<9> : k_push4<16>;
+            f<<<dim3((p->NC / 4 + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g);
+            return;
+        }
+    }
     k_push<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g);
 }
 
@@ -627,9 +635,13 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         rp.dx = p->d.dx; rp.dy = p->d.dy; rp.dz = p->d.dz;
         rp.x0 = p->d.x0; rp.y0 = p->d.y0; rp.z0 = p->d.z0;
         rp.mat = p->mat_nat; rp.scale_t = p->scale_t_nat; rp.sigma_t = p->sigma_t;
-        rp.src = p->src; rp.spec = p->spec; rp.unc = p->unc;
-        for (int g0 = 0; g0 < G; g0 += kRayGroups)
-            k_raytrace<<<dim3((p->V + 127) / 128, B), 128, 0, p->stream>>>(rp, g0);
+        rp.src = p->src; rp.spec = p->spec; rp.unc = p->unc; rp.n_mat = p->n_mat;
+        if (p->n_mat <= kRayMats) {
+            k_raytrace_mat<<<dim3((p->V + kRayThreads - 1) / kRayThreads, B), kRayThreads, 0, p->stream>>>(rp);
+        } else {
+            for (int g0 = 0; g0 < G; g0 += kRayGroups)
+                k_raytrace<<<dim3((p->V + 127) / 128, B), 128, 0, p->stream>>>(rp, g0);
+        }
         CK(cudaGetLastError());
     }
     for (int g = 0; g < std::min(G, W1); ++g) {
@@ -638,7 +650,7 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
     }
 
     int64_t updates = 0, sweeps = 0;
-    int64_t launches = (G + kRayGroups - 1) / kRayGroups + std::min(G, W1);
+    int64_t launches = (p->n_mat <= kRayMats ? 1 : (G + kRayGroups - 1) / kRayGroups) + std::min(G, W1);
     double max_res = 0.0, sweep_ms = 0.0, reduce_ms = 0.0;
     bool all_conv = true;
     const int64_t u_per_sweep = (int64_t)p->V * p->nd;
@@ -1172,7 +1184,7 @@ dts_status run_adjoint(dts_problem* p, int b)
     rp2.dx = p->d.dx; rp2.dy = p->d.dy; rp2.dz = p->d.dz;
     rp2.x0 = p->d.x0; rp2.y0 = p->d.y0; rp2.z0 = p->d.z0;
     rp2.mat = p->mat_nat; rp2.scale_t = p->scale_t_nat; rp2.sigma_t = p->sigma_t;
-    rp2.src = p->src; rp2.spec = p->spec; rp2.unc = p->unc;
+    rp2.src = p->src; rp2.spec = p->spec; rp2.unc = p->unc; rp2.n_mat = p->n_mat;
     k_adj_ray<<<(unsigned)((V + 127) / 128), 128, 0, p->stream>>>(rp2, p->adj_a, p->adj_dphiu, b, p->adj_gt);
     CK(cudaGetLastError());
     return DTS_OK;
