@@ -131,10 +131,19 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "of fallback"
 
 
-def sweep_bytes_per_update(K, ndo, rsz):
+def direct_output(tile, fp32, K, ndo):
+    """Whether the library's batched kernel writes angular fluxes (N_d per cell)
+    instead of 8 K octant moment partials: FP32 batched tiles with 8 K > N_d."""
+    return sweep_kernel_name(tile, fp32) == "k_sweep_batch" and 8 * K > 8 * ndo   # 8 K > N_d
+
+
+def sweep_bytes_per_update(K, ndo, rsz, psi=False):
     """Algorithmic bytes of the sweep kernel per cell-direction update: per
-    (cell, octant) it reads K source moments and sigma_t and writes K octant
-    moment partials; the octant's ndo directions share them."""
+    (cell, octant) it reads K source moments and sigma_t, shared by the
+    octant's ndo directions; it writes K octant moment partials per (cell,
+    octant), or in the direct-output form one angular flux per update."""
+    if psi:
+        return (K + 1) * rsz / ndo + rsz
     return (2 * K + 1) * rsz / ndo
 
 
@@ -256,14 +265,16 @@ def run_ours(args):
     K, ndo = (w.legendre_order + 1) ** 2, w.n_dirs // 8
     rsz = 4 if fp32 else 8
     sweep_ms = sum(s["sweep_ms"] for s in stats)
-    bpu = sweep_bytes_per_update(K, ndo, rsz)
+    psi = direct_output(tile, fp32, K, ndo)
+    bpu = sweep_bytes_per_update(K, ndo, rsz, psi)
     peaks, which = measured_peaks()
     achieved = (sum(s["updates"] for s in stats) * bpu / 1e9) / (sweep_ms / 1e3)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "kernel": sweep_kernel_name(tile, fp32), "peak_source": which,
                 "sweep_share_of_step": sweep_ms / ms if ms else None,
-                "bytes_per_update": bpu}
+                "bytes_per_update": bpu,
+                "sweep_output": "angular fluxes" if psi else "octant moment partials"}
 
     extra = {}
     if rank == 0 and fp32 and not args.no_fp64:

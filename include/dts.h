@@ -237,8 +237,9 @@ dts_status dts_quadrature(int sn_order, double *mu, double *eta, double *xi, dou
  * to 16 sources) each candidate tile that fits -- 8x4x4 (FP32 batched
  * kernel), 8x4x8, 4x4x8, 16x4x8, 8x8x4, 8x8x8, 4x4x4 -- times two source
  * iterations of a probe problem (one group, homogeneous scatterer, unit
- * volumetric source) and the fastest sweep in updates per second wins. Writes
- * desc->tile_x/y/z; *best_updates_per_s (may be NULL) gets the probe rate.
+ * volumetric source) and the highest rate of updates per second of sweep plus
+ * Eq. 3 reduction time wins. Writes desc->tile_x/y/z; *best_updates_per_s
+ * (may be NULL) gets that probe rate.
  * Results are cached per process. Runs on the device; allocates and frees
  * probe problems. Errors: DTS_ERR_INVALID_ARG, DTS_ERR_CUDA.
  */

@@ -589,6 +589,13 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return r;
 }
 
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -597,7 +604,7 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-template <int NDO, int K, int BX>
+template <int NDO, int K, int BX, bool PSI = false>
 struct BatchShape {
     static constexpr int BY = 4, BZ = 4, BV = BX * BY * BZ, NLINE = BY * BZ;
     static constexpr int SB = 32 / NDO, NL = SB * NDO;  // sources per warp, busy lanes
@@ -613,7 +620,7 @@ struct BatchShape {
     // float offsets
     static constexpr int oT = 0;                        // [2][SB][TSTR]
     static constexpr int oP = oT + 2 * SB * TSTR;       // [SB][PSTR]
-    static constexpr int oX = oP + SB * PSTR;           // [fxn][32] x faces, slot = local line
+    static constexpr int oX = oP + (PSI ? 0 : SB * PSTR);   // [fxn][32] x faces, slot = local line
     static constexpr int oY = oX + fxn * 32;            // [fyn][32] y faces, slot = lz * BX + lx
     static constexpr int oZ = oY + fyn * 32;            // [fzn][32] z faces, slot = ly * BX + lx
     static constexpr int oS = oZ + fzn * 32;            // [NLINE][BX] sigma_t, local line, storage x
@@ -621,8 +628,8 @@ struct BatchShape {
     static constexpr size_t bytes = sizeof(float) * nF + sizeof(double) * SB;
 };
 
-template <int NDO, int K, int BX>
-__host__ __device__ constexpr size_t sweep_batch_smem() { return BatchShape<NDO, K, BX>::bytes; }
+template <int NDO, int K, int BX, bool PSI>
+__host__ __device__ constexpr size_t sweep_batch_smem() { return BatchShape<NDO, K, BX, PSI>::bytes; }
 
 // Face buffers of the batched kernel: per (octant, source group, tile column)
 // one block of F slots x 32 lanes, in the octant-local frame of the sweep.
@@ -705,11 +712,11 @@ __device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], flo
     }
 }
 
-template <int NDO, int K, int BX, bool NX>
+template <int NDO, int K, int BX, bool PSI, bool NX>
 __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, const int oct, const int grp,
                                                  const int ta, const int tb, const int tc, const unsigned okmask)
 {
-    using S = BatchShape<NDO, K, BX>;
+    using S = BatchShape<NDO, K, BX, PSI>;
     constexpr int BY = S::BY, BZ = S::BZ, BV = S::BV, SB = S::SB, NL = S::NL, NQ = S::NQ;
     constexpr int TSTR = S::TSTR, PSTR = S::PSTR, NH = S::NH, NJ = S::NJ, NCP = S::NCP;
     constexpr int fxn = S::fxn, fyn = S::fyn, fzn = S::fzn;
@@ -786,14 +793,17 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     const float asum = ax + ay + az;
     const float* trow = Tst + (srcok ? bl : 0) * TSTR;
     float* prow = Ps + (srcok ? bl : 0) * PSTR + d * BX;
+    float* psi_lane = p.part + ((((size_t)(b0 + (srcok ? bl : 0)) * 8 + oct) * p.NT + tile) * NDO + d) * BV;
 
     // phase C lane: (moment kc, group h); items (source il, quad qd) = h + NH * j
     const int kc = lane % K, hc = lane / K;
-    unsigned long long dk[NDO];
+    unsigned long long dk[PSI ? 1 : NDO];
+    if constexpr (!PSI) {
 #pragma unroll
-    for (int dd = 0; dd < NDO; ++dd) {
-        const float v = hc < NH ? p.Dt[(n0 + dd) * K + kc] : 0.f;
-        dk[dd] = f2pack(v, v);
+        for (int dd = 0; dd < NDO; ++dd) {
+            const float v = hc < NH ? p.Dt[(n0 + dd) * K + kc] : 0.f;
+            dk[dd] = f2pack(v, v);
+        }
     }
     auto citem = [&](int j, int& pofs, int& oofs) {
         const int item = hc + NH * j;
@@ -803,7 +813,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         oofs = ok ? il * NTKB + kc * BV + 4 * qd : -1;
     };
     int cp_[S::PRE_C ? NJ : 1], co_[S::PRE_C ? NJ : 1];
-    if constexpr (S::PRE_C) {
+    if constexpr (S::PRE_C && !PSI) {
 #pragma unroll
         for (int j = 0; j < NJ; ++j) citem(j, cp_[j], co_[j]);
     }
@@ -878,7 +888,18 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 #pragma unroll
             for (int lx = 0; lx < BX; ++lx) fy[(lz * BX + lx) * 32 + lane] = yv[lx];
         }
-        if (srcok) {
+        if constexpr (PSI) {
+            // the lane's angular fluxes of the line go straight to HBM: psi[b][oct][tile][d][cell]
+            if (srcok) {
+                float* dst = psi_lane + (sz * BY + sy) * BX;
+#pragma unroll
+                for (int qd = 0; qd < NQ; ++qd)
+                    *reinterpret_cast<float4*>(dst + 4 * qd) =
+                        make_float4(qv[4 * qd], qv[4 * qd + 1], qv[4 * qd + 2], qv[4 * qd + 3]);
+            }
+            __syncwarp();   // every lane is done with this line's staged sources before they are refilled
+            continue;
+        } else if (srcok) {
 #pragma unroll
             for (int qd = 0; qd < NQ; ++qd)
                 *reinterpret_cast<float4*>(prow + 4 * qd) =
@@ -939,10 +960,10 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     }
 }
 
-template <int NDO, int K, int BX>
+template <int NDO, int K, int BX, bool PSI>
 __global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float> p, const int stage)
 {
-    constexpr int SB = BatchShape<NDO, K, BX>::SB;
+    constexpr int SB = BatchShape<NDO, K, BX, PSI>::SB;
     const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
     int bid = blockIdx.x;
     const int tl = bid % cnt;
@@ -955,8 +976,8 @@ __global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float>
     if (okmask == 0) return;
     const unsigned pk = p.stage_tiles[s0 + tl];
     const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
-    if (oct & 1) sweep_batch_body<NDO, K, BX, true>(p, oct, grp, ta, tb, tc, okmask);
-    else sweep_batch_body<NDO, K, BX, false>(p, oct, grp, ta, tb, tc, okmask);
+    if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true>(p, oct, grp, ta, tb, tc, okmask);
+    else sweep_batch_body<NDO, K, BX, PSI, false>(p, oct, grp, ta, tb, tc, okmask);
 }
 
 // Translation units that only launch the sweep define DTS_SWEEP_KERNEL_ONLY so
@@ -980,6 +1001,7 @@ struct RedParams {
     const R* sigs;             // [L+1][NC] in-group scatter per cell
     const double* sigs0;       // [NC] l = 0 in-group scatter, FP64
     const double* sigt64;      // [NC]
+    const R* sigt;             // [NC] sigma_t in the sweep precision
     const int* mat_t;          // [NC], -1 = padding
     const int* active;
     double vol;
@@ -1040,6 +1062,52 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedParams<R> p)
     }
 }
 
+// Error-free FP32 accumulation (Knuth's two-sum): s + e carries the exact sum
+// of the FP32 terms added so far (to within rounding of the small e), so the
+// FP64 scalar flux (double)s + (double)e equals the octant sum to ~2^-48.
+struct TwoSum {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
+
+// The per-cell tail of the FP32 reductions: store the FP64 scalar flux, form
+// T_0 = F_0 + sigma_s0 phi_00 in FP32, and accumulate this thread's residual
+// and balance terms in FP32 (summed across threads in FP64).
+struct RedTail {
+    float ds = 0.f, ns = 0.f, sr = 0.f, ab = 0.f;
+    __device__ __forceinline__ float cell(double s0, double old, float f0, float sl0, float st)
+    {
+        const float s0f = (float)s0, dd = (float)(s0 - old), oldf = (float)old;
+        ds = fmaf(dd, dd, ds);
+        ns = fmaf(s0f, s0f, ns);
+        ab = fmaf(st, s0f, ab);
+        sr += fmaf(sl0, oldf, f0);
+        return fmaf(sl0, s0f, f0);
+    }
+};
+
+__device__ __forceinline__ void red_tail_store(const RedParams<float>& p, const RedTail& t, double* red, int b)
+{
+    const double ds = block_sum((double)t.ds, red);
+    const double ns = block_sum((double)t.ns, red);
+    const double sr = block_sum((double)t.sr, red);
+    const double ab = block_sum((double)t.ab, red);
+    if (threadIdx.x == 0) {
+        double* o = p.blk + ((size_t)b * gridDim.x + blockIdx.x) * 4;
+        o[0] = ds;
+        o[1] = ns;
+        o[2] = p.vol * sr;
+        o[3] = p.vol * ab;
+    }
+}
+
 // The same reduction for FP32 sweeps, four consecutive cells per thread with
 // 16-byte loads and stores (tile volumes that are multiples of 4).
 template <int K>
@@ -1048,7 +1116,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce4(const RedParams<float> 
     __shared__ double red[32];
     const int b = blockIdx.y;
     const int c4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    double ds = 0.0, ns = 0.0, sr = 0.0, ab = 0.0;
+    RedTail tl;
     if (p.active[b] != 0 && c4 < p.NC) {
         const int tile = c4 / p.TV, c = c4 - tile * p.TV;
         const size_t base = ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
@@ -1059,35 +1127,36 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce4(const RedParams<float> 
         double* __restrict__ ph = p.phi00 + (size_t)b * p.NC + c4;
         const int4 m4 = *reinterpret_cast<const int4*>(p.mat_t + c4);
         const int mm[4] = {m4.x, m4.y, m4.z, m4.w};
-        double s0[4] = {0.0, 0.0, 0.0, 0.0};
+        TwoSum s0[4];
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
             const float4 v = *reinterpret_cast<const float4*>(pp + o * ostride);
-            s0[0] += (double)v.x;
-            s0[1] += (double)v.y;
-            s0[2] += (double)v.z;
-            s0[3] += (double)v.w;
+            s0[0].add(v.x);
+            s0[1].add(v.y);
+            s0[2].add(v.z);
+            s0[3].add(v.w);
         }
         const float4 f0 = *reinterpret_cast<const float4*>(F);
-        const float ff[4] = {f0.x, f0.y, f0.z, f0.w};
+        const float4 sl0 = *reinterpret_cast<const float4*>(p.sigs + c4);
+        const float4 st = *reinterpret_cast<const float4*>(p.sigt + c4);
+        const double2 o01 = *reinterpret_cast<const double2*>(ph), o23 = *reinterpret_cast<const double2*>(ph + 2);
+        const float ff[4] = {f0.x, f0.y, f0.z, f0.w}, sl[4] = {sl0.x, sl0.y, sl0.z, sl0.w};
+        const float sg[4] = {st.x, st.y, st.z, st.w};
+        const double old[4] = {o01.x, o01.y, o23.x, o23.y};
+        double phi[4];
         float t0[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (mm[j] < 0) {
-                s0[j] = 0.0;
+                phi[j] = 0.0;
                 t0[j] = 0.f;
                 continue;
             }
-            const double old = ph[j], sl0 = p.sigs0[c4 + j], fj = (double)ff[j];
-            const double dd = s0[j] - old;
-            ds += dd * dd;
-            ns += s0[j] * s0[j];
-            ab += p.vol * p.sigt64[c4 + j] * s0[j];
-            sr += p.vol * (fj + sl0 * old);
-            t0[j] = (float)(fj + sl0 * s0[j]);
+            phi[j] = s0[j].value();
+            t0[j] = tl.cell(phi[j], old[j], ff[j], sl[j], sg[j]);
         }
-        *reinterpret_cast<double2*>(ph) = make_double2(s0[0], s0[1]);
-        *reinterpret_cast<double2*>(ph + 2) = make_double2(s0[2], s0[3]);
+        *reinterpret_cast<double2*>(ph) = make_double2(phi[0], phi[1]);
+        *reinterpret_cast<double2*>(ph + 2) = make_double2(phi[2], phi[3]);
         *reinterpret_cast<float4*>(T) = make_float4(t0[0], t0[1], t0[2], t0[3]);
 #pragma unroll
         for (int k = 1; k < K; ++k) {
@@ -1101,22 +1170,144 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce4(const RedParams<float> 
                 acc.w += v.w;
             }
             const float4 f = *reinterpret_cast<const float4*>(F + (size_t)k * p.TV);
-            const float4 sl = *reinterpret_cast<const float4*>(p.sigs + (size_t)l_of_k(k) * p.NC + c4);
+            const float4 sk = *reinterpret_cast<const float4*>(p.sigs + (size_t)l_of_k(k) * p.NC + c4);
             *reinterpret_cast<float4*>(T + (size_t)k * p.TV) =
-                make_float4(f.x + sl.x * acc.x, f.y + sl.y * acc.y, f.z + sl.z * acc.z, f.w + sl.w * acc.w);
+                make_float4(fmaf(sk.x, acc.x, f.x), fmaf(sk.y, acc.y, f.y), fmaf(sk.z, acc.z, f.z), fmaf(sk.w, acc.w, f.w));
         }
     }
-    ds = block_sum(ds, red);
-    ns = block_sum(ns, red);
-    sr = block_sum(sr, red);
-    ab = block_sum(ab, red);
-    if (threadIdx.x == 0) {
-        double* o = p.blk + ((size_t)b * gridDim.x + blockIdx.x) * 4;
-        o[0] = ds;
-        o[1] = ns;
-        o[2] = sr;
-        o[3] = ab;
+    red_tail_store(p, tl, red, b);
+}
+
+// Eq. 3 and its higher moments from the angular fluxes written by the batched
+// sweep's direct-output form, psi[b][octant][tile][direction][cell], for two
+// consecutive tiled cells. The moment operator is read as pairs of moments
+// (D[n][2j], D[n][2j+1]) so that one 16-byte shared load feeds four packed
+// FMAs. Each octant's directions are summed in FP32; the scalar flux takes
+// those octant sums exactly (two-sum) in octant order 0..7, the higher
+// moments stay in FP32.
+template <int K> struct PsiPairs { static constexpr int value = ((K + 1) / 2 + 1) & ~1; };   // even
+
+template <int NDO, int K>
+__device__ __forceinline__ void psi_moments(const float* __restrict__ ps, size_t ostride, int TV,
+                                            const unsigned long long* Dp, TwoSum (&s0)[2], float (&m1)[2],
+                                            unsigned long long (&acc)[2][PsiPairs<K>::value])
+{
+    constexpr int KP = PsiPairs<K>::value;
+    m1[0] = m1[1] = 0.f;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) acc[0][j] = acc[1][j] = 0ull;
+#pragma unroll 2
+    for (int o = 0; o < 8; ++o) {
+        unsigned long long f0[2] = {0ull, 0ull};   // moments (0, 1) of this octant
+#pragma unroll
+        for (int d = 0; d < NDO; ++d) {
+            const unsigned long long v =
+                __ldg(reinterpret_cast<const unsigned long long*>(ps + o * ostride + (size_t)d * TV));
+            float p0, p1;
+            f2unpack(v, p0, p1);
+            const unsigned long long a = f2pack(p0, p0), bq = f2pack(p1, p1);
+            const ulonglong2* dq = reinterpret_cast<const ulonglong2*>(Dp + (o * NDO + d) * KP);
+#pragma unroll
+            for (int j = 0; j < KP / 2; ++j) {
+                const ulonglong2 dd = dq[j];
+                if (j == 0) {
+                    f0[0] = ffma2(dd.x, a, f0[0]);
+                    f0[1] = ffma2(dd.x, bq, f0[1]);
+                } else {
+                    acc[0][2 * j] = ffma2(dd.x, a, acc[0][2 * j]);
+                    acc[1][2 * j] = ffma2(dd.x, bq, acc[1][2 * j]);
+                }
+                acc[0][2 * j + 1] = ffma2(dd.y, a, acc[0][2 * j + 1]);
+                acc[1][2 * j + 1] = ffma2(dd.y, bq, acc[1][2 * j + 1]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float lo, hi;
+            f2unpack(f0[c], lo, hi);
+            s0[c].add(lo);
+            m1[c] += hi;
+        }
     }
+}
+
+// moment k >= 1 of cell c from psi_moments' accumulators
+template <int K>
+__device__ __forceinline__ float psi_moment(int k, int c, const float (&m1)[2],
+                                            const unsigned long long (&acc)[2][PsiPairs<K>::value])
+{
+    if (k == 1) return m1[c];
+    float lo, hi;
+    f2unpack(acc[c][k / 2], lo, hi);
+    return (k & 1) ? hi : lo;
+}
+
+template <int NDO, int K>
+__device__ __forceinline__ void load_dpairs(unsigned long long* Dp, const float* Dt)
+{
+    constexpr int KP = PsiPairs<K>::value;
+    for (int i = threadIdx.x; i < 8 * NDO * KP; i += blockDim.x) {
+        const int n = i / KP, j = i - n * KP;
+        const float lo = 2 * j < K ? Dt[n * K + 2 * j] : 0.f, hi = 2 * j + 1 < K ? Dt[n * K + 2 * j + 1] : 0.f;
+        Dp[i] = f2pack(lo, hi);
+    }
+    __syncthreads();
+}
+
+// A5 + A6 for the direct-output form: moments from psi, then T = F + sigma_s phi,
+// the FP64 scalar flux, and the residual and balance partials as k_reduce4.
+template <int NDO, int K>
+__global__ void __launch_bounds__(kRedThreads, 2) k_reduce_psi(const RedParams<float> p, const float* __restrict__ Dt)
+{
+    __shared__ __align__(16) unsigned long long Dp[8 * NDO * PsiPairs<K>::value];
+    __shared__ double red[32];
+    load_dpairs<NDO, K>(Dp, Dt);
+    const int b = blockIdx.y;
+    const int c2 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    RedTail tl;
+    if (p.active[b] != 0 && c2 < p.NC) {
+        const int tile = c2 / p.TV, c = c2 - tile * p.TV;
+        const size_t base = ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
+        const size_t ostride = (size_t)p.NT * NDO * p.TV;
+        const float* ps = p.part + (size_t)b * 8 * ostride + (size_t)tile * NDO * p.TV + c;
+        TwoSum s0[2];
+        float m1[2];
+        unsigned long long acc[2][PsiPairs<K>::value];
+        psi_moments<NDO, K>(ps, ostride, p.TV, Dp, s0, m1, acc);
+        float* __restrict__ T = p.T + base;
+        const float* __restrict__ F = p.F + (size_t)p.ctl[1] * p.Fstride + base;
+        double* __restrict__ ph = p.phi00 + (size_t)b * p.NC + c2;
+        const int2 mv = *reinterpret_cast<const int2*>(p.mat_t + c2);
+        const int mm[2] = {mv.x, mv.y};
+        const float2 f0 = *reinterpret_cast<const float2*>(F);
+        const float2 sl0 = *reinterpret_cast<const float2*>(p.sigs + c2);
+        const float2 st = *reinterpret_cast<const float2*>(p.sigt + c2);
+        const double2 od = *reinterpret_cast<const double2*>(ph);
+        const float ff[2] = {f0.x, f0.y}, sl[2] = {sl0.x, sl0.y}, sg[2] = {st.x, st.y};
+        const double old[2] = {od.x, od.y};
+        double phi[2];
+        float t0[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (mm[j] < 0) {
+                phi[j] = 0.0;
+                t0[j] = 0.f;
+                continue;
+            }
+            phi[j] = s0[j].value();
+            t0[j] = tl.cell(phi[j], old[j], ff[j], sl[j], sg[j]);
+        }
+        *reinterpret_cast<double2*>(ph) = make_double2(phi[0], phi[1]);
+        *reinterpret_cast<float2*>(T) = make_float2(t0[0], t0[1]);
+#pragma unroll
+        for (int k = 1; k < K; ++k) {
+            const float a0 = psi_moment<K>(k, 0, m1, acc), a1 = psi_moment<K>(k, 1, m1, acc);
+            const float2 f = *reinterpret_cast<const float2*>(F + (size_t)k * p.TV);
+            const float2 sk = *reinterpret_cast<const float2*>(p.sigs + (size_t)l_of_k(k) * p.NC + c2);
+            *reinterpret_cast<float2*>(T + (size_t)k * p.TV) = make_float2(fmaf(sk.x, a0, f.x), fmaf(sk.y, a1, f.y));
+        }
+    }
+    red_tail_store(p, tl, red, b);
 }
 
 // per source: residual = sqrt(sum dphi^2 / sum phi^2), balance terms, leakage
@@ -1612,6 +1803,73 @@ __global__ void __launch_bounds__(256) k_push4(const PushParams<float> p, int g)
             fv.y = fmaf(sc[w][l][1], s4.y, fv.y);
             fv.z = fmaf(sc[w][l][2], s4.z, fv.z);
             fv.w = fmaf(sc[w][l][3], s4.w, fv.w);
+            *f = fv;
+        }
+    }
+}
+
+// The downscatter push of the direct-output form: the converged group's
+// moments are recomputed from the last sweep's angular fluxes (as k_reduce_psi
+// forms them, two cells per thread), then pushed as in k_push4.
+template <int NDO, int K>
+__global__ void __launch_bounds__(256) k_push_psi(const PushParams<float> p, int g, const float* __restrict__ Dt)
+{
+    __shared__ __align__(16) unsigned long long Dp[8 * NDO * PsiPairs<K>::value];
+    load_dpairs<NDO, K>(Dp, Dt);
+    const int c2 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const int b = blockIdx.y;
+    const CellParams& c = p.c;
+    if (c2 >= c.NC) return;
+    const int2 mv = *reinterpret_cast<const int2*>(c.mat_t + c2);
+    const int mm[2] = {mv.x, mv.y};
+    if ((mm[0] & mm[1]) < 0) return;
+    const int tile = c2 / c.TV, cc = c2 - tile * c.TV;
+    const size_t base = ((size_t)b * c.NT + tile) * (size_t)(K * c.TV) + cc;
+    const size_t ostride = (size_t)c.NT * NDO * c.TV;
+    const float* ps = p.part + (size_t)b * 8 * ostride + (size_t)tile * NDO * c.TV + cc;
+    TwoSum s0t[2];
+    float m1[2];
+    unsigned long long acc[2][PsiPairs<K>::value];
+    psi_moments<NDO, K>(ps, ostride, c.TV, Dp, s0t, m1, acc);
+    const int v0 = tiled_to_natural(c, c2, nullptr);           // the 2 cells are x-consecutive
+    const int x0 = v0 % c.nx;
+    const int W1 = p.W + 1;
+    const int nw = min(c.G - 1, g + p.W) - g;
+    const int L1 = c.L + 1;
+    double ss[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) ss[j] = c.scale_s_t ? c.scale_s_t[c2 + j] : 1.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double ph[2];
+        float2 s2;
+        if (k == 0) {
+            ph[0] = s0t[0].value();
+            ph[1] = s0t[1].value();
+            s2 = make_float2((float)ph[0], (float)ph[1]);
+        } else {
+            s2 = make_float2(psi_moment<K>(k, 0, m1, acc), psi_moment<K>(k, 1, m1, acc));
+            ph[0] = s2.x;
+            ph[1] = s2.y;
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (mm[j] < 0 || x0 + j >= c.nx) continue;
+            if (k == 0) p.col[((size_t)b * c.G + g) * p.V + v0 + j] = ph[j];
+            if (p.mom) p.mom[(((size_t)b * c.G + g) * K + k) * p.V + v0 + j] = ph[j];
+        }
+        const int l = l_of_k(k);
+        for (int w = 0; w < nw; ++w) {
+            float sc[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                sc[j] = mm[j] < 0 ? 0.f
+                                  : (float)(c.sigma_s[(((size_t)mm[j] * L1 + l) * c.G + g) * c.G + g + 1 + w] * ss[j]);
+            float2* f = reinterpret_cast<float2*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base +
+                                                  (size_t)k * c.TV);
+            float2 fv = *f;
+            fv.x = fmaf(sc[0], s2.x, fv.x);
+            fv.y = fmaf(sc[1], s2.y, fv.y);
             *f = fv;
         }
     }

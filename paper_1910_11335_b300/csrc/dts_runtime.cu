@@ -55,9 +55,10 @@ struct dts_problem {
     std::string err = "no error";
     int V = 0, G = 0, L = 0, K = 0, nd = 0, ndo = 0, B = 0;
     int TX = 0, TY = 0, TZ = 0, TV = 0, NTx = 0, NTy = 0, NTz = 0, NT = 0, NC = 0;
-    int n_stages = 0, nsub = 0, n_mat = 0, W = 0, nblk = 0;
+    int n_stages = 0, nsub = 0, n_mat = 0, W = 0, nblk = 0, n_sm = 148;
     int line_warps = 2;               // warps per CTA of the line sweep kernel
     bool fp64 = true;
+    bool psi_mode = false;   // batched FP32 sweep writes angular fluxes; moments formed by k_reduce_psi
     size_t rsz = 8;                   // sizeof(R)
     std::vector<int> stage_off_h;     // [n_stages+1]
     std::vector<double> mu, eta, xi, w;
@@ -342,58 +343,92 @@ bool batch_tile(const dts_problem* p)
 
 int batch_sources_per_warp(const dts_problem* p) { return 32 / p->ndo; }
 
-template <int NDO, int BX>
+// the direct-output form pays N_d angular fluxes per cell instead of 8 K octant
+// partials, so it is taken where that is less traffic (e.g. S8 with P3)
+bool psi_form(const dts_problem* p) { return batch_tile(p) && 8 * p->K > p->nd; }
+
+template <int NDO, int BX, bool PSI>
 SweepFn<float> batch_fn_k(int K)
 {
     switch (K) {
-    case 1: return k_sweep_batch<NDO, 1, BX>;
-    case 4: return k_sweep_batch<NDO, 4, BX>;
-    case 9: return k_sweep_batch<NDO, 9, BX>;
-    case 16: return k_sweep_batch<NDO, 16, BX>;
+    case 1: return k_sweep_batch<NDO, 1, BX, PSI>;
+    case 4: return k_sweep_batch<NDO, 4, BX, PSI>;
+    case 9: return k_sweep_batch<NDO, 9, BX, PSI>;
+    case 16: return k_sweep_batch<NDO, 16, BX, PSI>;
     }
     return nullptr;
 }
 
-template <int NDO, int BX>
+template <int NDO, int BX, bool PSI>
 size_t batch_smem_k(int K)
 {
     switch (K) {
-    case 1: return sweep_batch_smem<NDO, 1, BX>();
-    case 4: return sweep_batch_smem<NDO, 4, BX>();
-    case 9: return sweep_batch_smem<NDO, 9, BX>();
-    case 16: return sweep_batch_smem<NDO, 16, BX>();
+    case 1: return sweep_batch_smem<NDO, 1, BX, PSI>();
+    case 4: return sweep_batch_smem<NDO, 4, BX, PSI>();
+    case 9: return sweep_batch_smem<NDO, 9, BX, PSI>();
+    case 16: return sweep_batch_smem<NDO, 16, BX, PSI>();
     }
     return 0;
 }
 
-template <int BX>
+template <int BX, bool PSI>
 size_t batch_smem_x(int ndo, int K)
 {
     switch (ndo) {
-    case 1: return batch_smem_k<1, BX>(K);
-    case 3: return batch_smem_k<3, BX>(K);
-    case 6: return batch_smem_k<6, BX>(K);
-    case 10: return batch_smem_k<10, BX>(K);
+    case 1: return batch_smem_k<1, BX, PSI>(K);
+    case 3: return batch_smem_k<3, BX, PSI>(K);
+    case 6: return batch_smem_k<6, BX, PSI>(K);
+    case 10: return batch_smem_k<10, BX, PSI>(K);
     }
     return 0;
 }
 
-template <int BX>
+template <int BX, bool PSI>
 SweepFn<float> batch_fn_x(int ndo, int K)
 {
     switch (ndo) {
-    case 1: return batch_fn_k<1, BX>(K);
-    case 3: return batch_fn_k<3, BX>(K);
-    case 6: return batch_fn_k<6, BX>(K);
-    case 10: return batch_fn_k<10, BX>(K);
+    case 1: return batch_fn_k<1, BX, PSI>(K);
+    case 3: return batch_fn_k<3, BX, PSI>(K);
+    case 6: return batch_fn_k<6, BX, PSI>(K);
+    case 10: return batch_fn_k<10, BX, PSI>(K);
     }
     return nullptr;
 }
 
 SweepFn<float> batch_fn(const dts_problem* p)
 {
-    return p->TX == 8 ? batch_fn_x<8>(p->ndo, p->K) : batch_fn_x<4>(p->ndo, p->K);
+    if (p->psi_mode) return p->TX == 8 ? batch_fn_x<8, true>(p->ndo, p->K) : batch_fn_x<4, true>(p->ndo, p->K);
+    return p->TX == 8 ? batch_fn_x<8, false>(p->ndo, p->K) : batch_fn_x<4, false>(p->ndo, p->K);
 }
+
+using RedPsiFn = void (*)(const RedParams<float>, const float*);
+using PushPsiFn = void (*)(const PushParams<float>, int, const float*);
+
+template <int NDO>
+void psi_fns_k(int K, RedPsiFn& r, PushPsiFn& u)
+{
+    switch (K) {
+    case 1: r = k_reduce_psi<NDO, 1>; u = k_push_psi<NDO, 1>; return;
+    case 4: r = k_reduce_psi<NDO, 4>; u = k_push_psi<NDO, 4>; return;
+    case 9: r = k_reduce_psi<NDO, 9>; u = k_push_psi<NDO, 9>; return;
+    case 16: r = k_reduce_psi<NDO, 16>; u = k_push_psi<NDO, 16>; return;
+    }
+    r = nullptr;
+    u = nullptr;
+}
+
+void psi_fns(const dts_problem* p, RedPsiFn& r, PushPsiFn& u)
+{
+    r = nullptr;
+    u = nullptr;
+    switch (p->ndo) {
+    case 1: psi_fns_k<1>(p->K, r, u); return;
+    case 3: psi_fns_k<3>(p->K, r, u); return;
+    case 6: psi_fns_k<6>(p->K, r, u); return;
+    case 10: psi_fns_k<10>(p->K, r, u); return;
+    }
+}
+
 
 template <typename R>
 SweepFn<R> sweep_fn(const dts_problem* p)
@@ -431,7 +466,10 @@ RedFn<float> reduce4_fn(int K)
 
 size_t sweep_smem(const dts_problem* p)
 {
-    if (batch_tile(p)) return p->TX == 8 ? batch_smem_x<8>(p->ndo, p->K) : batch_smem_x<4>(p->ndo, p->K);
+    if (batch_tile(p)) {
+        if (p->psi_mode) return p->TX == 8 ? batch_smem_x<8, true>(p->ndo, p->K) : batch_smem_x<4, true>(p->ndo, p->K);
+        return p->TX == 8 ? batch_smem_x<8, false>(p->ndo, p->K) : batch_smem_x<4, false>(p->ndo, p->K);
+    }
     const int xfaces = line_tile(p) ? 32 : p->TY * p->TZ;
     const size_t n = (size_t)p->ndo * p->TV +
                      (size_t)p->ndo * (xfaces + p->TX * p->TZ + p->TX * p->TY) + p->TV +
@@ -499,12 +537,18 @@ dts_status record_reduce(dts_problem* p)
     rp.B = p->B; rp.NT = p->NT; rp.TV = p->TV; rp.NC = p->NC;
     rp.part = (const R*)p->part; rp.phi00 = p->phi00; rp.T = (R*)p->T; rp.F = (const R*)p->F;
     rp.Fstride = p->Fstride; rp.ctl = p->ctl; rp.sigs = (const R*)p->sigs; rp.sigs0 = p->sigs0;
-    rp.sigt64 = p->sigt64;
+    rp.sigt64 = p->sigt64; rp.sigt = (const R*)p->sigt_r;
     rp.mat_t = p->mat_t; rp.active = p->active; rp.vol = p->d.dx * p->d.dy * p->d.dz;
     rp.blk = p->blk;
     int nblk = p->nblk;
     if constexpr (sizeof(R) == 4) {
-        if (p->TV % 4 == 0) {   // four cells per thread
+        if (p->psi_mode) {      // moments from the angular fluxes, two cells per thread
+            nblk = (p->NC / 2 + kRedThreads - 1) / kRedThreads;
+            RedPsiFn rf;
+            PushPsiFn uf;
+            psi_fns(p, rf, uf);
+            rf<<<dim3(nblk, p->B), kRedThreads, 0, p->stream>>>(rp, (const float*)p->Dt);
+        } else if (p->TV % 4 == 0) {   // four cells per thread
             nblk = (p->NC / 4 + kRedThreads - 1) / kRedThreads;
             RedFn<float> rf4 = reduce4_fn(p->K);
             rf4<<<dim3(nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
@@ -611,6 +655,13 @@ void launch_push(dts_problem* p, int g)
     pp.part = (const R*)p->part; pp.F = (R*)p->F; pp.Fstride = p->Fstride; pp.W = p->W; pp.V = p->V;
     pp.col = p->col; pp.mom = p->d.keep_moments ? p->mom : nullptr;
     if constexpr (sizeof(R) == 4) {
+        if (p->psi_mode && p->W <= 4) {
+            RedPsiFn rf;
+            PushPsiFn uf;
+            psi_fns(p, rf, uf);
+            uf<<<dim3((p->NC / 2 + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g, (const float*)p->Dt);
+            return;
+        }
         if (p->TX % 4 == 0 && p->W <= 4) {
             using PushFn = void (*)(const PushParams<float>, int);
             const PushFn f = p->K == 1 ? k_push4<1> : p->K == 4 ? k_push4<4> : p->K == 9 ? k_push4<9> : k_push4<16>;
@@ -902,6 +953,7 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     p->fp64 = d.precision == DTS_PREC_FP64;
     p->rsz = p->fp64 ? sizeof(double) : sizeof(float);
     choose_tile(p);
+    p->psi_mode = psi_form(p);
 
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));
@@ -909,6 +961,13 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     DevGuard guard(d.device);
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, d.device));
+    p->n_sm = prop.multiProcessorCount;
+    if (p->psi_mode) {
+        RedPsiFn rf;
+        PushPsiFn uf;
+        psi_fns(p, rf, uf);
+        if (!rf) p->psi_mode = false;   // octant partials instead
+    }
     if (sweep_smem(p) > prop.sharedMemPerBlockOptin)
         return fail(p, DTS_ERR_INVALID_ARG, "wavefront tile needs more shared memory than a CTA has");
     if (d.cuda_stream) {
@@ -932,7 +991,9 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     TRY(dalloc_t(p, &p->mat_nat, V));
     TRY(dalloc_t(p, &p->phi00, B * NC));
     TRY(dalloc(p, &p->T, B * NC * K * p->rsz));
-    TRY(dalloc(p, &p->part, 8 * B * NC * K * p->rsz));
+    // octant partials [8][B][NT][K][TV], or in the direct-output form the
+    // angular fluxes [B][8][NT][N_d/8][TV]
+    TRY(dalloc(p, &p->part, 8 * B * NC * (p->psi_mode ? (size_t)p->ndo : (size_t)K) * p->rsz));
     const size_t nf = (size_t)p->ndo;
     size_t fxs = 8 * B * (size_t)p->NTy * p->NTz * nf * p->TY * p->TZ * p->rsz;
     size_t fys = 8 * B * (size_t)p->NTx * p->NTz * nf * p->TX * p->TZ * p->rsz;
@@ -1136,7 +1197,7 @@ dts_status run_adjoint(dts_problem* p, int b)
     rp.B = 1; rp.NT = p->NT; rp.TV = p->TV; rp.NC = p->NC;
     rp.part = p->adj_part; rp.phi00 = p->adj_u00; rp.T = p->adj_T; rp.F = p->adj_S;
     rp.Fstride = NC * K; rp.ctl = p->adj_ctl; rp.sigs = (const double*)p->sigs; rp.sigs0 = p->sigs0;
-    rp.sigt64 = p->sigt64; rp.mat_t = p->mat_t; rp.active = p->adj_active;
+    rp.sigt64 = p->sigt64; rp.sigt = (const double*)p->sigt_r; rp.mat_t = p->mat_t; rp.active = p->adj_active;
     rp.vol = p->d.dx * p->d.dy * p->d.dz; rp.blk = p->adj_blk;
     RedFn<double> rf = reduce_fn<double>(p->K);
 
@@ -1565,7 +1626,8 @@ dts_status dts_tune_tile(dts_problem_desc* desc, double* best_updates_per_s)
         dts_solve_stats stats{};
         if (ok) ok = dts_solve(pr, &stats) == DTS_OK;
         if (ok && stats.sweep_ms > 0.0) {
-            const double ups = (double)stats.updates / (stats.sweep_ms * 1e-3);
+            // sweep and reduction together: the direct-output form moves work between them
+            const double ups = (double)stats.updates / ((stats.sweep_ms + stats.reduce_ms) * 1e-3);
             if (ups > best) {
                 best = ups;
                 best_t = t;

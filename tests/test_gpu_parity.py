@@ -137,6 +137,23 @@ def test_batched_fp32_kernel(ora, dims, N, L, G, B):
             assert abs(bal[b, g, 0] - bal[b, g, 1] - bal[b, g, 2]) <= 1e-5 * bal[b, g, 0]
 
 
+@pytest.mark.parametrize("tile", [(8, 4, 4), (4, 4, 4)])
+def test_batched_direct_output_moments(ora, tile):
+    """S8 P3 batches take the direct angular-flux output of the batched kernel
+    (N_d = 80 fluxes per cell instead of 8 x 16 octant partials); every Legendre
+    moment, not only the scalar flux, is formed from them and pushed into the
+    lower groups."""
+    w = inputs.small_cone(11, 9, 10, n_groups=3, sn_order=8, legendre_order=3, n_sources=5)
+    p, st = _gpu(w, precision=dts.PREC_FP32, tol=0.0, max_iters=4, tile=tile, keep_moments=True)
+    assert (st.tile_x, st.tile_y, st.tile_z) == tile
+    for b in (0, 4):
+        r = ora.solve(w, b, tol=0.0, max_iters=4, n_threads=8)
+        for g in range(w.n_groups):
+            m = p.moments(b, g)
+            assert rel_l2(m, r.phi_c[g]) <= TOL_FP32_L2, (b, g)
+            assert rel_l2(m[0], r.collided[g]) <= TOL_FP32_L2, (b, g)
+
+
 def test_batched_fp32_sources_converging_at_different_counts(ora):
     w = inputs.small_cone(16, 15, 14, n_groups=3, sn_order=8, legendre_order=3, n_sources=8)
     # members 4..7: volumetric sources in air, water and bone regions, which
