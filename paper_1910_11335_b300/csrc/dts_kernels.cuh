@@ -596,6 +596,12 @@ __device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsign
     return r;
 }
 
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
+}
+
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -1189,20 +1195,35 @@ template <int K> struct PsiPairs { static constexpr int value = ((K + 1) / 2 + 1
 
 template <int NDO, int K>
 __device__ __forceinline__ void psi_moments(const float* __restrict__ ps, size_t ostride, int TV,
-                                            const unsigned long long* Dp, TwoSum (&s0)[2], float (&m1)[2],
+                                            const unsigned long long* Dp, unsigned long long* stg,
+                                            TwoSum (&s0)[2], float (&m1)[2],
                                             unsigned long long (&acc)[2][PsiPairs<K>::value])
 {
+    // stg: this thread's column of a [2][NDO][blockDim.x] staging area; the next
+    // octant's fluxes are copied with cp.async while this one is reduced, so the
+    // loads in flight hold no registers (each thread reads only its own copies)
     constexpr int KP = PsiPairs<K>::value;
+    const int nt = blockDim.x;
     m1[0] = m1[1] = 0.f;
 #pragma unroll
     for (int j = 0; j < KP; ++j) acc[0][j] = acc[1][j] = 0ull;
-#pragma unroll 2
+    auto issue = [&](int o) {
+        unsigned long long* dst = stg + (o & 1) * NDO * nt;
+#pragma unroll
+        for (int d = 0; d < NDO; ++d) cp_async8(dst + d * nt, ps + o * ostride + (size_t)d * TV);
+        cp_async_commit();
+    };
+    issue(0);
+#pragma unroll 1
     for (int o = 0; o < 8; ++o) {
+        if (o + 1 < 8) issue(o + 1);
+        else cp_async_commit();
+        cp_async_wait1();
+        const unsigned long long* src = stg + (o & 1) * NDO * nt;
         unsigned long long f0[2] = {0ull, 0ull};   // moments (0, 1) of this octant
 #pragma unroll
         for (int d = 0; d < NDO; ++d) {
-            const unsigned long long v =
-                __ldg(reinterpret_cast<const unsigned long long*>(ps + o * ostride + (size_t)d * TV));
+            const unsigned long long v = src[d * nt];
             float p0, p1;
             f2unpack(v, p0, p1);
             const unsigned long long a = f2pack(p0, p0), bq = f2pack(p1, p1);
@@ -1257,9 +1278,10 @@ __device__ __forceinline__ void load_dpairs(unsigned long long* Dp, const float*
 // A5 + A6 for the direct-output form: moments from psi, then T = F + sigma_s phi,
 // the FP64 scalar flux, and the residual and balance partials as k_reduce4.
 template <int NDO, int K>
-__global__ void __launch_bounds__(kRedThreads, 2) k_reduce_psi(const RedParams<float> p, const float* __restrict__ Dt)
+__global__ void __launch_bounds__(kRedThreads, 3) k_reduce_psi(const RedParams<float> p, const float* __restrict__ Dt)
 {
     __shared__ __align__(16) unsigned long long Dp[8 * NDO * PsiPairs<K>::value];
+    __shared__ unsigned long long stg[2 * NDO * kRedThreads];
     __shared__ double red[32];
     load_dpairs<NDO, K>(Dp, Dt);
     const int b = blockIdx.y;
@@ -1273,7 +1295,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) k_reduce_psi(const RedParams<f
         TwoSum s0[2];
         float m1[2];
         unsigned long long acc[2][PsiPairs<K>::value];
-        psi_moments<NDO, K>(ps, ostride, p.TV, Dp, s0, m1, acc);
+        psi_moments<NDO, K>(ps, ostride, p.TV, Dp, stg + threadIdx.x, s0, m1, acc);
         float* __restrict__ T = p.T + base;
         const float* __restrict__ F = p.F + (size_t)p.ctl[1] * p.Fstride + base;
         double* __restrict__ ph = p.phi00 + (size_t)b * p.NC + c2;
@@ -1815,6 +1837,7 @@ template <int NDO, int K>
 __global__ void __launch_bounds__(256) k_push_psi(const PushParams<float> p, int g, const float* __restrict__ Dt)
 {
     __shared__ __align__(16) unsigned long long Dp[8 * NDO * PsiPairs<K>::value];
+    __shared__ unsigned long long stg[2 * NDO * 256];
     load_dpairs<NDO, K>(Dp, Dt);
     const int c2 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     const int b = blockIdx.y;
@@ -1830,7 +1853,7 @@ __global__ void __launch_bounds__(256) k_push_psi(const PushParams<float> p, int
     TwoSum s0t[2];
     float m1[2];
     unsigned long long acc[2][PsiPairs<K>::value];
-    psi_moments<NDO, K>(ps, ostride, c.TV, Dp, s0t, m1, acc);
+    psi_moments<NDO, K>(ps, ostride, c.TV, Dp, stg + threadIdx.x, s0t, m1, acc);
     const int v0 = tiled_to_natural(c, c2, nullptr);           // the 2 cells are x-consecutive
     const int x0 = v0 % c.nx;
     const int W1 = p.W + 1;
