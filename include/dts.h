@@ -105,6 +105,7 @@ typedef struct {
     int64_t launches;           /* kernels launched by this solve */
     int converged;              /* 1 when every (source, group) reached tol */
     int tile_x, tile_y, tile_z; /* wavefront tile used */
+    int64_t sweep_launches;     /* wavefront-stage kernel launches of this solve */
 } dts_solve_stats;
 
 /*

@@ -27,31 +27,32 @@ constexpr double kPi = 3.14159265358979323846;
 // real spherical harmonics in Cartesian form, l <= 3, k = l*l + l + m,
 // normalised so that sum_m Y_lm(a) Y_lm(b) = P_l(a.b)
 // ---------------------------------------------------------------------------
-__host__ __device__ inline void sh_eval(int L, double x, double y, double z, double* Y)
+template <typename T>
+__host__ __device__ inline void sh_eval(int L, T x, T y, T z, T* Y)
 {
-    Y[0] = 1.0;
+    Y[0] = T(1);
     if (L < 1) return;
     Y[1] = y;
     Y[2] = z;
     Y[3] = x;
     if (L < 2) return;
-    const double s3 = 1.7320508075688772;   // sqrt(3)
+    const T s3 = T(1.7320508075688772);   // sqrt(3)
     Y[4] = s3 * x * y;
     Y[5] = s3 * y * z;
-    Y[6] = 0.5 * (3.0 * z * z - 1.0);
+    Y[6] = T(0.5) * (T(3) * z * z - T(1));
     Y[7] = s3 * x * z;
-    Y[8] = 0.5 * s3 * (x * x - y * y);
+    Y[8] = T(0.5) * s3 * (x * x - y * y);
     if (L < 3) return;
-    const double s58 = 0.7905694150420949;  // sqrt(5/8)
-    const double s15 = 3.872983346207417;   // sqrt(15)
-    const double s38 = 0.6123724356957945;  // sqrt(3/8)
-    Y[9] = s58 * (3.0 * x * x * y - y * y * y);
+    const T s58 = T(0.7905694150420949);  // sqrt(5/8)
+    const T s15 = T(3.872983346207417);   // sqrt(15)
+    const T s38 = T(0.6123724356957945);  // sqrt(3/8)
+    Y[9] = s58 * (T(3) * x * x * y - y * y * y);
     Y[10] = s15 * x * y * z;
-    Y[11] = s38 * y * (5.0 * z * z - 1.0);
-    Y[12] = 0.5 * (5.0 * z * z * z - 3.0 * z);
-    Y[13] = s38 * x * (5.0 * z * z - 1.0);
-    Y[14] = 0.5 * s15 * z * (x * x - y * y);
-    Y[15] = s58 * (x * x * x - 3.0 * x * y * y);
+    Y[11] = s38 * y * (T(5) * z * z - T(1));
+    Y[12] = T(0.5) * (T(5) * z * z * z - T(3) * z);
+    Y[13] = s38 * x * (T(5) * z * z - T(1));
+    Y[14] = T(0.5) * s15 * z * (x * x - y * y);
+    Y[15] = s58 * (x * x * x - T(3) * x * y * y);
 }
 
 __host__ __device__ inline int l_of_k(int k) { return k >= 9 ? 3 : k >= 4 ? 2 : k >= 1 ? 1 : 0; }
@@ -1639,9 +1640,10 @@ struct SrcParams {
     const double* src;     // [B][8]
     const double* unc;     // [B][G][V]
     const double* q;       // [B][G][V] or null
+    const float* sigma_s_f;   // [n_mat][L+1][G][G] in FP32 (FP32 forms)
     R* F;
     size_t Fstride;
-    int V;
+    int V, W;              // W: downscatter band (sigma_s(g' -> g) = 0 for g - g' > W)
 };
 
 template <typename R>
@@ -1667,18 +1669,35 @@ __global__ void k_fixed_source(const SrcParams<R> p, int gt, int slot)
         return;
     }
     const double* s = p.src + (size_t)b * 8;
-    const double d0 = C[0] - s[1], d1 = C[1] - s[2], d2 = C[2] - s[3];
-    const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-    double Y[16];
-    sh_eval(c.L, d0 / r, d1 / r, d2 / r, Y);
-    const double ss = c.scale_s_t ? c.scale_s_t[ct] : 1.0;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int gp = 0; gp <= gt; ++gp) {
-        const double phu = p.unc[((size_t)b * c.G + gp) * p.V + v];
-        for (int l = 0; l <= c.L; ++l)
-            acc[l] += c.sigma_s[(((size_t)m * (c.L + 1) + l) * c.G + gp) * c.G + gt] * ss * phu;
+    const int g0 = max(0, gt - p.W);   // groups outside the band add exact zeros
+    if constexpr (sizeof(R) == 4) {
+        // FP32 form: the product is stored in FP32, so it is formed in FP32
+        const float d0 = (float)(C[0] - s[1]), d1 = (float)(C[1] - s[2]), d2 = (float)(C[2] - s[3]);
+        const float ri = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        float Y[16];
+        sh_eval(c.L, d0 * ri, d1 * ri, d2 * ri, Y);
+        const float ss = c.scale_s_t ? (float)c.scale_s_t[ct] : 1.f;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int gp = g0; gp <= gt; ++gp) {
+            const float phu = (float)p.unc[((size_t)b * c.G + gp) * p.V + v] * ss;
+            for (int l = 0; l <= c.L; ++l)
+                acc[l] = fmaf(p.sigma_s_f[(((size_t)m * (c.L + 1) + l) * c.G + gp) * c.G + gt], phu, acc[l]);
+        }
+        for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = acc[l_of_k(k)] * Y[k];
+    } else {
+        const double d0 = C[0] - s[1], d1 = C[1] - s[2], d2 = C[2] - s[3];
+        const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        double Y[16];
+        sh_eval(c.L, d0 / r, d1 / r, d2 / r, Y);
+        const double ss = c.scale_s_t ? c.scale_s_t[ct] : 1.0;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int gp = g0; gp <= gt; ++gp) {
+            const double phu = p.unc[((size_t)b * c.G + gp) * p.V + v];
+            for (int l = 0; l <= c.L; ++l)
+                acc[l] += c.sigma_s[(((size_t)m * (c.L + 1) + l) * c.G + gp) * c.G + gt] * ss * phu;
+        }
+        for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = (R)(acc[l_of_k(k)] * Y[k]);
     }
-    for (int k = 0; k < c.K; ++k) F[(size_t)k * c.TV] = (R)(acc[l_of_k(k)] * Y[k]);
 }
 
 // ---------------------------------------------------------------------------

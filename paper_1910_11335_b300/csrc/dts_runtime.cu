@@ -70,6 +70,7 @@ struct dts_problem {
     void *Mt = nullptr, *Dt = nullptr, *At = nullptr;
     double* Lw = nullptr;
     double *sigma_t = nullptr, *sigma_s = nullptr;
+    float* sigma_s_f = nullptr;       // FP32 copy of sigma_s for FP32 forms
     int *mat_t = nullptr, *mat_nat = nullptr;
     double *scale_t_t = nullptr, *scale_s_t = nullptr, *scale_t_nat = nullptr;
     void* F = nullptr;                // fixed-source ring, sweep precision
@@ -643,7 +644,7 @@ void launch_fixed_source(dts_problem* p, int gt, int slot)
     SrcParams<R> sp;
     sp.c = cell_params(p);
     sp.src = p->src; sp.unc = p->unc; sp.q = p->q; sp.F = (R*)p->F; sp.Fstride = p->Fstride;
-    sp.V = p->V;
+    sp.V = p->V; sp.W = p->W; sp.sigma_s_f = p->sigma_s_f;
     k_fixed_source<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(sp, gt, slot);
 }
 
@@ -700,7 +701,7 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         else launch_fixed_source<float>(p, g, g % W1);
     }
 
-    int64_t updates = 0, sweeps = 0;
+    int64_t updates = 0, sweeps = 0, sweep_launches = 0;
     int64_t launches = (p->n_mat <= kRayMats ? 1 : (G + kRayGroups - 1) / kRayGroups) + std::min(G, W1);
     double max_res = 0.0, sweep_ms = 0.0, reduce_ms = 0.0;
     bool all_conv = true;
@@ -734,6 +735,7 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
             CK(cudaEventRecord(p->evc, p->stream));
             CK(cudaStreamSynchronize(p->stream));
             launches += p->graph_launches;
+            sweep_launches += p->n_stages;
             {
                 float a = 0.f, b2 = 0.f;
                 CK(cudaEventElapsedTime(&a, p->eva, p->evb));
@@ -800,6 +802,7 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         st->sweep_ms = sweep_ms;
         st->reduce_ms = reduce_ms;
         st->launches = launches;
+        st->sweep_launches = sweep_launches;
         st->converged = all_conv ? 1 : 0;
         st->tile_x = p->TX;
         st->tile_y = p->TY;
@@ -1310,13 +1313,21 @@ dts_status dts_set_materials(dts_problem* p, int n_mat, const double* sigma_t, c
     if (n_mat != p->n_mat) {
         dfree(p, p->sigma_t);
         dfree(p, p->sigma_s);
+        dfree(p, p->sigma_s_f);
         p->sigma_t = p->sigma_s = nullptr;
+        p->sigma_s_f = nullptr;
         TRY(dalloc_t(p, &p->sigma_t, (size_t)n_mat * G));
         TRY(dalloc_t(p, &p->sigma_s, (size_t)n_mat * (L + 1) * G * G));
+        TRY(dalloc_t(p, &p->sigma_s_f, (size_t)n_mat * (L + 1) * G * G));
         p->n_mat = n_mat;
     }
     CK(cudaMemcpy(p->sigma_t, sigma_t, sizeof(double) * n_mat * G, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->sigma_s, sigma_s, sizeof(double) * (size_t)n_mat * (L + 1) * G * G, cudaMemcpyHostToDevice));
+    {
+        std::vector<float> sf((size_t)n_mat * (L + 1) * G * G);
+        for (size_t i = 0; i < sf.size(); ++i) sf[i] = (float)sigma_s[i];
+        CK(cudaMemcpy(p->sigma_s_f, sf.data(), sizeof(float) * sf.size(), cudaMemcpyHostToDevice));
+    }
     std::vector<int32_t> mt = to_tiled<int32_t>(p, mat_id, -1);
     CK(cudaMemcpy(p->mat_t, mt.data(), sizeof(int32_t) * p->NC, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->mat_nat, mat_id, sizeof(int32_t) * V, cudaMemcpyHostToDevice));

@@ -46,7 +46,8 @@ class SolveStats(C.Structure):
     _fields_ = [("updates", C.c_int64), ("sweeps", C.c_int64), ("max_residual", C.c_double),
                 ("solve_ms", C.c_double), ("sweep_ms", C.c_double), ("reduce_ms", C.c_double),
                 ("launches", C.c_int64), ("converged", C.c_int),
-                ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int)]
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int),
+                ("sweep_launches", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
