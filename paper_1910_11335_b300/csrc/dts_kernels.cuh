@@ -610,6 +610,7 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int NDO, int K, int BX, bool PSI = false>
 struct BatchShape {
@@ -625,8 +626,8 @@ struct BatchShape {
     static constexpr bool PRE_CP = NCP <= 4, PRE_C = NJ <= 4;   // keep per-lane offsets in registers
     static constexpr int fxn = BY * BZ, fyn = BX * BZ, fzn = BX * BY;
     // float offsets
-    static constexpr int oT = 0;                        // [2][SB][TSTR]
-    static constexpr int oP = oT + 2 * SB * TSTR;       // [SB][PSTR]
+    static constexpr int oT = 0;                        // [SB][TSTR] the line being swept, refilled after phase A
+    static constexpr int oP = oT + SB * TSTR;           // [SB][PSTR]
     static constexpr int oX = oP + (PSI ? 0 : SB * PSTR);   // [fxn][32] x faces, slot = local line
     static constexpr int oY = oX + fxn * 32;            // [fyn][32] y faces, slot = lz * BX + lx
     static constexpr int oZ = oY + fyn * 32;            // [fzn][32] z faces, slot = ly * BX + lx
@@ -851,10 +852,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 
 #pragma unroll 1
     for (int line = 0; line < S::NLINE; ++line) {
-        const int buf = line & 1;
-        if (line + 1 < S::NLINE) stage_line(line + 1, buf ^ 1);
-        else cp_async_commit();
-        cp_async_wait1();
+        cp_async_wait0();   // this line's sources (copied during the previous line's walk)
         __syncwarp();
         const int ly = line % BY, lz = line / BY;
         const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
@@ -862,7 +860,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         // A: Q for the line's cells, two cells per packed FMA, storage x order
         float qv[BX];
         {
-            const float* tr = trow + buf * SB * TSTR;
+            const float* tr = trow;
 #pragma unroll
             for (int qd = 0; qd < NQ; ++qd) {
                 unsigned long long a0 = 0ull, a1 = 0ull;
@@ -876,6 +874,11 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
                 f2unpack(a1, qv[4 * qd + 2], qv[4 * qd + 3]);
             }
         }
+
+        // the staged sources are consumed: every lane is past phase A, so the
+        // next line's sources can land in the same buffer during the walk
+        __syncwarp();
+        if (line + 1 < S::NLINE) stage_line(line + 1, 0);
 
         // B: walk the line
         if (ly == 0) {
@@ -968,7 +971,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 }
 
 template <int NDO, int K, int BX, bool PSI>
-__global__ void __launch_bounds__(32, 16) k_sweep_batch(const SweepParams<float> p, const int stage)
+__global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float> p, const int stage)
 {
     constexpr int SB = BatchShape<NDO, K, BX, PSI>::SB;
     const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
