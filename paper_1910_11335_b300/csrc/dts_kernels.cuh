@@ -655,6 +655,16 @@ __device__ __forceinline__ void batch_faces_in(float* sh, const float* g, bool u
     }
 }
 
+// the same copy issued as cp.async (completed by the caller's wait on the group)
+template <int F>
+__device__ __forceinline__ void batch_faces_in_async(float* sh, const float* g, bool upstream)
+{
+    for (int j = threadIdx.x; j < F * 8; j += 32) {
+        if (upstream) cp_async16(sh + 4 * j, g + 4 * j);
+        else *reinterpret_cast<float4*>(sh + 4 * j) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 template <int F>
 __device__ __forceinline__ void batch_faces_out(const float* sh, float* g)
 {
@@ -833,17 +843,17 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
             const int srow = i / NQ, h = i - srow * NQ;
             const int sy = srow % BY, sz = srow / BY;
             const int ly = negy ? BY - 1 - sy : sy, lz = negz ? BZ - 1 - sz : sz;
-            *reinterpret_cast<float4*>(sg + (lz * BY + ly) * BX + 4 * h) =
-                *reinterpret_cast<const float4*>(st + srow * BX + 4 * h);
+            cp_async16(sg + (lz * BY + ly) * BX + 4 * h, st + srow * BX + 4 * h);   // with the faces' group
         }
     }
     const size_t og = (size_t)oct * ngrp + grp;
     float* gx = p.xf + ((og * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * fxn) * 32;
     float* gy = p.yf + ((og * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * fyn) * 32;
     float* gz = p.zf + ((og * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * fzn) * 32;
-    batch_faces_in<fxn>(fx, gx, ta > 0);
-    batch_faces_in<fyn>(fy, gy, tb > 0);
-    batch_faces_in<fzn>(fz, gz, tc > 0);
+    batch_faces_in_async<fxn>(fx, gx, ta > 0);   // land with the first line's sources
+    batch_faces_in_async<fyn>(fy, gy, tb > 0);
+    batch_faces_in_async<fzn>(fz, gz, tc > 0);
+    cp_async_commit();
 
     const int nvx = p.nx - tx * BX, nvy = p.ny - ty * BY, nvz = p.nz - tz * BZ;
     constexpr unsigned FULL = (1u << BX) - 1u;
