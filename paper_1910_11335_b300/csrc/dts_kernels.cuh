@@ -732,7 +732,8 @@ __device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], flo
 
 template <int NDO, int K, int BX, bool PSI, bool NX>
 __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, const int oct, const int grp,
-                                                 const int ta, const int tb, const int tc, const unsigned okmask)
+                                                 const int ta, const int tb, const int tc, const unsigned okmask,
+                                                 const float (&mrow)[K], const float (&arow)[3])
 {
     using S = BatchShape<NDO, K, BX, PSI>;
     constexpr int BY = S::BY, BZ = S::BZ, BV = S::BV, SB = S::SB, NL = S::NL, NQ = S::NQ;
@@ -796,18 +797,13 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     // phase A/B lane: (source bl, direction d)
     const int bl = lane / NDO, d = lane - bl * NDO;
     const bool srcok = lane < NL && (okmask >> bl & 1u);
-    float ax = 0.f, ay = 0.f, az = 0.f;
     unsigned long long m2[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float m = srcok ? p.M[(n0 + d) * K + k] : 0.f;
+        const float m = srcok ? mrow[k] : 0.f;
         m2[k] = f2pack(m, m);
     }
-    if (srcok) {
-        ax = p.A[(n0 + d) * 3];
-        ay = p.A[(n0 + d) * 3 + 1];
-        az = p.A[(n0 + d) * 3 + 2];
-    }
+    const float ax = srcok ? arow[0] : 0.f, ay = srcok ? arow[1] : 0.f, az = srcok ? arow[2] : 0.f;
     const float asum = ax + ay + az;
     const float* trow = Tst + (srcok ? bl : 0) * TSTR;
     float* prow = Ps + (srcok ? bl : 0) * PSTR + d * BX;
@@ -980,24 +976,33 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     }
 }
 
+// s0, cnt: the stage's first entry in stage_tiles and its tile count (kernel
+// arguments, so a CTA's first dependent global load is its tile)
 template <int NDO, int K, int BX, bool PSI>
-__global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float> p, const int stage)
+__global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float> p, const int s0, const int cnt)
 {
-    constexpr int SB = BatchShape<NDO, K, BX, PSI>::SB;
-    const int s0 = p.stage_off[stage], cnt = p.stage_off[stage + 1] - s0;
+    using S = BatchShape<NDO, K, BX, PSI>;
     int bid = blockIdx.x;
     const int tl = bid % cnt;
     bid /= cnt;
-    const int oct = bid & 7, grp = bid >> 3, b0 = grp * SB;
-    const int nb = min(SB, p.B - b0);
+    const int oct = bid & 7, grp = bid >> 3, b0 = grp * S::SB;
+    // the loads that depend on nothing else go first: tile, lane operator row, source flags
+    const unsigned pk = p.stage_tiles[s0 + tl];
+    const int lane = threadIdx.x, d = lane % NDO;
+    const bool dl = lane < S::NL;
+    float mrow[K], arow[3];
+#pragma unroll
+    for (int k = 0; k < K; ++k) mrow[k] = dl ? p.M[(oct * NDO + d) * K + k] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) arow[j] = dl ? p.A[(oct * NDO + d) * 3 + j] : 0.f;
+    const int nb = min(S::SB, p.B - b0);
     unsigned okmask = 0;                           // sources of this warp still iterating
     for (int i = 0; i < nb; ++i)
         if (p.active[b0 + i]) okmask |= 1u << i;
     if (okmask == 0) return;
-    const unsigned pk = p.stage_tiles[s0 + tl];
     const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
-    if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true>(p, oct, grp, ta, tb, tc, okmask);
-    else sweep_batch_body<NDO, K, BX, PSI, false>(p, oct, grp, ta, tb, tc, okmask);
+    if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+    else sweep_batch_body<NDO, K, BX, PSI, false>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
 }
 
 // Translation units that only launch the sweep define DTS_SWEEP_KERNEL_ONLY so

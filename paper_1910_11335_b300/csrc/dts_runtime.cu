@@ -348,8 +348,10 @@ int batch_sources_per_warp(const dts_problem* p) { return 32 / p->ndo; }
 // partials, so it is taken where that is less traffic (e.g. S8 with P3)
 bool psi_form(const dts_problem* p) { return batch_tile(p) && 8 * p->K > p->nd; }
 
+using BatchFn = void (*)(const SweepParams<float>, int, int);
+
 template <int NDO, int BX, bool PSI>
-SweepFn<float> batch_fn_k(int K)
+BatchFn batch_fn_k(int K)
 {
     switch (K) {
     case 1: return k_sweep_batch<NDO, 1, BX, PSI>;
@@ -385,7 +387,7 @@ size_t batch_smem_x(int ndo, int K)
 }
 
 template <int BX, bool PSI>
-SweepFn<float> batch_fn_x(int ndo, int K)
+BatchFn batch_fn_x(int ndo, int K)
 {
     switch (ndo) {
     case 1: return batch_fn_k<1, BX, PSI>(K);
@@ -396,7 +398,7 @@ SweepFn<float> batch_fn_x(int ndo, int K)
     return nullptr;
 }
 
-SweepFn<float> batch_fn(const dts_problem* p)
+BatchFn batch_fn(const dts_problem* p)
 {
     if (p->psi_mode) return p->TX == 8 ? batch_fn_x<8, true>(p->ndo, p->K) : batch_fn_x<4, true>(p->ndo, p->K);
     return p->TX == 8 ? batch_fn_x<8, false>(p->ndo, p->K) : batch_fn_x<4, false>(p->ndo, p->K);
@@ -434,9 +436,6 @@ void psi_fns(const dts_problem* p, RedPsiFn& r, PushPsiFn& u)
 template <typename R>
 SweepFn<R> sweep_fn(const dts_problem* p)
 {
-    if constexpr (sizeof(R) == 4) {
-        if (batch_tile(p)) return batch_fn(p);
-    }
     if (line_tile(p))
         return p->TY == 4 ? lines_fn<R, 4, 8>(p->ndo, p->K) : lines_fn<R, 8, 4>(p->ndo, p->K);
     return sweep_fn_generic<R>(p->ndo, p->K);
@@ -516,9 +515,21 @@ dts_status record_sweep(dts_problem* p)
     sp.T = (const R*)p->T; sp.sigt = (const R*)p->sigt_r; sp.part = (R*)p->part;
     sp.xf = (R*)p->xf; sp.yf = (R*)p->yf; sp.zf = (R*)p->zf;
     sp.active = p->active; sp.leak = p->leak;
+    const size_t smem = sweep_smem(p);
+    if constexpr (sizeof(R) == 4) {
+        if (batch_tile(p)) {   // the batched kernel takes the stage's (first tile, count) directly
+            BatchFn bf = batch_fn(p);
+            if (!bf) return fail(p, DTS_ERR_INTERNAL, "no sweep kernel for this (S_N, P_L)");
+            const unsigned groups = (unsigned)((p->B + batch_sources_per_warp(p) - 1) / batch_sources_per_warp(p));
+            for (int s = 0; s < p->n_stages; ++s) {
+                const int s0 = p->stage_off_h[s], cnt = p->stage_off_h[s + 1] - s0;
+                bf<<<(unsigned)cnt * 8u * groups, 32, smem, p->stream>>>(sp, s0, cnt);
+            }
+            return DTS_OK;
+        }
+    }
     SweepFn<R> sf = sweep_fn<R>(p);
     if (!sf) return fail(p, DTS_ERR_INTERNAL, "no sweep kernel for this (S_N, P_L)");
-    const size_t smem = sweep_smem(p);
     const int nthr = sweep_threads(p);
     for (int s = 0; s < p->n_stages; ++s) {
         const int cnt = p->stage_off_h[s + 1] - p->stage_off_h[s];
@@ -594,6 +605,8 @@ dts_status build_graph(dts_problem* p)
     cudaError_t e;
     if (p->fp64) e = cudaFuncSetAttribute(sweep_fn<double>(p),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (batch_tile(p)) e = cudaFuncSetAttribute(batch_fn(p),
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else e = cudaFuncSetAttribute(sweep_fn<float>(p),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(p, DTS_ERR_CUDA, std::string("sweep smem attribute: ") + cudaGetErrorString(e));
