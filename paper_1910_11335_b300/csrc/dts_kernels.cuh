@@ -702,13 +702,25 @@ template <int BX, bool NX, bool CHECK>
 __device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], float* zrow, const float* srow,
                                            float& xin, unsigned vm, float ax, float ay, float az, float asum)
 {
+    // the line's z-faces and sigma_t go to registers first, off the cell-to-cell chain
+    float zv[BX], sv[BX];
+#pragma unroll
+    for (int lx = 0; lx < BX; ++lx) zv[lx] = zrow[lx * 32];
+#pragma unroll
+    for (int h = 0; h < BX / 4; ++h) {
+        const float4 s4 = *reinterpret_cast<const float4*>(srow + 4 * h);
+        sv[4 * h] = s4.x;
+        sv[4 * h + 1] = s4.y;
+        sv[4 * h + 2] = s4.z;
+        sv[4 * h + 3] = s4.w;
+    }
 #pragma unroll
     for (int lx = 0; lx < BX; ++lx) {
         const int sx = NX ? BX - 1 - lx : lx;
-        const float yin = yv[lx], zin = zrow[lx * 32];
+        const float yin = yv[lx], zin = zv[lx];
         float psi, ox, oy, oz;
         if (!CHECK || (vm >> sx & 1u)) {
-            const float q = qv[sx], sig = srow[sx];
+            const float q = qv[sx], sig = sv[sx];
             psi = __fdividef(fmaf(ax, xin, fmaf(ay, yin, fmaf(az, zin, q))), sig + asum);
             ox = fmaf(2.f, psi, -xin);
             oy = fmaf(2.f, psi, -yin);
