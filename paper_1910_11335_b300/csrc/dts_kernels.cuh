@@ -725,7 +725,8 @@ __device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], flo
             ox = fmaf(2.f, psi, -xin);
             oy = fmaf(2.f, psi, -yin);
             oz = fmaf(2.f, psi, -zin);
-            const bool neg = fminf(ox, fminf(oy, oz)) < 0.f;
+            // any sign bit set (a -0 outflow only enters the fixup to leave it unchanged)
+            const bool neg = (__float_as_int(ox) | __float_as_int(oy) | __float_as_int(oz)) < 0;
             if (__any_sync(0xffffffffu, neg)) {
                 if (neg) batch_fixup(q, sig, ax, ay, az, xin, yin, zin, psi, ox, oy, oz);
             }
@@ -925,8 +926,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
                     *reinterpret_cast<float4*>(dst + 4 * qd) =
                         make_float4(qv[4 * qd], qv[4 * qd + 1], qv[4 * qd + 2], qv[4 * qd + 3]);
             }
-            __syncwarp();   // every lane is done with this line's staged sources before they are refilled
-            continue;
+            continue;   // the staging buffer was released after phase A
         } else if (srcok) {
 #pragma unroll
             for (int qd = 0; qd < NQ; ++qd)
