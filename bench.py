@@ -193,7 +193,7 @@ def run_reference(args):
 MEASURED_TRAFFIC = {
     ("k_sweep_batch", "batch96_s8p3_19g_x32", (8, 4, 4)): {
         "dram_over_algorithmic": 1.33,
-        "source_sha256": "732bb492dd67a6fd3b0a238f47f3a49076328fe63e85a4426895021ba7abd49f",
+        "source_sha256": "68360d3ed6fa8192e1e03f9fb45e39e56ba7e1c49055f93b6ed52622cf6d45e4",
     },
 }
 

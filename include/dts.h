@@ -146,6 +146,23 @@ dts_status dts_set_materials(dts_problem *p, int n_mat, const double *sigma_t,
 dts_status dts_set_source(dts_problem *p, int batch_index, const dts_source *src);
 
 /*
+ * Several cone beams summed into one source for batch member batch_index (the
+ * CT mode of Sec. II.E and the results section: 16 cones around the phantom
+ * in one solve). cones[0..n_cones-1] are kind-1 sources (host memory, copied).
+ * By linearity the uncollided fluence is the sum of the cones' (Eq. 4 per
+ * cone) and the first-collision source (Eq. 5) the sum of theirs, which the
+ * solver forms as sum_g' sigma_s,l(g'->g) U_lm^g' with
+ * U_lm^g(v) = sum_c phi_u,c^g(v) Y_lm(Omega_c(v)) (one extra [G][K][V] FP64
+ * array per such member). At most 8 materials. The adjoint
+ * (dts_solve_adjoint) covers kind 0 and kind 1 only. A later dts_set_source
+ * on the member replaces the cones.
+ * Errors: DTS_ERR_INVALID_ARG (index, n_cones outside 1..4096, a cone that is
+ * not kind 1 or has NULL / non-finite data), DTS_ERR_OOM.
+ */
+dts_status dts_set_source_cones(dts_problem *p, int batch_index, int n_cones,
+                                const dts_source *cones);
+
+/*
  * Solve every batch member: ray trace (Eq. 4), first-collision source (Eq. 5),
  * then for g = 0..G-1 source iteration to tol (Eqs. 2-3, 6-7) followed by the
  * downscatter into later groups. Blocks until the results are on the device.

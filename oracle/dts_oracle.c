@@ -233,10 +233,13 @@ typedef struct {
 } ora_problem;
 
 typedef struct {
-    int kind;                /* 0 volumetric, 1 point / cone */
+    int kind;                /* 0 volumetric, 1 point / cone, 2 sum of point / cone sources */
     const double *q;         /* kind 0: [G][V] photons/cm^3 */
     double pos[3], axis[3], half_angle;
     const double *spectrum;  /* kind 1: [G] */
+    int n_cones;             /* kind 2: number of cones */
+    const double *cone_geo;  /* kind 2: [n_cones][7] pos, axis, half-angle */
+    const double *cone_spec; /* kind 2: [n_cones][G] */
 } ora_source;
 
 typedef struct {
@@ -467,7 +470,7 @@ int ora_solve(const ora_problem *p, const ora_source *s, ora_result *res)
     const double vol = p->dx * p->dy * p->dz;
     int nd, n, k, g, v, l, m, it, o;
     double mu[80], eta[80], xi[80], w[80];
-    double *Y, *D, *M, *phi_u, *omu, *F, *phi, *T, *sigt, *sigs, *part, *leak_o;
+    double *Y, *D, *M, *phi_u, *omu, *F, *phi, *T, *sigt, *sigs, *part, *leak_o, *uy = NULL;
     int64_t *fix_o;
     int npo, nthreads = p->n_threads > 0 ? p->n_threads : 1;
 
@@ -510,6 +513,35 @@ int ora_solve(const ora_problem *p, const ora_source *s, ora_result *res)
         }
         free(pg);
     }
+    /* several cones summed into one source (the CT mode of Sec. II.E): the
+     * uncollided fluence is the sum of the cones' and the first-collision
+     * source needs, per group and moment, sum_c phi_u,c Y_lm(Omega_c) */
+    if (s->kind == 2) {
+        double *pg = (double *)malloc(sizeof(double) * G), om[3];
+        int c;
+        uy = (double *)calloc((size_t)G * K * V, sizeof(double));
+        for (c = 0; c < s->n_cones; ++c) {
+            ora_source one;
+            memset(&one, 0, sizeof one);
+            one.kind = 1;
+            for (l = 0; l < 3; ++l) {
+                one.pos[l] = s->cone_geo[7 * c + l];
+                one.axis[l] = s->cone_geo[7 * c + 3 + l];
+            }
+            one.half_angle = s->cone_geo[7 * c + 6];
+            one.spectrum = s->cone_spec + (size_t)c * G;
+            for (v = 0; v < V; ++v) {
+                ora_uncollided_voxel(p, &one, v, pg, om);
+                for (g = 0; g < G; ++g) {
+                    phi_u[(size_t)g * V + v] += pg[g];
+                    for (l = 0; l <= L; ++l)
+                        for (m = -l; m <= l; ++m)
+                            uy[((size_t)g * K + l * l + l + m) * V + v] += pg[g] * ora_real_sh(l, m, om[0], om[1], om[2]);
+                }
+            }
+        }
+        free(pg);
+    }
     if (res->phi_u) memcpy(res->phi_u, phi_u, sizeof(double) * (size_t)G * V);
 
     for (g = 0; g < G; ++g) {
@@ -526,6 +558,9 @@ int ora_solve(const ora_problem *p, const ora_source *s, ora_result *res)
                 int gp;
                 if (s->kind == 0) {
                     if (k == 0) f = s->q[(size_t)g * V + v];
+                } else if (s->kind == 2) {
+                    for (gp = 0; gp <= g; ++gp)
+                        f += ora_sigs(p, v, l, gp, g) * uy[((size_t)gp * K + k) * V + v];
                 } else {
                     double y = ora_real_sh(l, m, omu[3 * v], omu[3 * v + 1], omu[3 * v + 2]);
                     for (gp = 0; gp <= g; ++gp)
@@ -603,7 +638,7 @@ int ora_solve(const ora_problem *p, const ora_source *s, ora_result *res)
         if (res->fixups) res->fixups[g] = nfix_g;
         memcpy(res->phi_c + (size_t)g * K * V, phi, sizeof(double) * (size_t)K * V);
     }
-    free(Y); free(D); free(M); free(phi_u); free(omu); free(F); free(phi); free(T);
+    free(Y); free(D); free(M); free(phi_u); free(omu); free(F); free(phi); free(T); free(uy);
     free(sigt); free(sigs); free(part); free(leak_o); free(fix_o);
     return 0;
 }
@@ -701,6 +736,7 @@ static int ora_l_of_k(int k)
 int ora_adjoint(const ora_problem *p, const ora_source *s, const double *dL_dphi,
                 double *dL_dscale_t, double *dL_dscale_s, double *dsig_t_g)
 {
+    if (s->kind == 2) return -3;   /* the adjoint covers volumetric and single-cone sources */
     const int V = p->nx * p->ny * p->nz, G = p->G, L = p->L, K = (L + 1) * (L + 1);
     int nd, n, k, g, gp, v, it, l;
     double mu[80], eta[80], xi[80], w[80];

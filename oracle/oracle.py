@@ -47,7 +47,8 @@ class _Problem(C.Structure):
 
 class _Source(C.Structure):
     _fields_ = [("kind", C.c_int), ("q", _dp), ("pos", C.c_double * 3),
-                ("axis", C.c_double * 3), ("half_angle", C.c_double), ("spectrum", _dp)]
+                ("axis", C.c_double * 3), ("half_angle", C.c_double), ("spectrum", _dp),
+                ("n_cones", C.c_int), ("cone_geo", _dp), ("cone_spec", _dp)]
 
 
 class _Result(C.Structure):
@@ -162,9 +163,15 @@ def _problem(w, tol=None, max_iters=None, n_threads=1, keep=None, fixup=True):
 def _source(src, keep):
     q = None if src.q is None else np.ascontiguousarray(src.q, dtype=np.float64)
     spec = None if src.spectrum is None else np.ascontiguousarray(src.spectrum, dtype=np.float64)
-    keep += [q, spec]
+    geo = cspec = None
+    n = 0
+    if src.kind == 2:
+        n = len(src.cones)
+        geo = np.ascontiguousarray([[*c.pos, *c.axis, c.half_angle] for c in src.cones], dtype=np.float64)
+        cspec = np.ascontiguousarray([c.spectrum for c in src.cones], dtype=np.float64)
+    keep += [q, spec, geo, cspec]
     s = _Source(src.kind, _ptr(q), (C.c_double * 3)(*src.pos), (C.c_double * 3)(*src.axis),
-                src.half_angle, _ptr(spec))
+                src.half_angle, _ptr(spec), n, _ptr(geo), _ptr(cspec))
     return s
 
 

@@ -1559,33 +1559,29 @@ __global__ void k_raytrace(const RayParams p, int g0)
 constexpr int kRayMats = 8;
 constexpr int kRayThreads = 128;
 
-__global__ void __launch_bounds__(kRayThreads) k_raytrace_mat(const RayParams p)
+// Path length through every material (weighted by the voxel's sigma_t scale)
+// on the segment from the source point P to the centre of voxel v, written to
+// Ls[m * kRayThreads] (this thread's column of a shared-memory table), for a
+// source collimated to a cone (axis, half angle; >= pi: isotropic). Returns
+// false when the voxel is outside the cone; r2 = |C - P|^2 and om the unit
+// direction of flight are set either way.
+__device__ inline bool ray_lengths(const RayParams& p, int v, const double* s7, double* Ls, double& r2,
+                                   double (&om)[3])
 {
-    __shared__ double Ls[kRayMats][kRayThreads];
-    const int tid = threadIdx.x;
-    const int v = blockIdx.x * blockDim.x + tid;
-    const int b = blockIdx.y;
-    if (v >= p.V) return;
 #pragma unroll
-    for (int m = 0; m < kRayMats; ++m) Ls[m][tid] = 0.0;
-    const double* s = p.src + (size_t)b * 8;
-    double* out = p.unc + (size_t)b * p.G * p.V + v;
-    if (s[0] != 1.0) {
-        for (int g = 0; g < p.G; ++g) out[(size_t)g * p.V] = 0.0;
-        return;
-    }
+    for (int m = 0; m < kRayMats; ++m) Ls[m * kRayThreads] = 0.0;
     const int cx = v % p.nx, cy = (v / p.nx) % p.ny, cz = v / (p.nx * p.ny);
-    const double Px = s[1], Py = s[2], Pz = s[3];
+    const double Px = s7[0], Py = s7[1], Pz = s7[2];
     const double dx = p.x0 + (cx + 0.5) * p.dx - Px, dy = p.y0 + (cy + 0.5) * p.dy - Py,
                  dz = p.z0 + (cz + 0.5) * p.dz - Pz;
-    const double r2 = dx * dx + dy * dy + dz * dz;
+    r2 = dx * dx + dy * dy + dz * dz;
     const double r = sqrt(r2);
-    const double an = sqrt(s[4] * s[4] + s[5] * s[5] + s[6] * s[6]);
-    const double cosang = (dx * s[4] + dy * s[5] + dz * s[6]) / (r * an);
-    if (s[7] < kPi && cosang < cos(s[7])) {
-        for (int g = 0; g < p.G; ++g) out[(size_t)g * p.V] = 0.0;
-        return;
-    }
+    om[0] = dx / r;
+    om[1] = dy / r;
+    om[2] = dz / r;
+    const double an = sqrt(s7[3] * s7[3] + s7[4] * s7[4] + s7[5] * s7[5]);
+    const double cosang = (dx * s7[3] + dy * s7[4] + dz * s7[5]) / (r * an);
+    if (s7[6] < kPi && cosang < cos(s7[6])) return false;
     // parameter where the segment P -> C enters the grid box
     double a_in = 0.0;
     auto enter = [&](double lo, int n, double h, double P, double d) {
@@ -1627,7 +1623,7 @@ __global__ void __launch_bounds__(kRayThreads) k_raytrace_mat(const RayParams p)
         if (seg > 0.0) {
             const int vv = (iz * p.ny + iy) * p.nx + ix;
             const int m = p.mat[vv];
-            Ls[m][tid] += p.scale_t ? p.scale_t[vv] * seg : seg;
+            Ls[m * kRayThreads] += p.scale_t ? p.scale_t[vv] * seg : seg;
         }
         if (a1 >= 1.0) break;
         acur = a1;
@@ -1645,6 +1641,23 @@ __global__ void __launch_bounds__(kRayThreads) k_raytrace_mat(const RayParams p)
             tz = (p.z0 + (iz + (sz > 0 ? 1 : 0)) * p.dz - Pz) * ivz;
         }
     }
+    return true;
+}
+
+__global__ void __launch_bounds__(kRayThreads) k_raytrace_mat(const RayParams p)
+{
+    __shared__ double Ls[kRayMats][kRayThreads];
+    const int tid = threadIdx.x;
+    const int v = blockIdx.x * blockDim.x + tid;
+    const int b = blockIdx.y;
+    if (v >= p.V) return;
+    const double* s = p.src + (size_t)b * 8;
+    double* out = p.unc + (size_t)b * p.G * p.V + v;
+    double r2, om[3];
+    if (s[0] != 1.0 || !ray_lengths(p, v, s + 1, &Ls[0][tid], r2, om)) {
+        for (int g = 0; g < p.G; ++g) out[(size_t)g * p.V] = 0.0;
+        return;
+    }
     double Lm[kRayMats];
 #pragma unroll
     for (int m = 0; m < kRayMats; ++m) Lm[m] = Ls[m][tid];
@@ -1655,6 +1668,60 @@ __global__ void __launch_bounds__(kRayThreads) k_raytrace_mat(const RayParams p)
         for (int m = 0; m < kRayMats; ++m)
             if (m < p.n_mat) tau += Lm[m] * p.sigma_t[(size_t)m * p.G + g];
         out[(size_t)g * p.V] = p.spec[(size_t)b * p.G + g] * exp(-tau) * inv;
+    }
+}
+
+// Several cones summed into one source (batch members with n_cones[b] > 0):
+// the uncollided fluence is the sum of the cones' (Eq. 4 per cone) and, for
+// the first-collision source, U_lm^g(v) = sum_c phi_u,c^g(v) Y_lm(Omega_c(v))
+// is accumulated per group and moment (each thread owns its voxel).
+struct ConeParams {
+    const double* geo;     // [B][cap][8]: pos, axis, half angle
+    const double* spec;    // [B][cap][G]
+    const int* n_cones;    // [B]
+    const int* slot;       // [B] row of U, -1 for none
+    double* U;             // [slots][G][K][V]
+    int cap, K, L;
+};
+
+__global__ void __launch_bounds__(kRayThreads) k_raytrace_cones(const RayParams p, const ConeParams cp)
+{
+    __shared__ double Ls[kRayMats][kRayThreads];
+    const int tid = threadIdx.x;
+    const int v = blockIdx.x * blockDim.x + tid;
+    const int b = blockIdx.y;
+    const int nc = cp.n_cones[b];
+    if (v >= p.V || nc <= 0) return;
+    double* out = p.unc + (size_t)b * p.G * p.V + v;
+    double* U = cp.U + (size_t)cp.slot[b] * p.G * cp.K * p.V + v;
+    for (int c = 0; c < nc; ++c) {
+        const double* s7 = cp.geo + ((size_t)b * cp.cap + c) * 8;
+        const double* spec = cp.spec + ((size_t)b * cp.cap + c) * p.G;
+        double r2, om[3];
+        const bool in = ray_lengths(p, v, s7, &Ls[0][tid], r2, om);
+        double Lm[kRayMats], Y[16];
+#pragma unroll
+        for (int m = 0; m < kRayMats; ++m) Lm[m] = Ls[m][tid];
+        sh_eval(cp.L, om[0], om[1], om[2], Y);
+        const double inv = 1.0 / (4.0 * kPi * r2);
+        for (int g = 0; g < p.G; ++g) {
+            double phi = 0.0;
+            if (in) {
+                double tau = 0.0;
+#pragma unroll
+                for (int m = 0; m < kRayMats; ++m)
+                    if (m < p.n_mat) tau += Lm[m] * p.sigma_t[(size_t)m * p.G + g];
+                phi = spec[g] * exp(-tau) * inv;
+            }
+            double* Ug = U + (size_t)g * cp.K * p.V;
+            if (c == 0) {
+                out[(size_t)g * p.V] = phi;
+                for (int k = 0; k < cp.K; ++k) Ug[(size_t)k * p.V] = phi * Y[k];
+            } else {
+                out[(size_t)g * p.V] += phi;
+                for (int k = 0; k < cp.K; ++k) Ug[(size_t)k * p.V] += phi * Y[k];
+            }
+        }
     }
 }
 
@@ -1671,6 +1738,8 @@ struct SrcParams {
     const double* unc;     // [B][G][V]
     const double* q;       // [B][G][V] or null
     const float* sigma_s_f;   // [n_mat][L+1][G][G] in FP32 (FP32 forms)
+    const double* U;       // [slots][G][K][V] cone-summed uncollided moments (kind 2), or null
+    const int* uslot;      // [B] row of U
     R* F;
     size_t Fstride;
     int V, W;              // W: downscatter band (sigma_s(g' -> g) = 0 for g - g' > W)
@@ -1700,6 +1769,20 @@ __global__ void k_fixed_source(const SrcParams<R> p, int gt, int slot)
     }
     const double* s = p.src + (size_t)b * 8;
     const int g0 = max(0, gt - p.W);   // groups outside the band add exact zeros
+    if (kind == 2) {
+        // several cones: F_lm = sum_g' sigma_s,l(g' -> g) scale_s U_lm^g'
+        const double* U = p.U + (size_t)p.uslot[b] * c.G * c.K * p.V + v;
+        const double ss = c.scale_s_t ? c.scale_s_t[ct] : 1.0;
+        for (int k = 0; k < c.K; ++k) {
+            const int l = l_of_k(k);
+            double acc = 0.0;
+            for (int gp = g0; gp <= gt; ++gp)
+                acc += c.sigma_s[(((size_t)m * (c.L + 1) + l) * c.G + gp) * c.G + gt] * ss *
+                       U[((size_t)gp * c.K + k) * p.V];
+            F[(size_t)k * c.TV] = (R)acc;
+        }
+        return;
+    }
     if constexpr (sizeof(R) == 4) {
         // FP32 form: the product is stored in FP32, so it is formed in FP32
         const float d0 = (float)(C[0] - s[1]), d1 = (float)(C[1] - s[2]), d2 = (float)(C[2] - s[3]);

@@ -79,6 +79,13 @@ struct dts_problem {
     void *T = nullptr, *part = nullptr, *xf = nullptr, *yf = nullptr, *zf = nullptr, *sigt_r = nullptr;
     double *unc = nullptr, *col = nullptr, *mom = nullptr, *q = nullptr, *tmp = nullptr;
     double *src = nullptr, *spec = nullptr, *leak = nullptr, *blk = nullptr, *status = nullptr;
+    // combined multi-cone sources (kind 2): per member its cones (host copies), device
+    // tables [B][cone_cap][8] / [B][cone_cap][G], and a row of U per such member
+    std::vector<std::vector<double>> cone_geo_h, cone_spec_h;
+    std::vector<int> cone_n_h, uslot_h;
+    int cone_cap = 0, n_uslots = 0;
+    double *cone_geo = nullptr, *cone_spec = nullptr, *U = nullptr;
+    int *cone_n = nullptr, *uslot = nullptr;
     int *active = nullptr, *ctl = nullptr;
     size_t Fstride = 0;
     int F_W = -1;
@@ -657,7 +664,7 @@ void launch_fixed_source(dts_problem* p, int gt, int slot)
     SrcParams<R> sp;
     sp.c = cell_params(p);
     sp.src = p->src; sp.unc = p->unc; sp.q = p->q; sp.F = (R*)p->F; sp.Fstride = p->Fstride;
-    sp.V = p->V; sp.W = p->W; sp.sigma_s_f = p->sigma_s_f;
+    sp.V = p->V; sp.W = p->W; sp.sigma_s_f = p->sigma_s_f; sp.U = p->U; sp.uslot = p->uslot;
     k_fixed_source<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(sp, gt, slot);
 }
 
@@ -706,6 +713,14 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         } else {
             for (int g0 = 0; g0 < G; g0 += kRayGroups)
                 k_raytrace<<<dim3((p->V + 127) / 128, B), 128, 0, p->stream>>>(rp, g0);
+        }
+        if (p->n_uslots > 0) {   // members with several cones
+            if (p->n_mat > kRayMats)
+                return fail(p, DTS_ERR_INVALID_ARG, "combined cone sources need at most 8 materials");
+            ConeParams cp;
+            cp.geo = p->cone_geo; cp.spec = p->cone_spec; cp.n_cones = p->cone_n; cp.slot = p->uslot;
+            cp.U = p->U; cp.cap = p->cone_cap; cp.K = p->K; cp.L = p->L;
+            k_raytrace_cones<<<dim3((p->V + kRayThreads - 1) / kRayThreads, B), kRayThreads, 0, p->stream>>>(rp, cp);
         }
         CK(cudaGetLastError());
     }
@@ -1045,6 +1060,14 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     CK(cudaMallocHost((void**)&p->h_active, sizeof(int) * B));
     p->src_h.assign(B * 8, 0.0);
     for (size_t b = 0; b < B; ++b) p->src_h[b * 8] = -1.0;
+    p->cone_geo_h.assign(B, {});
+    p->cone_spec_h.assign(B, {});
+    p->cone_n_h.assign(B, 0);
+    p->uslot_h.assign(B, -1);
+    TRY(dalloc_t(p, &p->cone_n, B));
+    TRY(dalloc_t(p, &p->uslot, B));
+    CK(cudaMemset(p->cone_n, 0, sizeof(int) * B));
+    CK(cudaMemset(p->uslot, 0, sizeof(int) * B));
     p->spec_h.assign(B * G, 0.0);
     p->src_set.assign(B, 0);
     p->iters.assign(B * G, 0);
@@ -1376,6 +1399,10 @@ dts_status dts_set_source(dts_problem* p, int batch_index, const dts_source* s)
     const int G = p->G, V = p->V;
     DevGuard guard(p->d.device);
     double* row = &p->src_h[(size_t)batch_index * 8];
+    if (p->cone_n_h[batch_index] != 0) {   // the member stops being a combined source
+        p->cone_n_h[batch_index] = 0;
+        CK(cudaMemcpy(p->cone_n + batch_index, &p->cone_n_h[batch_index], sizeof(int), cudaMemcpyHostToDevice));
+    }
     if (s->kind == 0) {
         if (!s->q) return fail(p, DTS_ERR_INVALID_ARG, "kind 0 needs q");
         for (size_t i = 0; i < (size_t)G * V; ++i)
@@ -1412,6 +1439,80 @@ dts_status dts_set_source(dts_problem* p, int batch_index, const dts_source* s)
     CK(cudaMemcpy(p->src + (size_t)batch_index * 8, row, sizeof(double) * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->spec + (size_t)batch_index * G, &p->spec_h[(size_t)batch_index * G],
                   sizeof(double) * G, cudaMemcpyHostToDevice));
+    p->src_set[batch_index] = 1;
+    p->solved = false;
+    return DTS_OK;
+}
+
+dts_status dts_set_source_cones(dts_problem* p, int batch_index, int n_cones, const dts_source* cones)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!cones) return fail(p, DTS_ERR_INVALID_ARG, "cones is NULL");
+    if (batch_index < 0 || batch_index >= p->B) return fail(p, DTS_ERR_INVALID_ARG, "batch_index out of range");
+    if (n_cones < 1 || n_cones > 4096) return fail(p, DTS_ERR_INVALID_ARG, "n_cones must be in 1..4096");
+    const int G = p->G, B = p->B;
+    std::vector<double> geo((size_t)n_cones * 8, 0.0), spec((size_t)n_cones * G);
+    for (int c = 0; c < n_cones; ++c) {
+        const dts_source* s = cones + c;
+        if (s->kind != 1) return fail(p, DTS_ERR_INVALID_ARG, "every cone must be a kind-1 source");
+        if (!s->spectrum) return fail(p, DTS_ERR_INVALID_ARG, "every cone needs a spectrum");
+        const double an = std::sqrt(s->axis[0] * s->axis[0] + s->axis[1] * s->axis[1] + s->axis[2] * s->axis[2]);
+        if (!(an > 0.0) || !isfin(an)) return fail(p, DTS_ERR_INVALID_ARG, "cone axis must be non-zero");
+        if (!(s->half_angle > 0.0) || !(s->half_angle <= kPi + 1e-12))
+            return fail(p, DTS_ERR_INVALID_ARG, "half_angle must be in (0, pi]");
+        for (int i = 0; i < 3; ++i) {
+            if (!isfin(s->pos[i])) return fail(p, DTS_ERR_INVALID_ARG, "source position must be finite");
+            geo[(size_t)c * 8 + i] = s->pos[i];
+            geo[(size_t)c * 8 + 3 + i] = s->axis[i];
+        }
+        geo[(size_t)c * 8 + 6] = s->half_angle >= kPi ? kPi : s->half_angle;
+        for (int g = 0; g < G; ++g) {
+            if (!isfin(s->spectrum[g]) || s->spectrum[g] < 0.0)
+                return fail(p, DTS_ERR_INVALID_ARG, "spectrum must be finite and >= 0");
+            spec[(size_t)c * G + g] = s->spectrum[g];
+        }
+    }
+    DevGuard guard(p->d.device);
+    CK(cudaStreamSynchronize(p->stream));
+    p->cone_geo_h[batch_index] = geo;
+    p->cone_spec_h[batch_index] = spec;
+    p->cone_n_h[batch_index] = n_cones;
+    if (n_cones > p->cone_cap) {   // wider tables: re-upload every member's cones
+        dfree(p, p->cone_geo);
+        dfree(p, p->cone_spec);
+        p->cone_geo = p->cone_spec = nullptr;
+        p->cone_cap = n_cones;
+        TRY(dalloc_t(p, &p->cone_geo, (size_t)B * p->cone_cap * 8));
+        TRY(dalloc_t(p, &p->cone_spec, (size_t)B * p->cone_cap * G));
+        for (int b = 0; b < B; ++b) {
+            const int n = (int)p->cone_geo_h[b].size() / 8;
+            if (n == 0) continue;
+            CK(cudaMemcpy(p->cone_geo + (size_t)b * p->cone_cap * 8, p->cone_geo_h[b].data(),
+                          sizeof(double) * n * 8, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(p->cone_spec + (size_t)b * p->cone_cap * G, p->cone_spec_h[b].data(),
+                          sizeof(double) * (size_t)n * G, cudaMemcpyHostToDevice));
+        }
+    } else {
+        CK(cudaMemcpy(p->cone_geo + (size_t)batch_index * p->cone_cap * 8, geo.data(), sizeof(double) * geo.size(),
+                      cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->cone_spec + (size_t)batch_index * p->cone_cap * G, spec.data(),
+                      sizeof(double) * spec.size(), cudaMemcpyHostToDevice));
+    }
+    if (p->uslot_h[batch_index] < 0) {   // a row of U for this member (recomputed by every solve)
+        p->uslot_h[batch_index] = p->n_uslots++;
+        dfree(p, p->U);
+        p->U = nullptr;
+        TRY(dalloc_t(p, &p->U, (size_t)p->n_uslots * G * p->K * p->V));
+        CK(cudaMemcpy(p->uslot, p->uslot_h.data(), sizeof(int) * B, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(p->cone_n + batch_index, &p->cone_n_h[batch_index], sizeof(int), cudaMemcpyHostToDevice));
+    double* row = &p->src_h[(size_t)batch_index * 8];
+    for (int i = 0; i < 8; ++i) row[i] = 0.0;
+    row[0] = 2.0;
+    for (int g = 0; g < G; ++g) p->spec_h[(size_t)batch_index * G + g] = 0.0;
+    CK(cudaMemcpy(p->src + (size_t)batch_index * 8, row, sizeof(double) * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->spec + (size_t)batch_index * G, &p->spec_h[(size_t)batch_index * G], sizeof(double) * G,
+                  cudaMemcpyHostToDevice));
     p->src_set[batch_index] = 1;
     p->solved = false;
     return DTS_OK;
@@ -1507,6 +1608,8 @@ dts_status dts_solve_adjoint(dts_problem* p, int batch_index, const double* dL_d
     if (!p->solved) return fail(p, DTS_ERR_STATE, "no forward solve has completed");
     if (batch_index < 0 || batch_index >= p->B) return fail(p, DTS_ERR_INVALID_ARG, "batch_index out of range");
     if (!dL_dphi || !dL_dscale_t || !dL_dscale_s) return fail(p, DTS_ERR_INVALID_ARG, "NULL pointer");
+    if (p->cone_n_h[batch_index] > 0)
+        return fail(p, DTS_ERR_STATE, "the adjoint covers volumetric and single-cone sources");
     DevGuard guard(p->d.device);
     TRY(adj_alloc(p));
     const size_t GV = (size_t)p->G * p->V, V = p->V;

@@ -67,7 +67,7 @@ EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_sol
            "dts_get_balance", "dts_last_error", "dts_destroy_problem", "dts_status_string",
            "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size",
            "dts_sweep_once_noalloc", "dts_solve_adjoint", "dts_get_adjoint_iterations",
-           "dts_tune_tile")
+           "dts_tune_tile", "dts_set_source_cones")
 
 
 def lib():
@@ -84,6 +84,7 @@ def lib():
         "dts_create_problem": ([C.POINTER(ProblemDesc), pp], C.c_int),
         "dts_set_materials": ([C.c_void_p, C.c_int, _dp, _dp, _ip, _dp, _dp], C.c_int),
         "dts_set_source": ([C.c_void_p, C.c_int, C.POINTER(SourceDesc)], C.c_int),
+        "dts_set_source_cones": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(SourceDesc)], C.c_int),
         "dts_solve": ([C.c_void_p, C.POINTER(SolveStats)], C.c_int),
         "dts_get_scalar_fluence": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
         "dts_get_moments": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
@@ -222,6 +223,14 @@ class Problem:
                                        mi.ctypes.data_as(_ip), _dptr(a), _dptr(b)), self._h)
 
     def set_source(self, b: int, src: inputs.Source):
+        if src.kind == 2:   # several cone beams summed into one source
+            specs = [np.ascontiguousarray(c.spectrum, dtype=np.float64) for c in src.cones]
+            arr = (SourceDesc * len(src.cones))()
+            for i, (c, sp) in enumerate(zip(src.cones, specs)):
+                arr[i] = SourceDesc(c.kind, None, (C.c_double * 3)(*c.pos), (C.c_double * 3)(*c.axis),
+                                    c.half_angle, _dptr(sp))
+            _check(lib().dts_set_source_cones(self._h, b, len(src.cones), arr), self._h)
+            return
         q = None if src.q is None else np.ascontiguousarray(src.q, dtype=np.float64)
         sp = None if src.spectrum is None else np.ascontiguousarray(src.spectrum, dtype=np.float64)
         s = SourceDesc(src.kind, _dptr(q), (C.c_double * 3)(*src.pos),

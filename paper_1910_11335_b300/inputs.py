@@ -40,7 +40,8 @@ class Source:
     kind 0: isotropic volumetric source ``q[G][V]`` in photons/cm^3 (total over
     4 pi). kind 1: point source at ``pos`` collimated to a cone around ``axis``
     with half-angle ``half_angle`` (radians; >= pi means isotropic), emitting
-    ``spectrum[g]`` photons per source particle into group g.
+    ``spectrum[g]`` photons per source particle into group g. kind 2: the sum
+    of the kind-1 sources in ``cones`` (several cone beams at once).
     """
     kind: int
     q: Optional[np.ndarray] = None
@@ -48,6 +49,7 @@ class Source:
     axis: tuple = (0.0, 1.0, 0.0)
     half_angle: float = math.pi
     spectrum: Optional[np.ndarray] = None
+    cones: Optional[list] = None
 
 
 @dataclasses.dataclass
@@ -384,6 +386,17 @@ def first_groups(w: Workload, n_groups: int) -> Workload:
     t.sources = srcs
     if w.group_energy_kev is not None:
         t.group_energy_kev = w.group_energy_kev[:n_groups]
+    return t
+
+
+def combined_cones(w: Workload, n_cones: int = 16, distance=50.0, half_angle=math.radians(15.0)) -> Workload:
+    """The same problem with one source made of n_cones cone beams on a ring (the
+    paper's CT mode of several cones at once), each with source 0's spectrum."""
+    import copy
+    t = copy.copy(w)
+    cones = ring_sources(w.sources[0].spectrum, n_cones, distance, half_angle)
+    t.sources = [Source(kind=2, cones=cones)]
+    t.name = f"{w.name}_cones{n_cones}"
     return t
 
 
