@@ -183,6 +183,21 @@ dts_status dts_get_scalar_fluence(dts_problem *p, int batch_index, dts_component
                                   double *out, size_t out_len, int out_is_device);
 
 /*
+ * Absorbed dose per source particle (Gy) of batch member batch_index from the
+ * scalar fluence of component comp: the post-processing module's conversion
+ * of photon fluence to absorbed dose (Sec. II.C), in the collision-kerma form
+ * since no electrons are transported (Sec. IV):
+ *   D(v) = c * sum_g phi_g(v) E_g (mu_en/rho)_g(mat(v)),  c = 1 MeV/g = 1.602176634e-10 Gy,
+ * groups summed in order. mu_en_rho [n_mat][G] (cm^2/g) and energy_mev [G]
+ * (MeV) are host arrays; out [V] natural order (x fastest), host memory or
+ * device memory (out_is_device), written on the problem's stream and
+ * synchronised. Errors: DTS_ERR_STATE (no solve), DTS_ERR_INVALID_ARG (index,
+ * component, NULL, out_len < V, negative or non-finite coefficients).
+ */
+dts_status dts_get_dose(dts_problem *p, int batch_index, dts_component comp, const double *mu_en_rho,
+                        const double *energy_mev, double *out, size_t out_len, int out_is_device);
+
+/*
  * All K = (L+1)^2 collided flux moments of one group, out[K][V], ordered
  * k = l*l + l + m with real spherical harmonics normalised so that
  * sum_m Y_lm(a) Y_lm(b) = P_l(a.b); k = 0 is the Eq. 3 scalar fluence.

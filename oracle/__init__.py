@@ -7,5 +7,6 @@ of the paper each part follows.
 """
 from .oracle import (  # noqa: F401
     build, load, quadrature, real_sh, sh_tables, subsweep_size, subsweep_cells,
-    dd_cell, sweep_dir, uncollided_voxel, solve, solve_workload, adjoint, OracleResult,
+    dd_cell, sweep_dir, uncollided_voxel, solve, solve_workload, adjoint, OracleResult, dose,
+    MEV_PER_G_TO_GY,
 )

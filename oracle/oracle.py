@@ -258,3 +258,21 @@ def solve_workload(w, **kw):
 
 def n_threads_available() -> int:
     return int(load().ora_has_openmp())
+
+
+MEV_PER_G_TO_GY = 1.602176634e-10   # 1 MeV/g in J/kg (elementary charge x 1e6 J/MeV / 1e-3 kg)
+
+
+def dose(phi, mat, mu_en_rho, energy_mev):
+    """Absorbed dose per source particle (Gy) from the scalar fluence phi[G][V]
+    (photons/cm^2 per source particle): the post-processing module's
+    fluence-to-dose conversion (Sec. II.C), in the collision-kerma form
+    D(v) = c sum_g phi_g(v) E_g (mu_en/rho)_g(mat(v)), c = 1 MeV/g in Gy, since
+    the method transports no electrons (Sec. IV). Plain numpy, one term per
+    group in group order."""
+    phi = np.asarray(phi, dtype=np.float64)
+    mat = np.asarray(mat).reshape(-1)
+    out = np.zeros(phi.shape[1])
+    for g in range(phi.shape[0]):
+        out += phi[g] * energy_mev[g] * mu_en_rho[mat, g]
+    return MEV_PER_G_TO_GY * out

@@ -1731,6 +1731,24 @@ __global__ void __launch_bounds__(kRayThreads) k_raytrace_cones(const RayParams 
 //   q_lm = sum_{g'<=gt} sigma_{s,l}^{g'->gt} phi_u^{g'} Y_lm(Omega_u)
 // or the volumetric source (l = 0 only).
 // ---------------------------------------------------------------------------
+// Fluence to absorbed dose (post-processing, collision-kerma form): per voxel
+// D = c sum_g (phi_g E_g) (mu_en/rho)_g(mat), groups in order; comp 0 uncollided,
+// 1 collided, 2 total (uncollided + collided).
+__global__ void k_dose(int V, int G, const double* u, const double* col, int comp, const int* mat,
+                       const double* mu_en, const double* e_mev, double c, double* out)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const double* mrow = mu_en + (size_t)mat[v] * G;
+    double acc = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double uf = u[(size_t)g * V + v], cf = col[(size_t)g * V + v];
+        const double phi = comp == 0 ? uf : comp == 1 ? cf : uf + cf;
+        acc += phi * e_mev[g] * mrow[g];
+    }
+    out[v] = c * acc;
+}
+
 template <typename R>
 struct SrcParams {
     CellParams c;

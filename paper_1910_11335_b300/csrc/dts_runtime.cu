@@ -1557,6 +1557,44 @@ dts_status dts_get_scalar_fluence(dts_problem* p, int batch_index, dts_component
     return DTS_OK;
 }
 
+dts_status dts_get_dose(dts_problem* p, int batch_index, dts_component comp, const double* mu_en_rho,
+                        const double* energy_mev, double* out, size_t out_len, int out_is_device)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->solved) return fail(p, DTS_ERR_STATE, "no solve has completed");
+    if (batch_index < 0 || batch_index >= p->B) return fail(p, DTS_ERR_INVALID_ARG, "batch_index out of range");
+    if (!mu_en_rho || !energy_mev || !out) return fail(p, DTS_ERR_INVALID_ARG, "NULL pointer");
+    if (comp != DTS_COMP_UNCOLLIDED && comp != DTS_COMP_COLLIDED && comp != DTS_COMP_TOTAL)
+        return fail(p, DTS_ERR_INVALID_ARG, "unknown component");
+    if (out_len < (size_t)p->V) return fail(p, DTS_ERR_INVALID_ARG, "out_len < V");
+    const int G = p->G, V = p->V;
+    for (size_t i = 0; i < (size_t)p->n_mat * G; ++i)
+        if (!isfin(mu_en_rho[i]) || mu_en_rho[i] < 0.0)
+            return fail(p, DTS_ERR_INVALID_ARG, "mu_en_rho must be finite and >= 0");
+    for (int g = 0; g < G; ++g)
+        if (!isfin(energy_mev[g]) || energy_mev[g] < 0.0)
+            return fail(p, DTS_ERR_INVALID_ARG, "energy_mev must be finite and >= 0");
+    DevGuard guard(p->d.device);
+    double* tab = nullptr;   // [n_mat][G] coefficients, then [G] energies
+    CK(cudaMallocAsync((void**)&tab, sizeof(double) * ((size_t)p->n_mat * G + G + (out_is_device ? 0 : V)),
+                       p->stream));
+    double* dout = out_is_device ? out : tab + (size_t)p->n_mat * G + G;
+    CK(cudaMemcpyAsync(tab, mu_en_rho, sizeof(double) * (size_t)p->n_mat * G, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(tab + (size_t)p->n_mat * G, energy_mev, sizeof(double) * G, cudaMemcpyHostToDevice,
+                       p->stream));
+    const size_t n = (size_t)G * V;
+    k_dose<<<(unsigned)((V + 255) / 256), 256, 0, p->stream>>>(
+        V, G, p->unc + (size_t)batch_index * n, p->col + (size_t)batch_index * n,
+        comp == DTS_COMP_UNCOLLIDED ? 0 : comp == DTS_COMP_COLLIDED ? 1 : 2, p->mat_nat, tab,
+        tab + (size_t)p->n_mat * G, 1.602176634e-10, dout);
+    CK(cudaGetLastError());
+    if (!out_is_device)
+        CK(cudaMemcpyAsync(out, dout, sizeof(double) * V, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaFreeAsync(tab, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    return DTS_OK;
+}
+
 dts_status dts_get_moments(dts_problem* p, int batch_index, int group, double* out, size_t out_len,
                            int out_is_device)
 {

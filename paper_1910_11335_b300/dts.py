@@ -67,7 +67,7 @@ EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_sol
            "dts_get_balance", "dts_last_error", "dts_destroy_problem", "dts_status_string",
            "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size",
            "dts_sweep_once_noalloc", "dts_solve_adjoint", "dts_get_adjoint_iterations",
-           "dts_tune_tile", "dts_set_source_cones")
+           "dts_tune_tile", "dts_set_source_cones", "dts_get_dose")
 
 
 def lib():
@@ -85,6 +85,7 @@ def lib():
         "dts_set_materials": ([C.c_void_p, C.c_int, _dp, _dp, _ip, _dp, _dp], C.c_int),
         "dts_set_source": ([C.c_void_p, C.c_int, C.POINTER(SourceDesc)], C.c_int),
         "dts_set_source_cones": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(SourceDesc)], C.c_int),
+        "dts_get_dose": ([C.c_void_p, C.c_int, C.c_int, _dp, _dp, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
         "dts_solve": ([C.c_void_p, C.POINTER(SolveStats)], C.c_int),
         "dts_get_scalar_fluence": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
         "dts_get_moments": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
@@ -260,6 +261,15 @@ class Problem:
         _check(lib().dts_get_scalar_fluence(self._h, b, comp, host.ctypes.data_as(C.c_void_p), n, 0),
                self._h)
         return host.reshape(self.G, self.V)
+
+    def dose(self, b: int, mu_en_rho, energy_mev, comp: int = TOTAL):
+        """Absorbed dose per source particle (Gy) [V] from fluence component comp."""
+        mu = np.ascontiguousarray(mu_en_rho, dtype=np.float64)
+        e = np.ascontiguousarray(energy_mev, dtype=np.float64)
+        out = np.empty(self.V)
+        _check(lib().dts_get_dose(self._h, b, comp, mu.ctypes.data_as(_dp), e.ctypes.data_as(_dp),
+                                  out.ctypes.data_as(C.c_void_p), out.size, 0), self._h)
+        return out
 
     def moments(self, b: int, g: int):
         out = np.empty(self.K * self.V)

@@ -389,6 +389,26 @@ def first_groups(w: Workload, n_groups: int) -> Workload:
     return t
 
 
+def dose_coefficients(w: Workload, seed_index: int = 7):
+    """Seeded synthetic mass energy-absorption coefficients mu_en/rho [n_mat][G]
+    (cm^2/g) and group energies E [G] (MeV) for the fluence-to-dose
+    post-processing (no measured data is present): a power law
+    a (E / 60 keV)^-p per material with p ~ U[1.5, 2.5] (photo-absorption
+    falling with energy) flattening to a floor of 0.02 cm^2/g; bone-like
+    materials get a ~ U[2, 4] x water, air ~ water."""
+    rng = rng_for(seed_index)
+    n_mat = w.sigma_t.shape[0]
+    e_kev = np.asarray(w.group_energy_kev if w.group_energy_kev is not None
+                       else np.linspace(120.0, 25.0, w.n_groups), dtype=np.float64)
+    a = np.empty(n_mat)
+    a[:] = rng.uniform(0.03, 0.05)                 # water at 60 keV
+    a[MAT_AIR] = a[MAT_WATER] * rng.uniform(0.9, 1.0)
+    a[2:] = a[MAT_WATER] * rng.uniform(2.0, 4.0, size=n_mat - 2)
+    p = rng.uniform(1.5, 2.5, size=n_mat)
+    mu = a[:, None] * (e_kev[None, :] / 60.0) ** (-p[:, None]) + 0.02
+    return mu, e_kev / 1000.0
+
+
 def combined_cones(w: Workload, n_cones: int = 16, distance=50.0, half_angle=math.radians(15.0)) -> Workload:
     """The same problem with one source made of n_cones cone beams on a ring (the
     paper's CT mode of several cones at once), each with source 0's spectrum."""
