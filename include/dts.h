@@ -92,6 +92,10 @@ typedef struct {
     double axis[3];             /* kind 1: cone axis (any non-zero length) */
     double half_angle;          /* kind 1: cone half-angle in radians, (0, pi]; pi = isotropic */
     const double *spectrum;     /* kind 1: [G] photons per source particle, host */
+    int aperture;               /* kind 1: 0 cone beam (half_angle), 1 fan beam (the fields below) */
+    double normal[3];           /* fan: normal of the fan plane, not parallel to axis */
+    double half_azimuth;        /* fan: half the azimuthal angle subtended in the fan plane, (0, pi] */
+    double half_polar;          /* fan: half the polar angle subtended out of the plane, (0, pi/2] */
 } dts_source;
 
 typedef struct {
@@ -140,7 +144,13 @@ dts_status dts_set_materials(dts_problem *p, int n_mat, const double *sigma_t,
  * kind 0: volumetric isotropic source q[G][V]; the uncollided component is
  *         then zero and the collided component holds the whole fluence.
  * kind 1: point source at pos emitting spectrum[g] photons per source particle
- *         isotropically into the cone |angle(r - pos, axis)| <= half_angle.
+ *         isotropically into its beam (Sec. II.C source types): a cone
+ *         |angle(r - pos, axis)| <= half_angle (aperture 0), or a fan
+ *         (aperture 1): with a = axis, n = normal made orthogonal to a and
+ *         t = n x a, the direction u = (r - pos)/|r - pos| is in the beam when
+ *         |asin(u.n)| <= half_polar and |atan2(u.t, u.a)| <= half_azimuth
+ *         (the paper's theta and phi are the full angles, 2 half_polar and
+ *         2 half_azimuth).
  * Errors: DTS_ERR_INVALID_ARG (index, kind, NULL or non-finite data).
  */
 dts_status dts_set_source(dts_problem *p, int batch_index, const dts_source *src);

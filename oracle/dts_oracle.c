@@ -238,9 +238,42 @@ typedef struct {
     double pos[3], axis[3], half_angle;
     const double *spectrum;  /* kind 1: [G] */
     int n_cones;             /* kind 2: number of cones */
-    const double *cone_geo;  /* kind 2: [n_cones][7] pos, axis, half-angle */
+    const double *cone_geo;  /* kind 2: [n_cones][13] pos, axis, half-angle, aperture, normal,
+                                half azimuth, half polar */
     const double *cone_spec; /* kind 2: [n_cones][G] */
+    int aperture;            /* kind 1: 0 cone (half_angle), 1 fan (the next three fields) */
+    double normal[3];        /* fan: normal of the fan plane (not parallel to axis) */
+    double half_azimuth;     /* fan: half the azimuthal angle subtended, in the fan plane */
+    double half_polar;       /* fan: half the polar angle subtended, out of the fan plane */
 } ora_source;
+
+/* Whether the unit direction u from the source lies in its beam (Sec. II.C
+ * source types). Cone: angle(u, axis) <= half_angle. Fan: in the frame of the
+ * central ray a, the fan-plane normal n (made orthogonal to a) and t = n x a,
+ * the elevation asin(u.n) and the azimuth atan2(u.t, u.a) lie within the half
+ * polar and half azimuthal angles. */
+static int ora_in_beam(const ora_source *s, const double u[3])
+{
+    double a[3], n[3], t[3], an, nn, na, ua, un, ut;
+    int i;
+    an = sqrt(s->axis[0] * s->axis[0] + s->axis[1] * s->axis[1] + s->axis[2] * s->axis[2]);
+    for (i = 0; i < 3; ++i) a[i] = s->axis[i] / an;
+    if (s->aperture != 1) {
+        if (s->half_angle >= ORA_PI) return 1;
+        return u[0] * a[0] + u[1] * a[1] + u[2] * a[2] >= cos(s->half_angle);
+    }
+    na = s->normal[0] * a[0] + s->normal[1] * a[1] + s->normal[2] * a[2];
+    for (i = 0; i < 3; ++i) n[i] = s->normal[i] - na * a[i];
+    nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (i = 0; i < 3; ++i) n[i] /= nn;
+    t[0] = n[1] * a[2] - n[2] * a[1];
+    t[1] = n[2] * a[0] - n[0] * a[2];
+    t[2] = n[0] * a[1] - n[1] * a[0];
+    ua = u[0] * a[0] + u[1] * a[1] + u[2] * a[2];
+    un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+    ut = u[0] * t[0] + u[1] * t[1] + u[2] * t[2];
+    return fabs(un) <= sin(s->half_polar) && fabs(atan2(ut, ua)) <= s->half_azimuth;
+}
 
 typedef struct {
     double *phi_u;      /* [G][V] uncollided fluence (kind 1), may be NULL */
@@ -325,7 +358,7 @@ int ora_uncollided_voxel(const ora_problem *p, const ora_source *s, int v,
 {
     int i = v % p->nx, j = (v / p->nx) % p->ny, k = v / (p->nx * p->ny), g, ns, t;
     int na = ora_max_alphas(p);
-    double C[3], d[3], r2, r, an, cosang, cmin;
+    double C[3], d[3], r2, r;
     double *alpha = (double *)malloc(sizeof(double) * na);
     int *sv = (int *)malloc(sizeof(int) * na);
     double *sl = (double *)malloc(sizeof(double) * na);
@@ -337,10 +370,7 @@ int ora_uncollided_voxel(const ora_problem *p, const ora_source *s, int v,
     r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     r = sqrt(r2);
     for (t = 0; t < 3; ++t) omega_u[t] = d[t] / r;
-    an = sqrt(s->axis[0] * s->axis[0] + s->axis[1] * s->axis[1] + s->axis[2] * s->axis[2]);
-    cosang = (d[0] * s->axis[0] + d[1] * s->axis[1] + d[2] * s->axis[2]) / (r * an);
-    cmin = cos(s->half_angle);
-    if (s->half_angle < ORA_PI && cosang < cmin) {
+    if (!ora_in_beam(s, omega_u)) {
         for (g = 0; g < p->G; ++g) phi_u_g[g] = 0.0;
     } else {
         ns = ora_segments(p, s->pos, C, alpha, sv, sl);
@@ -525,10 +555,14 @@ int ora_solve(const ora_problem *p, const ora_source *s, ora_result *res)
             memset(&one, 0, sizeof one);
             one.kind = 1;
             for (l = 0; l < 3; ++l) {
-                one.pos[l] = s->cone_geo[7 * c + l];
-                one.axis[l] = s->cone_geo[7 * c + 3 + l];
+                one.pos[l] = s->cone_geo[13 * c + l];
+                one.axis[l] = s->cone_geo[13 * c + 3 + l];
             }
-            one.half_angle = s->cone_geo[7 * c + 6];
+            one.half_angle = s->cone_geo[13 * c + 6];
+            one.aperture = (int)s->cone_geo[13 * c + 7];
+            for (l = 0; l < 3; ++l) one.normal[l] = s->cone_geo[13 * c + 8 + l];
+            one.half_azimuth = s->cone_geo[13 * c + 11];
+            one.half_polar = s->cone_geo[13 * c + 12];
             one.spectrum = s->cone_spec + (size_t)c * G;
             for (v = 0; v < V; ++v) {
                 ora_uncollided_voxel(p, &one, v, pg, om);

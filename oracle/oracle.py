@@ -48,7 +48,9 @@ class _Problem(C.Structure):
 class _Source(C.Structure):
     _fields_ = [("kind", C.c_int), ("q", _dp), ("pos", C.c_double * 3),
                 ("axis", C.c_double * 3), ("half_angle", C.c_double), ("spectrum", _dp),
-                ("n_cones", C.c_int), ("cone_geo", _dp), ("cone_spec", _dp)]
+                ("n_cones", C.c_int), ("cone_geo", _dp), ("cone_spec", _dp),
+                ("aperture", C.c_int), ("normal", C.c_double * 3), ("half_azimuth", C.c_double),
+                ("half_polar", C.c_double)]
 
 
 class _Result(C.Structure):
@@ -167,11 +169,13 @@ def _source(src, keep):
     n = 0
     if src.kind == 2:
         n = len(src.cones)
-        geo = np.ascontiguousarray([[*c.pos, *c.axis, c.half_angle] for c in src.cones], dtype=np.float64)
+        geo = np.ascontiguousarray([[*c.pos, *c.axis, c.half_angle, c.aperture, *c.normal, c.half_azimuth,
+                                     c.half_polar] for c in src.cones], dtype=np.float64)
         cspec = np.ascontiguousarray([c.spectrum for c in src.cones], dtype=np.float64)
     keep += [q, spec, geo, cspec]
     s = _Source(src.kind, _ptr(q), (C.c_double * 3)(*src.pos), (C.c_double * 3)(*src.axis),
-                src.half_angle, _ptr(spec), n, _ptr(geo), _ptr(cspec))
+                src.half_angle, _ptr(spec), n, _ptr(geo), _ptr(cspec), src.aperture,
+                (C.c_double * 3)(*src.normal), src.half_azimuth, src.half_polar)
     return s
 
 

@@ -1461,6 +1461,7 @@ __global__ void k_set_ctl(int* ctl, int g, int slot)
 // ---------------------------------------------------------------------------
 struct RayParams {
     int nx, ny, nz, V, G, n_mat;
+    const double* fan;             // [B][8]: aperture (0 cone, 1 fan), fan normal, half azimuth, half polar
     double dx, dy, dz, x0, y0, z0;
     const int* mat;                // natural [V]
     const double* scale_t;         // natural [V] or null
@@ -1469,6 +1470,29 @@ struct RayParams {
     const double* spec;            // [B][G]
     double* unc;                   // [B][G][V]
 };
+
+// Whether the unit direction u (source -> voxel centre) is in the beam.
+// s7: pos[3], axis[3], cone half-angle; f: aperture (0 cone, 1 fan), fan-plane
+// normal[3], half azimuth, half polar. Fan: with a = axis, n = normal made
+// orthogonal to a, t = n x a: |asin(u.n)| <= half polar and
+// |atan2(u.t, u.a)| <= half azimuth.
+__device__ inline bool in_beam(const double* s7, const double* f, const double (&u)[3])
+{
+    const double an = sqrt(s7[3] * s7[3] + s7[4] * s7[4] + s7[5] * s7[5]);
+    const double a[3] = {s7[3] / an, s7[4] / an, s7[5] / an};
+    const double ua = u[0] * a[0] + u[1] * a[1] + u[2] * a[2];
+    if (f == nullptr || f[0] != 1.0) return s7[6] >= kPi || ua >= cos(s7[6]);
+    const double na = f[1] * a[0] + f[2] * a[1] + f[3] * a[2];
+    double n[3] = {f[1] - na * a[0], f[2] - na * a[1], f[3] - na * a[2]};
+    const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    n[0] /= nn;
+    n[1] /= nn;
+    n[2] /= nn;
+    const double t[3] = {n[1] * a[2] - n[2] * a[1], n[2] * a[0] - n[0] * a[2], n[0] * a[1] - n[1] * a[0]};
+    const double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+    const double ut = u[0] * t[0] + u[1] * t[1] + u[2] * t[2];
+    return fabs(un) <= sin(f[5]) && fabs(atan2(ut, ua)) <= f[4];
+}
 
 __global__ void k_raytrace(const RayParams p, int g0)
 {
@@ -1492,9 +1516,8 @@ __global__ void k_raytrace(const RayParams p, int g0)
     }
     const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const double r = sqrt(r2);
-    const double an = sqrt(s[4] * s[4] + s[5] * s[5] + s[6] * s[6]);
-    const double cosang = (d[0] * s[4] + d[1] * s[5] + d[2] * s[6]) / (r * an);
-    if (s[7] < kPi && cosang < cos(s[7])) {
+    const double u[3] = {d[0] / r, d[1] / r, d[2] / r};
+    if (!in_beam(s + 1, p.fan + (size_t)b * 8, u)) {
         for (int gg = 0; gg < ng; ++gg) out[(size_t)gg * p.V] = 0.0;
         return;
     }
@@ -1565,8 +1588,8 @@ constexpr int kRayThreads = 128;
 // source collimated to a cone (axis, half angle; >= pi: isotropic). Returns
 // false when the voxel is outside the cone; r2 = |C - P|^2 and om the unit
 // direction of flight are set either way.
-__device__ inline bool ray_lengths(const RayParams& p, int v, const double* s7, double* Ls, double& r2,
-                                   double (&om)[3])
+__device__ inline bool ray_lengths(const RayParams& p, int v, const double* s7, const double* fan, double* Ls,
+                                   double& r2, double (&om)[3])
 {
 #pragma unroll
     for (int m = 0; m < kRayMats; ++m) Ls[m * kRayThreads] = 0.0;
@@ -1579,9 +1602,7 @@ __device__ inline bool ray_lengths(const RayParams& p, int v, const double* s7, 
     om[0] = dx / r;
     om[1] = dy / r;
     om[2] = dz / r;
-    const double an = sqrt(s7[3] * s7[3] + s7[4] * s7[4] + s7[5] * s7[5]);
-    const double cosang = (dx * s7[3] + dy * s7[4] + dz * s7[5]) / (r * an);
-    if (s7[6] < kPi && cosang < cos(s7[6])) return false;
+    if (!in_beam(s7, fan, om)) return false;
     // parameter where the segment P -> C enters the grid box
     double a_in = 0.0;
     auto enter = [&](double lo, int n, double h, double P, double d) {
@@ -1654,7 +1675,7 @@ __global__ void __launch_bounds__(kRayThreads) k_raytrace_mat(const RayParams p)
     const double* s = p.src + (size_t)b * 8;
     double* out = p.unc + (size_t)b * p.G * p.V + v;
     double r2, om[3];
-    if (s[0] != 1.0 || !ray_lengths(p, v, s + 1, &Ls[0][tid], r2, om)) {
+    if (s[0] != 1.0 || !ray_lengths(p, v, s + 1, p.fan + (size_t)b * 8, &Ls[0][tid], r2, om)) {
         for (int g = 0; g < p.G; ++g) out[(size_t)g * p.V] = 0.0;
         return;
     }
@@ -1676,7 +1697,7 @@ __global__ void __launch_bounds__(kRayThreads) k_raytrace_mat(const RayParams p)
 // the first-collision source, U_lm^g(v) = sum_c phi_u,c^g(v) Y_lm(Omega_c(v))
 // is accumulated per group and moment (each thread owns its voxel).
 struct ConeParams {
-    const double* geo;     // [B][cap][8]: pos, axis, half angle
+    const double* geo;     // [B][cap][16]: pos, axis, half angle, aperture, normal, half azimuth, half polar
     const double* spec;    // [B][cap][G]
     const int* n_cones;    // [B]
     const int* slot;       // [B] row of U, -1 for none
@@ -1695,10 +1716,10 @@ __global__ void __launch_bounds__(kRayThreads) k_raytrace_cones(const RayParams 
     double* out = p.unc + (size_t)b * p.G * p.V + v;
     double* U = cp.U + (size_t)cp.slot[b] * p.G * cp.K * p.V + v;
     for (int c = 0; c < nc; ++c) {
-        const double* s7 = cp.geo + ((size_t)b * cp.cap + c) * 8;
+        const double* s7 = cp.geo + ((size_t)b * cp.cap + c) * 16;   // pos, axis, half, then aperture row
         const double* spec = cp.spec + ((size_t)b * cp.cap + c) * p.G;
         double r2, om[3];
-        const bool in = ray_lengths(p, v, s7, &Ls[0][tid], r2, om);
+        const bool in = ray_lengths(p, v, s7, s7 + 7, &Ls[0][tid], r2, om);
         double Lm[kRayMats], Y[16];
 #pragma unroll
         for (int m = 0; m < kRayMats; ++m) Lm[m] = Ls[m][tid];

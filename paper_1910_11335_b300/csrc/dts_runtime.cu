@@ -81,6 +81,8 @@ struct dts_problem {
     double *src = nullptr, *spec = nullptr, *leak = nullptr, *blk = nullptr, *status = nullptr;
     // combined multi-cone sources (kind 2): per member its cones (host copies), device
     // tables [B][cone_cap][8] / [B][cone_cap][G], and a row of U per such member
+    std::vector<double> fan_h;        // [B][8] beam aperture of kind-1 members (0 cone, 1 fan + its angles)
+    double* fan = nullptr;
     std::vector<std::vector<double>> cone_geo_h, cone_spec_h;
     std::vector<int> cone_n_h, uslot_h;
     int cone_cap = 0, n_uslots = 0;
@@ -707,7 +709,7 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         rp.dx = p->d.dx; rp.dy = p->d.dy; rp.dz = p->d.dz;
         rp.x0 = p->d.x0; rp.y0 = p->d.y0; rp.z0 = p->d.z0;
         rp.mat = p->mat_nat; rp.scale_t = p->scale_t_nat; rp.sigma_t = p->sigma_t;
-        rp.src = p->src; rp.spec = p->spec; rp.unc = p->unc; rp.n_mat = p->n_mat;
+        rp.src = p->src; rp.spec = p->spec; rp.unc = p->unc; rp.n_mat = p->n_mat; rp.fan = p->fan;
         if (p->n_mat <= kRayMats) {
             k_raytrace_mat<<<dim3((p->V + kRayThreads - 1) / kRayThreads, B), kRayThreads, 0, p->stream>>>(rp);
         } else {
@@ -1060,6 +1062,9 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     CK(cudaMallocHost((void**)&p->h_active, sizeof(int) * B));
     p->src_h.assign(B * 8, 0.0);
     for (size_t b = 0; b < B; ++b) p->src_h[b * 8] = -1.0;
+    p->fan_h.assign(B * 8, 0.0);
+    TRY(dalloc_t(p, &p->fan, B * 8));
+    CK(cudaMemset(p->fan, 0, sizeof(double) * B * 8));
     p->cone_geo_h.assign(B, {});
     p->cone_spec_h.assign(B, {});
     p->cone_n_h.assign(B, 0);
@@ -1284,7 +1289,7 @@ dts_status run_adjoint(dts_problem* p, int b)
     rp2.dx = p->d.dx; rp2.dy = p->d.dy; rp2.dz = p->d.dz;
     rp2.x0 = p->d.x0; rp2.y0 = p->d.y0; rp2.z0 = p->d.z0;
     rp2.mat = p->mat_nat; rp2.scale_t = p->scale_t_nat; rp2.sigma_t = p->sigma_t;
-    rp2.src = p->src; rp2.spec = p->spec; rp2.unc = p->unc; rp2.n_mat = p->n_mat;
+    rp2.src = p->src; rp2.spec = p->spec; rp2.unc = p->unc; rp2.n_mat = p->n_mat; rp2.fan = p->fan;
     k_adj_ray<<<(unsigned)((V + 127) / 128), 128, 0, p->stream>>>(rp2, p->adj_a, p->adj_dphiu, b, p->adj_gt);
     CK(cudaGetLastError());
     return DTS_OK;
@@ -1295,6 +1300,30 @@ dts_status run_adjoint(dts_problem* p, int b)
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// the beam of a kind-1 source: the cone half-angle, or a fan (aperture 1) with
+// its plane normal and half angles; writes the 8-double aperture row
+dts_status beam_row(dts_problem* p, const dts_source* s, double* row)
+{
+    for (int i = 0; i < 8; ++i) row[i] = 0.0;
+    if (s->aperture == 0) return DTS_OK;
+    if (s->aperture != 1) return fail(p, DTS_ERR_INVALID_ARG, "aperture must be 0 (cone) or 1 (fan)");
+    const double an = std::sqrt(s->axis[0] * s->axis[0] + s->axis[1] * s->axis[1] + s->axis[2] * s->axis[2]);
+    const double nn = std::sqrt(s->normal[0] * s->normal[0] + s->normal[1] * s->normal[1] +
+                                s->normal[2] * s->normal[2]);
+    if (!(nn > 0.0) || !isfin(nn)) return fail(p, DTS_ERR_INVALID_ARG, "fan normal must be non-zero and finite");
+    const double c = (s->normal[0] * s->axis[0] + s->normal[1] * s->axis[1] + s->normal[2] * s->axis[2]) / (an * nn);
+    if (!(std::fabs(c) < 1.0 - 1e-9)) return fail(p, DTS_ERR_INVALID_ARG, "fan normal parallel to the axis");
+    if (!(s->half_azimuth > 0.0) || !(s->half_azimuth <= kPi + 1e-12))
+        return fail(p, DTS_ERR_INVALID_ARG, "half_azimuth must be in (0, pi]");
+    if (!(s->half_polar > 0.0) || !(s->half_polar <= 0.5 * kPi + 1e-12))
+        return fail(p, DTS_ERR_INVALID_ARG, "half_polar must be in (0, pi/2]");
+    row[0] = 1.0;
+    for (int i = 0; i < 3; ++i) row[1 + i] = s->normal[i];
+    row[4] = s->half_azimuth;
+    row[5] = s->half_polar;
+    return DTS_OK;
+}
+
 extern "C" {
 
 dts_status dts_create_problem(const dts_problem_desc* desc, dts_problem** out)
@@ -1436,6 +1465,12 @@ dts_status dts_set_source(dts_problem* p, int batch_index, const dts_source* s)
     } else {
         return fail(p, DTS_ERR_INVALID_ARG, "source kind must be 0 or 1");
     }
+    {
+        double* frow = &p->fan_h[(size_t)batch_index * 8];
+        if (s->kind == 1) TRY(beam_row(p, s, frow));
+        else for (int i = 0; i < 8; ++i) frow[i] = 0.0;
+        CK(cudaMemcpy(p->fan + (size_t)batch_index * 8, frow, sizeof(double) * 8, cudaMemcpyHostToDevice));
+    }
     CK(cudaMemcpy(p->src + (size_t)batch_index * 8, row, sizeof(double) * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->spec + (size_t)batch_index * G, &p->spec_h[(size_t)batch_index * G],
                   sizeof(double) * G, cudaMemcpyHostToDevice));
@@ -1451,7 +1486,7 @@ dts_status dts_set_source_cones(dts_problem* p, int batch_index, int n_cones, co
     if (batch_index < 0 || batch_index >= p->B) return fail(p, DTS_ERR_INVALID_ARG, "batch_index out of range");
     if (n_cones < 1 || n_cones > 4096) return fail(p, DTS_ERR_INVALID_ARG, "n_cones must be in 1..4096");
     const int G = p->G, B = p->B;
-    std::vector<double> geo((size_t)n_cones * 8, 0.0), spec((size_t)n_cones * G);
+    std::vector<double> geo((size_t)n_cones * 16, 0.0), spec((size_t)n_cones * G);
     for (int c = 0; c < n_cones; ++c) {
         const dts_source* s = cones + c;
         if (s->kind != 1) return fail(p, DTS_ERR_INVALID_ARG, "every cone must be a kind-1 source");
@@ -1462,10 +1497,11 @@ dts_status dts_set_source_cones(dts_problem* p, int batch_index, int n_cones, co
             return fail(p, DTS_ERR_INVALID_ARG, "half_angle must be in (0, pi]");
         for (int i = 0; i < 3; ++i) {
             if (!isfin(s->pos[i])) return fail(p, DTS_ERR_INVALID_ARG, "source position must be finite");
-            geo[(size_t)c * 8 + i] = s->pos[i];
-            geo[(size_t)c * 8 + 3 + i] = s->axis[i];
+            geo[(size_t)c * 16 + i] = s->pos[i];
+            geo[(size_t)c * 16 + 3 + i] = s->axis[i];
         }
-        geo[(size_t)c * 8 + 6] = s->half_angle >= kPi ? kPi : s->half_angle;
+        geo[(size_t)c * 16 + 6] = s->half_angle >= kPi ? kPi : s->half_angle;
+        TRY(beam_row(p, s, &geo[(size_t)c * 16 + 7]));   // aperture, normal, half azimuth, half polar
         for (int g = 0; g < G; ++g) {
             if (!isfin(s->spectrum[g]) || s->spectrum[g] < 0.0)
                 return fail(p, DTS_ERR_INVALID_ARG, "spectrum must be finite and >= 0");
@@ -1482,18 +1518,18 @@ dts_status dts_set_source_cones(dts_problem* p, int batch_index, int n_cones, co
         dfree(p, p->cone_spec);
         p->cone_geo = p->cone_spec = nullptr;
         p->cone_cap = n_cones;
-        TRY(dalloc_t(p, &p->cone_geo, (size_t)B * p->cone_cap * 8));
+        TRY(dalloc_t(p, &p->cone_geo, (size_t)B * p->cone_cap * 16));
         TRY(dalloc_t(p, &p->cone_spec, (size_t)B * p->cone_cap * G));
         for (int b = 0; b < B; ++b) {
-            const int n = (int)p->cone_geo_h[b].size() / 8;
+            const int n = (int)p->cone_geo_h[b].size() / 16;
             if (n == 0) continue;
-            CK(cudaMemcpy(p->cone_geo + (size_t)b * p->cone_cap * 8, p->cone_geo_h[b].data(),
-                          sizeof(double) * n * 8, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(p->cone_geo + (size_t)b * p->cone_cap * 16, p->cone_geo_h[b].data(),
+                          sizeof(double) * n * 16, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(p->cone_spec + (size_t)b * p->cone_cap * G, p->cone_spec_h[b].data(),
                           sizeof(double) * (size_t)n * G, cudaMemcpyHostToDevice));
         }
     } else {
-        CK(cudaMemcpy(p->cone_geo + (size_t)batch_index * p->cone_cap * 8, geo.data(), sizeof(double) * geo.size(),
+        CK(cudaMemcpy(p->cone_geo + (size_t)batch_index * p->cone_cap * 16, geo.data(), sizeof(double) * geo.size(),
                       cudaMemcpyHostToDevice));
         CK(cudaMemcpy(p->cone_spec + (size_t)batch_index * p->cone_cap * G, spec.data(),
                       sizeof(double) * spec.size(), cudaMemcpyHostToDevice));

@@ -39,7 +39,8 @@ class ProblemDesc(C.Structure):
 
 class SourceDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("q", _dp), ("pos", C.c_double * 3), ("axis", C.c_double * 3),
-                ("half_angle", C.c_double), ("spectrum", _dp)]
+                ("half_angle", C.c_double), ("spectrum", _dp), ("aperture", C.c_int),
+                ("normal", C.c_double * 3), ("half_azimuth", C.c_double), ("half_polar", C.c_double)]
 
 
 class SolveStats(C.Structure):
@@ -229,13 +230,15 @@ class Problem:
             arr = (SourceDesc * len(src.cones))()
             for i, (c, sp) in enumerate(zip(src.cones, specs)):
                 arr[i] = SourceDesc(c.kind, None, (C.c_double * 3)(*c.pos), (C.c_double * 3)(*c.axis),
-                                    c.half_angle, _dptr(sp))
+                                    c.half_angle, _dptr(sp), c.aperture, (C.c_double * 3)(*c.normal),
+                                    c.half_azimuth, c.half_polar)
             _check(lib().dts_set_source_cones(self._h, b, len(src.cones), arr), self._h)
             return
         q = None if src.q is None else np.ascontiguousarray(src.q, dtype=np.float64)
         sp = None if src.spectrum is None else np.ascontiguousarray(src.spectrum, dtype=np.float64)
         s = SourceDesc(src.kind, _dptr(q), (C.c_double * 3)(*src.pos),
-                       (C.c_double * 3)(*src.axis), src.half_angle, _dptr(sp))
+                       (C.c_double * 3)(*src.axis), src.half_angle, _dptr(sp), src.aperture,
+                       (C.c_double * 3)(*src.normal), src.half_azimuth, src.half_polar)
         _check(lib().dts_set_source(self._h, b, C.byref(s)), self._h)
 
     # solve

@@ -40,8 +40,11 @@ class Source:
     kind 0: isotropic volumetric source ``q[G][V]`` in photons/cm^3 (total over
     4 pi). kind 1: point source at ``pos`` collimated to a cone around ``axis``
     with half-angle ``half_angle`` (radians; >= pi means isotropic), emitting
-    ``spectrum[g]`` photons per source particle into group g. kind 2: the sum
-    of the kind-1 sources in ``cones`` (several cone beams at once).
+    ``spectrum[g]`` photons per source particle into group g; with
+    ``aperture`` 1 the beam is a fan instead: the azimuthal angle subtended in
+    the plane normal to ``normal`` is 2 ``half_azimuth`` and the polar angle out
+    of that plane 2 ``half_polar``. kind 2: the sum of the kind-1 sources in
+    ``cones`` (several cone or fan beams at once).
     """
     kind: int
     q: Optional[np.ndarray] = None
@@ -50,6 +53,10 @@ class Source:
     half_angle: float = math.pi
     spectrum: Optional[np.ndarray] = None
     cones: Optional[list] = None
+    aperture: int = 0
+    normal: tuple = (0.0, 0.0, 1.0)
+    half_azimuth: float = 0.0
+    half_polar: float = 0.0
 
 
 @dataclasses.dataclass
@@ -407,6 +414,27 @@ def dose_coefficients(w: Workload, seed_index: int = 7):
     p = rng.uniform(1.5, 2.5, size=n_mat)
     mu = a[:, None] * (e_kev[None, :] / 60.0) ** (-p[:, None]) + 0.02
     return mu, e_kev / 1000.0
+
+
+def fan_sources(spectrum, n_sources: int, distance=50.0, half_azimuth=math.radians(20.0),
+                half_polar=math.radians(4.0)):
+    """Fan-beam point sources on a circle in the central z-plane, aimed at the
+    centre, fan plane normal to z (the rotation axis of a CT gantry)."""
+    out = ring_sources(spectrum, n_sources, distance)
+    for s in out:
+        s.aperture, s.normal = 1, (0.0, 0.0, 1.0)
+        s.half_azimuth, s.half_polar = half_azimuth, half_polar
+    return out
+
+
+def combined_fans(w: Workload, n_fans: int = 16, **kw) -> Workload:
+    """The same problem with one source made of n_fans fan beams on a ring
+    (multi-fan CT arrangement), each with source 0's spectrum."""
+    import copy
+    t = copy.copy(w)
+    t.sources = [Source(kind=2, cones=fan_sources(w.sources[0].spectrum, n_fans, **kw))]
+    t.name = f"{w.name}_fans{n_fans}"
+    return t
 
 
 def combined_cones(w: Workload, n_cones: int = 16, distance=50.0, half_angle=math.radians(15.0)) -> Workload:
