@@ -193,7 +193,7 @@ def run_reference(args):
 MEASURED_TRAFFIC = {
     ("k_sweep_batch", "batch96_s8p3_19g_x32", (8, 4, 4)): {
         "dram_over_algorithmic": 1.33,
-        "source_sha256": "68360d3ed6fa8192e1e03f9fb45e39e56ba7e1c49055f93b6ed52622cf6d45e4",
+        "source_sha256": "f53287b3d101fe2b58b18602fd4d49ee50f1132d46e9cc1f42b2468f8087e835",
     },
 }
 

@@ -629,8 +629,8 @@ struct BatchShape {
     static constexpr int oT = 0;                        // [SB][TSTR] the line being swept, refilled after phase A
     static constexpr int oP = oT + SB * TSTR;           // [SB][PSTR]
     static constexpr int oX = oP + (PSI ? 0 : SB * PSTR);   // [fxn][32] x faces, slot = local line
-    static constexpr int oY = oX + fxn * 32;            // [fyn][32] y faces, slot = lz * BX + lx
-    static constexpr int oZ = oY + fyn * 32;            // [fzn][32] z faces, slot = ly * BX + lx
+    static constexpr int oY = oX + fxn * 32;            // [BX][32] y faces of one z-layer, slot = lx
+    static constexpr int oZ = oY + BX * 32;             // [fzn][32] z faces, slot = ly * BX + lx
     static constexpr int oS = oZ + fzn * 32;            // [NLINE][BX] sigma_t, local line, storage x
     static constexpr int nF = (oS + BV + 3) & ~3;
     static constexpr size_t bytes = sizeof(float) * nF + sizeof(double) * SB;
@@ -860,7 +860,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     float* gy = p.yf + ((og * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * fyn) * 32;
     float* gz = p.zf + ((og * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * fzn) * 32;
     batch_faces_in_async<fxn>(fx, gx, ta > 0);   // land with the first line's sources
-    batch_faces_in_async<fyn>(fy, gy, tb > 0);
+    batch_faces_in_async<BX>(fy, gy, tb > 0);    // z-layer 0; later layers stream in with the lines
     batch_faces_in_async<fzn>(fz, gz, tc > 0);
     cp_async_commit();
 
@@ -868,6 +868,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     constexpr unsigned FULL = (1u << BX) - 1u;
     const unsigned vxs = nvx >= BX ? FULL : (1u << nvx) - 1u;   // valid cells, storage x bits
     float yv[BX];
+    float ysum = 0.f;   // the lane's outgoing y-faces (leakage when the tile is on the y boundary)
 
 #pragma unroll 1
     for (int line = 0; line < S::NLINE; ++line) {
@@ -897,12 +898,15 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         // the staged sources are consumed: every lane is past phase A, so the
         // next line's sources can land in the same buffer during the walk
         __syncwarp();
+        // the layer's y-faces went to registers during line ly = 0; the next layer's land in the
+        // same buffer with the next line's sources
+        if (ly == 1 && lz + 1 < BZ) batch_faces_in_async<BX>(fy, gy + (size_t)(lz + 1) * BX * 32, tb > 0);
         if (line + 1 < S::NLINE) stage_line(line + 1, 0);
 
         // B: walk the line
         if (ly == 0) {
 #pragma unroll
-            for (int lx = 0; lx < BX; ++lx) yv[lx] = fy[(lz * BX + lx) * 32 + lane];
+            for (int lx = 0; lx < BX; ++lx) yv[lx] = fy[lx * 32 + lane];
         }
         {
             const unsigned vm = (sy < nvy && sz < nvz) ? vxs : 0u;
@@ -915,7 +919,10 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         }
         if (ly == BY - 1) {
 #pragma unroll
-            for (int lx = 0; lx < BX; ++lx) fy[(lz * BX + lx) * 32 + lane] = yv[lx];
+            for (int lx = 0; lx < BX; ++lx) {
+                gy[(lz * BX + lx) * 32 + lane] = yv[lx];   // outgoing y-faces straight to the face block
+                ysum += yv[lx];
+            }
         }
         if constexpr (PSI) {
             // the lane's angular fluxes of the line go straight to HBM: psi[b][oct][tile][d][cell]
@@ -965,7 +972,6 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 
     // outgoing faces; the lane's own faces leaving the grid are its leakage
     batch_faces_out<fxn>(fx, gx);
-    batch_faces_out<fyn>(fy, gy);
     batch_faces_out<fzn>(fz, gz);
     const bool lbx = NX ? tx == 0 : tx == p.NTx - 1;
     const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
@@ -976,7 +982,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
             if (lbx)
                 for (int e = 0; e < fxn; ++e) sx_ += fx[e * 32 + lane];
             if (lby)
-                for (int e = 0; e < fyn; ++e) sy_ += fy[e * 32 + lane];
+                sy_ = ysum;
             if (lbz)
                 for (int e = 0; e < fzn; ++e) sz_ += fz[e * 32 + lane];
             const double lk = p.Lw[(n0 + d) * 3] * (double)sx_ + p.Lw[(n0 + d) * 3 + 1] * (double)sy_ +
@@ -1116,12 +1122,16 @@ struct TwoSum {
 
 // The per-cell tail of the FP32 reductions: store the FP64 scalar flux, form
 // T_0 = F_0 + sigma_s0 phi_00 in FP32, and accumulate this thread's residual
-// and balance terms in FP32 (summed across threads in FP64).
+// and balance terms in FP32 (summed across a warp in FP32, across warps and
+// blocks in FP64).
 struct RedTail {
     float ds = 0.f, ns = 0.f, sr = 0.f, ab = 0.f;
-    __device__ __forceinline__ float cell(double s0, double old, float f0, float sl0, float st)
+    // s0 = (double)ts.s + (double)ts.e rounds to the same FP32 value as the pair's FP32 sum (the
+    // FP64 sum is exact unless e is below 2^-29 of s, and then both round to s); the old flux
+    // enters only the balance term, where its FP32 value may be off by an ulp
+    __device__ __forceinline__ float cell(const TwoSum& ts, double s0, double old, float f0, float sl0, float st)
     {
-        const float s0f = (float)s0, dd = (float)(s0 - old), oldf = (float)old;
+        const float s0f = __fadd_rn(ts.s, ts.e), dd = (float)(s0 - old), oldf = s0f - dd;
         ds = fmaf(dd, dd, ds);
         ns = fmaf(s0f, s0f, ns);
         ab = fmaf(st, s0f, ab);
@@ -1130,18 +1140,28 @@ struct RedTail {
     }
 };
 
-__device__ __forceinline__ void red_tail_store(const RedParams<float>& p, const RedTail& t, double* red, int b)
+// The block's four partial sums: FP32 butterflies within each warp (FP64 runs
+// at a small fraction of the FP32 rate on this part), one barrier, then the
+// warps' totals added in FP64 by four threads.
+__device__ __forceinline__ void red_tail_store(const RedParams<float>& p, const RedTail& t, double* red, int b,
+                                               int blk, int nblk)
 {
-    const double ds = block_sum((double)t.ds, red);
-    const double ns = block_sum((double)t.ns, red);
-    const double sr = block_sum((double)t.sr, red);
-    const double ab = block_sum((double)t.ab, red);
-    if (threadIdx.x == 0) {
-        double* o = p.blk + ((size_t)b * gridDim.x + blockIdx.x) * 4;
-        o[0] = ds;
-        o[1] = ns;
-        o[2] = p.vol * sr;
-        o[3] = p.vol * ab;
+    static_assert(kRedThreads / 32 * 4 <= 32, "red[] holds four partials per warp");
+    float v[4] = {t.ds, t.ns, t.sr, t.ab};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) red[wid * 4 + i] = (double)v[i];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) acc += red[w * 4 + threadIdx.x];
+        double* o = p.blk + ((size_t)b * nblk + blk) * 4;
+        o[threadIdx.x] = threadIdx.x < 2 ? acc : p.vol * acc;
     }
 }
 
@@ -1190,7 +1210,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce4(const RedParams<float> 
                 continue;
             }
             phi[j] = s0[j].value();
-            t0[j] = tl.cell(phi[j], old[j], ff[j], sl[j], sg[j]);
+            t0[j] = tl.cell(s0[j], phi[j], old[j], ff[j], sl[j], sg[j]);
         }
         *reinterpret_cast<double2*>(ph) = make_double2(phi[0], phi[1]);
         *reinterpret_cast<double2*>(ph + 2) = make_double2(phi[2], phi[3]);
@@ -1212,7 +1232,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce4(const RedParams<float> 
                 make_float4(fmaf(sk.x, acc.x, f.x), fmaf(sk.y, acc.y, f.y), fmaf(sk.z, acc.z, f.z), fmaf(sk.w, acc.w, f.w));
         }
     }
-    red_tail_store(p, tl, red, b);
+    red_tail_store(p, tl, red, b, blockIdx.x, gridDim.x);
 }
 
 // Eq. 3 and its higher moments from the angular fluxes written by the batched
@@ -1348,7 +1368,7 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_reduce_psi(const RedParams<f
                 continue;
             }
             phi[j] = s0[j].value();
-            t0[j] = tl.cell(phi[j], old[j], ff[j], sl[j], sg[j]);
+            t0[j] = tl.cell(s0[j], phi[j], old[j], ff[j], sl[j], sg[j]);
         }
         *reinterpret_cast<double2*>(ph) = make_double2(phi[0], phi[1]);
         *reinterpret_cast<float2*>(T) = make_float2(t0[0], t0[1]);
@@ -1360,7 +1380,7 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_reduce_psi(const RedParams<f
             *reinterpret_cast<float2*>(T + (size_t)k * p.TV) = make_float2(fmaf(sk.x, a0, f.x), fmaf(sk.y, a1, f.y));
         }
     }
-    red_tail_store(p, tl, red, b);
+    red_tail_store(p, tl, red, b, blockIdx.x, gridDim.x);
 }
 
 // per source: residual = sqrt(sum dphi^2 / sum phi^2), balance terms, leakage
