@@ -20,6 +20,7 @@ namespace dts {
 
 constexpr int kSweepThreads = 256;
 constexpr int kRedThreads = 256;
+constexpr int kPushRing = 4;   // widest downscatter band of the FP32 push kernels (W <= 4)
 constexpr int kRayGroups = 16;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -2053,38 +2054,49 @@ __global__ void __launch_bounds__(256) k_push_psi(const PushParams<float> p, int
     double ss[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) ss[j] = c.scale_s_t ? c.scale_s_t[c2 + j] : 1.0;
+    // sigma_s(g -> g+1+w) scale_s rounded to FP32 once per (cell, l, lower group): formed for each
+    // Legendre order before its 2l+1 moments (FP64 runs at a small fraction of the FP32 rate)
+    constexpr int NL = K == 1 ? 1 : K == 4 ? 2 : K == 9 ? 3 : 4;
+    static_assert(NL * NL == K, "K = (L+1)^2");
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double ph[2];
-        float2 s2;
-        if (k == 0) {
-            ph[0] = s0t[0].value();
-            ph[1] = s0t[1].value();
-            s2 = make_float2((float)ph[0], (float)ph[1]);
-        } else {
-            s2 = make_float2(psi_moment<K>(k, 0, m1, acc), psi_moment<K>(k, 1, m1, acc));
-            ph[0] = s2.x;
-            ph[1] = s2.y;
-        }
+    for (int l = 0; l < NL; ++l) {
+        float sc[kPushRing][2];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            if (mm[j] < 0 || x0 + j >= c.nx) continue;
-            if (k == 0) p.col[((size_t)b * c.G + g) * p.V + v0 + j] = ph[j];
-            if (p.mom) p.mom[(((size_t)b * c.G + g) * K + k) * p.V + v0 + j] = ph[j];
-        }
-        const int l = l_of_k(k);
-        for (int w = 0; w < nw; ++w) {
-            float sc[2];
+        for (int w = 0; w < kPushRing; ++w)
 #pragma unroll
             for (int j = 0; j < 2; ++j)
-                sc[j] = mm[j] < 0 ? 0.f
-                                  : (float)(c.sigma_s[(((size_t)mm[j] * L1 + l) * c.G + g) * c.G + g + 1 + w] * ss[j]);
-            float2* f = reinterpret_cast<float2*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base +
-                                                  (size_t)k * c.TV);
-            float2 fv = *f;
-            fv.x = fmaf(sc[0], s2.x, fv.x);
-            fv.y = fmaf(sc[1], s2.y, fv.y);
-            *f = fv;
+                sc[w][j] = (w >= nw || mm[j] < 0)
+                               ? 0.f
+                               : (float)(c.sigma_s[(((size_t)mm[j] * L1 + l) * c.G + g) * c.G + g + 1 + w] * ss[j]);
+#pragma unroll
+        for (int k = l * l; k < (l + 1) * (l + 1); ++k) {
+            double ph[2];
+            float2 s2;
+            if (k == 0) {
+                ph[0] = s0t[0].value();
+                ph[1] = s0t[1].value();
+                s2 = make_float2((float)ph[0], (float)ph[1]);
+            } else {
+                s2 = make_float2(psi_moment<K>(k, 0, m1, acc), psi_moment<K>(k, 1, m1, acc));
+                ph[0] = s2.x;
+                ph[1] = s2.y;
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (mm[j] < 0 || x0 + j >= c.nx) continue;
+                if (k == 0) p.col[((size_t)b * c.G + g) * p.V + v0 + j] = ph[j];
+                if (p.mom) p.mom[(((size_t)b * c.G + g) * K + k) * p.V + v0 + j] = ph[j];
+            }
+#pragma unroll
+            for (int w = 0; w < kPushRing; ++w) {
+                if (w >= nw) break;
+                float2* f = reinterpret_cast<float2*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base +
+                                                      (size_t)k * c.TV);
+                float2 fv = *f;
+                fv.x = fmaf(sc[w][0], s2.x, fv.x);
+                fv.y = fmaf(sc[w][1], s2.y, fv.y);
+                *f = fv;
+            }
         }
     }
 }
