@@ -1245,7 +1245,17 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce4(const RedParams<float> 
 // moments stay in FP32.
 template <int K> struct PsiPairs { static constexpr int value = ((K + 1) / 2 + 1) & ~1; };   // even
 
-template <int NDO, int K>
+// the first octant's copies of psi_moments (buffer 0), for callers that start them early
+template <int NDO>
+__device__ __forceinline__ void psi_issue_first(const float* __restrict__ ps, int TV, unsigned long long* stg)
+{
+    const int nt = blockDim.x;
+#pragma unroll
+    for (int d = 0; d < NDO; ++d) cp_async8(stg + d * nt, ps + (size_t)d * TV);
+    cp_async_commit();
+}
+
+template <int NDO, int K, bool ISSUED = false>
 __device__ __forceinline__ void psi_moments(const float* __restrict__ ps, size_t ostride, int TV,
                                             const unsigned long long* Dp, unsigned long long* stg,
                                             TwoSum (&s0)[2], float (&m1)[2],
@@ -1265,7 +1275,7 @@ __device__ __forceinline__ void psi_moments(const float* __restrict__ ps, size_t
         for (int d = 0; d < NDO; ++d) cp_async8(dst + d * nt, ps + o * ostride + (size_t)d * TV);
         cp_async_commit();
     };
-    issue(0);
+    if (!ISSUED) issue(0);
 #pragma unroll 1
     for (int o = 0; o < 8; ++o) {
         if (o + 1 < 8) issue(o + 1);
@@ -1335,19 +1345,23 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_reduce_psi(const RedParams<f
     __shared__ __align__(16) unsigned long long Dp[8 * NDO * PsiPairs<K>::value];
     __shared__ unsigned long long stg[2 * NDO * kRedThreads];
     __shared__ double red[32];
-    load_dpairs<NDO, K>(Dp, Dt);
     const int b = blockIdx.y;
     const int c2 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const bool live = p.active[b] != 0 && c2 < p.NC;
+    const int tile = c2 / p.TV, c = c2 - tile * p.TV;
+    const size_t ostride = (size_t)p.NT * NDO * p.TV;
+    const size_t pofs = (size_t)b * 8 * ostride + (size_t)tile * NDO * p.TV + c;
+    // the first octant's fluxes are in flight while the block loads its moment operator
+    if (live) psi_issue_first<NDO>(p.part + pofs, p.TV, stg + threadIdx.x);
+    load_dpairs<NDO, K>(Dp, Dt);
     RedTail tl;
-    if (p.active[b] != 0 && c2 < p.NC) {
-        const int tile = c2 / p.TV, c = c2 - tile * p.TV;
+    if (live) {
         const size_t base = ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
-        const size_t ostride = (size_t)p.NT * NDO * p.TV;
-        const float* ps = p.part + (size_t)b * 8 * ostride + (size_t)tile * NDO * p.TV + c;
+        const float* ps = p.part + pofs;
         TwoSum s0[2];
         float m1[2];
         unsigned long long acc[2][PsiPairs<K>::value];
-        psi_moments<NDO, K>(ps, ostride, p.TV, Dp, stg + threadIdx.x, s0, m1, acc);
+        psi_moments<NDO, K, true>(ps, ostride, p.TV, Dp, stg + threadIdx.x, s0, m1, acc);
         float* __restrict__ T = p.T + base;
         const float* __restrict__ F = p.F + (size_t)p.ctl[1] * p.Fstride + base;
         double* __restrict__ ph = p.phi00 + (size_t)b * p.NC + c2;
