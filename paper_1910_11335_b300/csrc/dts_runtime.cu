@@ -652,12 +652,14 @@ void launch_group_xs(dts_problem* p, int g)
                                              p->sigs0);
 }
 
+// T = F of the group's ring slot (phi = 0 before the first sweep): one device-to-device copy
 template <typename R>
-void launch_group_init(dts_problem* p, int slot)
+dts_status launch_group_init(dts_problem* p, int slot)
 {
     const size_t total = (size_t)p->B * p->NC * p->K;
-    k_group_init<R><<<(unsigned)((total + 255) / 256), 256, 0, p->stream>>>(
-        total, (const R*)p->F + (size_t)slot * p->Fstride, (R*)p->T);
+    CK(cudaMemcpyAsync(p->T, (const R*)p->F + (size_t)slot * p->Fstride, total * sizeof(R), cudaMemcpyDeviceToDevice,
+                       p->stream));
+    return DTS_OK;
 }
 
 template <typename R>
@@ -742,10 +744,10 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         k_set_ctl<<<1, 1, 0, p->stream>>>(p->ctl, g, slot);
         if (p->fp64) {
             launch_group_xs<double>(p, g);
-            launch_group_init<double>(p, slot);
+            TRY(launch_group_init<double>(p, slot));
         } else {
             launch_group_xs<float>(p, g);
-            launch_group_init<float>(p, slot);
+            TRY(launch_group_init<float>(p, slot));
         }
         CK(cudaMemsetAsync(p->phi00, 0, sizeof(double) * B * p->NC, p->stream));
         for (int b = 0; b < B; ++b) {
@@ -811,7 +813,7 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         }
         if (p->fp64) launch_push<double>(p, g);
         else launch_push<float>(p, g);
-        launches += 4;   // set_ctl, group_xs, group_init, push
+        launches += 3;   // set_ctl, group_xs, push (the group's T = F is a copy, not a kernel)
         if (g + W1 < G) {
             if (p->fp64) launch_fixed_source<double>(p, g + W1, slot);
             else launch_fixed_source<float>(p, g + W1, slot);
