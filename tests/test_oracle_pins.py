@@ -386,6 +386,33 @@ def test_first_collision_source_matches_dense_direct_solve(ora):
         assert np.max(np.abs(r.collided[g] - phi[g])) <= 1e-11 * np.max(np.abs(phi[g]))
 
 
+@pytest.mark.parametrize("L", [0, 1, 2])
+def test_first_collision_source_direct_legendre_form(ora, L):
+    # Eq. 5 as the oracle forms it (moments Y_lm(Omega_u) phi_u, then the moment-to-direction operator)
+    # against the direct form: scattering of the uncollided beam into Omega_n is
+    # sum_l (2l+1)/(4 pi) sigma_sl phi_u P_l(Omega_n . Omega_u) (numpy Legendre polynomials, no
+    # spherical harmonics). One source iteration, so the collided flux is the weighted sum of one sweep
+    # per direction of that source; fixup off on both sides, so both are linear in the source.
+    w = inputs.small_cone(6, 5, 4, n_groups=1, sn_order=4, legendre_order=L)
+    src = w.sources[0]
+    mu, eta, xi, wt = ora.quadrature(4)
+    V, mat = w.n_voxels, w.mat_id.ravel()
+    phu, omu = np.zeros(V), np.zeros((V, 3))
+    for v in range(V):
+        pg, om = ora.uncollided_voxel(w, src, v)
+        phu[v], omu[v] = pg[0], om
+    assert (phu > 0).sum() > V // 10
+    sigt = w.sigma_t[mat, 0]
+    phi = np.zeros(V)
+    for n in range(len(wt)):
+        cosang = omu @ np.array([mu[n], eta[n], xi[n]])
+        Q = sum((2 * l + 1) / (4 * math.pi) * w.sigma_s[mat, l, 0, 0] * phu * _pl(l, cosang) for l in range(L + 1))
+        psi, _, _ = ora.sweep_dir(w, sigt, (mu[n], eta[n], xi[n]), Q, fixup=False)
+        phi += wt[n] * psi
+    r = ora.solve(w, 0, tol=0.0, max_iters=1, n_threads=4, fixup=False)
+    assert np.max(np.abs(r.collided[0] - phi)) <= 1e-12 * np.max(np.abs(phi))
+
+
 def test_particle_balance(ora):
     # per sweep: sum V T_00 = sum V sigma_t phi_00 + leakage (exact);
     # converged: sum_g sum V q = sum_g sum V sigma_a phi + sum_g leakage
