@@ -1649,52 +1649,64 @@ __device__ inline bool ray_lengths(const RayParams& p, int v, const double* s7, 
     enter(p.x0, p.nx, p.dx, Px, dx);
     enter(p.y0, p.ny, p.dy, Py, dy);
     enter(p.z0, p.nz, p.dz, Pz, dz);
-    // per axis: voxel index, step, reciprocal direction and next crossing parameter
-    auto init = [&](double lo, int n, double h, double P, double d, int c, int& id, int& st, double& inv,
-                    double& tn) {
+    // per axis: voxel index, step, and the next crossing parameter t = c0 + k c1 of plane k, with
+    // c0 = (lo - P) / d and c1 = h / d (the plane index k is exact in FP64)
+    auto init = [&](double lo, int n, double h, double P, double d, int c, int& id, int& st, double& c0,
+                    double& c1, double& tn) {
         if (d == 0.0) {
             id = c;
             st = 0;
-            inv = 0.0;
+            c0 = 2.0;
+            c1 = 0.0;
             tn = 2.0;
             return;
         }
         int i0 = (int)floor((P + a_in * d - lo) / h);
         id = i0 < 0 ? 0 : (i0 >= n ? n - 1 : i0);
         st = d > 0.0 ? 1 : -1;
-        inv = 1.0 / d;
-        tn = (lo + (id + (d > 0.0 ? 1 : 0)) * h - P) * inv;
+        const double inv = 1.0 / d;
+        c0 = (lo - P) * inv;
+        c1 = h * inv;
+        tn = fma((double)(id + (d > 0.0 ? 1 : 0)), c1, c0);
     };
     int ix, iy, iz, sx, sy, sz;
-    double ivx, ivy, ivz, tx, ty, tz;
-    init(p.x0, p.nx, p.dx, Px, dx, cx, ix, sx, ivx, tx);
-    init(p.y0, p.ny, p.dy, Py, dy, cy, iy, sy, ivy, ty);
-    init(p.z0, p.nz, p.dz, Pz, dz, cz, iz, sz, ivz, tz);
+    double cx0, cx1, cy0, cy1, cz0, cz1, tx, ty, tz;
+    init(p.x0, p.nx, p.dx, Px, dx, cx, ix, sx, cx0, cx1, tx);
+    init(p.y0, p.ny, p.dy, Py, dy, cy, iy, sy, cy0, cy1, ty);
+    init(p.z0, p.nz, p.dz, Pz, dz, cz, iz, sz, cz0, cz1, tz);
+    // The crossing parameters lie in [0, 2] (2 marks an axis the ray does not cross), so their order is
+    // that of their bit patterns as signed 64-bit integers: the selection below runs on the integer
+    // pipes instead of the FP64 pipe (a small fraction of the FP32 rate on this part). A crossing that
+    // rounds to -0 or just below 0 sorts first, as its value does; its segment is empty either way.
+    const long long one = __double_as_longlong(1.0);
     double acur = a_in;
     const int max_steps = p.nx + p.ny + p.nz + 3;
     for (int it = 0; it < max_steps; ++it) {
-        const int ax = (ty < tx) ? ((tz < ty) ? 2 : 1) : ((tz < tx) ? 2 : 0);
-        const double a1 = fmin(ax == 0 ? tx : ax == 1 ? ty : tz, 1.0);
-        const double seg = (a1 - acur) * r;
-        if (seg > 0.0) {
+        const long long bx = __double_as_longlong(tx), by = __double_as_longlong(ty), bz = __double_as_longlong(tz);
+        const int ax = (by < bx) ? ((bz < by) ? 2 : 1) : ((bz < bx) ? 2 : 0);
+        const long long bs = ax == 0 ? bx : ax == 1 ? by : bz;
+        const bool last = bs >= one;
+        const double a1 = last ? 1.0 : __longlong_as_double(bs);
+        if (__double_as_longlong(a1) > __double_as_longlong(acur)) {
+            const double seg = (a1 - acur) * r;
             const int vv = (iz * p.ny + iy) * p.nx + ix;
             const int m = p.mat[vv];
             Ls[m * kRayThreads] += p.scale_t ? p.scale_t[vv] * seg : seg;
         }
-        if (a1 >= 1.0) break;
+        if (last) break;
         acur = a1;
         if (ax == 0) {
             ix += sx;
             if (ix < 0 || ix >= p.nx) break;
-            tx = (p.x0 + (ix + (sx > 0 ? 1 : 0)) * p.dx - Px) * ivx;
+            tx = fma((double)(ix + (sx > 0 ? 1 : 0)), cx1, cx0);
         } else if (ax == 1) {
             iy += sy;
             if (iy < 0 || iy >= p.ny) break;
-            ty = (p.y0 + (iy + (sy > 0 ? 1 : 0)) * p.dy - Py) * ivy;
+            ty = fma((double)(iy + (sy > 0 ? 1 : 0)), cy1, cy0);
         } else {
             iz += sz;
             if (iz < 0 || iz >= p.nz) break;
-            tz = (p.z0 + (iz + (sz > 0 ? 1 : 0)) * p.dz - Pz) * ivz;
+            tz = fma((double)(iz + (sz > 0 ? 1 : 0)), cz1, cz0);
         }
     }
     return true;
