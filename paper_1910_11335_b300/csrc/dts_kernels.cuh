@@ -1912,7 +1912,19 @@ struct PushParams {
     int W, V;
     double* col;           // [B][G][V]
     double* mom;           // [B][G][K][V] or null
+    const float* sigma_s_f;   // [n_mat][L+1][G][G], the FP32 rounding of sigma_s
 };
+
+// sigma_s(mat, l, g -> gt) scale_s rounded to FP32 once: without a per-cell scatter scale it is the
+// FP32 table entry (the same rounding of the same FP64 value, with no FP64 arithmetic)
+template <typename R>
+__device__ __forceinline__ float push_factor(const PushParams<R>& p, int m, int l, int g, int gt, const double* ss_t,
+                                             int cell)
+{
+    const CellParams& c = p.c;
+    const size_t i = (((size_t)m * (c.L + 1) + l) * c.G + g) * c.G + gt;
+    return ss_t ? (float)(c.sigma_s[i] * ss_t[cell]) : p.sigma_s_f[i];
+}
 
 // the converged moments are the octant sums of the last sweep's partials
 // (scalar flux in FP64, higher moments in the sweep precision, as the
@@ -1979,12 +1991,8 @@ __global__ void __launch_bounds__(256) k_push4(const PushParams<float> p, int g)
     const int x0 = v0 % c.nx;
     const int W1 = p.W + 1;
     const int gmax = min(c.G - 1, g + p.W);
-    const int L1 = c.L + 1;
     constexpr int LK = K == 1 ? 1 : K == 4 ? 2 : K == 9 ? 3 : 4;  // Legendre orders present
     const int nw = gmax - g;
-    double ss[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) ss[j] = c.scale_s_t ? c.scale_s_t[c4 + j] : 1.0;
     float sc[4][LK][4];                                         // [g2 - g - 1][l][cell], W <= 4
 #pragma unroll
     for (int w = 0; w < 4; ++w)
@@ -1992,9 +2000,7 @@ __global__ void __launch_bounds__(256) k_push4(const PushParams<float> p, int g)
         for (int l = 0; l < LK; ++l)
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                sc[w][l][j] = (w >= nw || mm[j] < 0)
-                                  ? 0.f
-                                  : (float)(c.sigma_s[(((size_t)mm[j] * L1 + l) * c.G + g) * c.G + g + 1 + w] * ss[j]);
+                sc[w][l][j] = (w >= nw || mm[j] < 0) ? 0.f : push_factor(p, mm[j], l, g, g + 1 + w, c.scale_s_t, c4 + j);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float* pp = p.part + base + (size_t)k * c.TV;
@@ -2076,10 +2082,6 @@ __global__ void __launch_bounds__(256) k_push_psi(const PushParams<float> p, int
     const int x0 = v0 % c.nx;
     const int W1 = p.W + 1;
     const int nw = min(c.G - 1, g + p.W) - g;
-    const int L1 = c.L + 1;
-    double ss[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) ss[j] = c.scale_s_t ? c.scale_s_t[c2 + j] : 1.0;
     // sigma_s(g -> g+1+w) scale_s rounded to FP32 once per (cell, l, lower group): formed for each
     // Legendre order before its 2l+1 moments (FP64 runs at a small fraction of the FP32 rate)
     constexpr int NL = K == 1 ? 1 : K == 4 ? 2 : K == 9 ? 3 : 4;
@@ -2091,9 +2093,7 @@ __global__ void __launch_bounds__(256) k_push_psi(const PushParams<float> p, int
         for (int w = 0; w < kPushRing; ++w)
 #pragma unroll
             for (int j = 0; j < 2; ++j)
-                sc[w][j] = (w >= nw || mm[j] < 0)
-                               ? 0.f
-                               : (float)(c.sigma_s[(((size_t)mm[j] * L1 + l) * c.G + g) * c.G + g + 1 + w] * ss[j]);
+                sc[w][j] = (w >= nw || mm[j] < 0) ? 0.f : push_factor(p, mm[j], l, g, g + 1 + w, c.scale_s_t, c2 + j);
 #pragma unroll
         for (int k = l * l; k < (l + 1) * (l + 1); ++k) {
             double ph[2];

@@ -679,6 +679,7 @@ void launch_push(dts_problem* p, int g)
     pp.c = cell_params(p);
     pp.part = (const R*)p->part; pp.F = (R*)p->F; pp.Fstride = p->Fstride; pp.W = p->W; pp.V = p->V;
     pp.col = p->col; pp.mom = p->d.keep_moments ? p->mom : nullptr;
+    pp.sigma_s_f = p->sigma_s_f;
     if constexpr (sizeof(R) == 4) {
         if (p->psi_mode && p->W <= 4) {
             RedPsiFn rf;

@@ -283,3 +283,22 @@ def test_full_size_batch96_fp32(ora):
         for v in rng.integers(0, w.n_voxels, size=32):
             pu, _ = ora.uncollided_voxel(w, w.sources[b], int(v))
             assert np.allclose(unc[:, v], pu, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("tile", [(8, 4, 4), (4, 4, 4)])
+def test_batched_fp32_with_density_scales(ora, tile):
+    # per-voxel density scales on sigma_t and sigma_s (CT-derived densities): the FP32 forms round
+    # sigma_s * scale_s once per (cell, l, group) in the downscatter push and the first-collision source
+    import copy
+    w = copy.copy(inputs.small_cone(10, 9, 8, n_groups=3, sn_order=8, legendre_order=3, n_sources=3))
+    rng = np.random.default_rng(11)
+    w.scale_t = rng.uniform(0.6, 1.4, size=w.mat_id.shape)
+    w.scale_s = w.scale_t * rng.uniform(0.9, 1.1, size=w.mat_id.shape)
+    p = dts.problem_from_workload(w, precision=dts.PREC_FP32, tol=0.0, max_iters=4, tile=tile)
+    p.solve(allow_not_converged=True)
+    for b in range(3):
+        r = ora.solve(w, b, tol=0.0, max_iters=4, n_threads=8)
+        assert rel_max(p.fluence(b, dts.UNCOLLIDED), r.phi_u) <= 1e-12
+        col = p.fluence(b, dts.COLLIDED)
+        for g in range(w.n_groups):
+            assert rel_l2(col[g], r.collided[g]) <= TOL_FP32_L2, (b, g)
