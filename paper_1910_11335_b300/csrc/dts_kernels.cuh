@@ -2039,17 +2039,22 @@ __global__ void __launch_bounds__(256) k_push4(const PushParams<float> p, int g)
             if (p.mom) p.mom[(((size_t)b * c.G + g) * K + k) * p.V + v0 + j] = ph[j];
         }
         const int l = l_of_k(k);
+        // the lower groups' ring slots are loaded together, then updated (one memory latency per moment)
+        float4* fp[4];
+        float4 fv[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            fp[w] = reinterpret_cast<float4*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base + (size_t)k * c.TV);
+            if (w < nw) fv[w] = *fp[w];
+        }
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             if (w >= nw) break;
-            float4* f = reinterpret_cast<float4*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base +
-                                                  (size_t)k * c.TV);
-            float4 fv = *f;
-            fv.x = fmaf(sc[w][l][0], s4.x, fv.x);
-            fv.y = fmaf(sc[w][l][1], s4.y, fv.y);
-            fv.z = fmaf(sc[w][l][2], s4.z, fv.z);
-            fv.w = fmaf(sc[w][l][3], s4.w, fv.w);
-            *f = fv;
+            fv[w].x = fmaf(sc[w][l][0], s4.x, fv[w].x);
+            fv[w].y = fmaf(sc[w][l][1], s4.y, fv[w].y);
+            fv[w].z = fmaf(sc[w][l][2], s4.z, fv[w].z);
+            fv[w].w = fmaf(sc[w][l][3], s4.w, fv[w].w);
+            *fp[w] = fv[w];
         }
     }
 }
@@ -2113,15 +2118,22 @@ __global__ void __launch_bounds__(256) k_push_psi(const PushParams<float> p, int
                 if (k == 0) p.col[((size_t)b * c.G + g) * p.V + v0 + j] = ph[j];
                 if (p.mom) p.mom[(((size_t)b * c.G + g) * K + k) * p.V + v0 + j] = ph[j];
             }
+            // the ring slots of the lower groups are loaded together, then updated: one memory latency per
+            // moment instead of one per (moment, group) (the compiler may not move a load above a store)
+            float2* fp[kPushRing];
+            float2 fv[kPushRing];
+#pragma unroll
+            for (int w = 0; w < kPushRing; ++w) {
+                fp[w] = reinterpret_cast<float2*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base +
+                                                  (size_t)k * c.TV);
+                if (w < nw) fv[w] = *fp[w];
+            }
 #pragma unroll
             for (int w = 0; w < kPushRing; ++w) {
                 if (w >= nw) break;
-                float2* f = reinterpret_cast<float2*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base +
-                                                      (size_t)k * c.TV);
-                float2 fv = *f;
-                fv.x = fmaf(sc[w][0], s2.x, fv.x);
-                fv.y = fmaf(sc[w][1], s2.y, fv.y);
-                *f = fv;
+                fv[w].x = fmaf(sc[w][0], s2.x, fv[w].x);
+                fv[w].y = fmaf(sc[w][1], s2.y, fv[w].y);
+                *fp[w] = fv[w];
             }
         }
     }
