@@ -1340,7 +1340,7 @@ __device__ __forceinline__ void load_dpairs(unsigned long long* Dp, const float*
 // A5 + A6 for the direct-output form: moments from psi, then T = F + sigma_s phi,
 // the FP64 scalar flux, and the residual and balance partials as k_reduce4.
 template <int NDO, int K>
-__global__ void __launch_bounds__(kRedThreads, 3) k_reduce_psi(const RedParams<float> p, const float* __restrict__ Dt)
+__global__ void __launch_bounds__(kRedThreads, 4) k_reduce_psi(const RedParams<float> p, const float* __restrict__ Dt)
 {
     __shared__ __align__(16) unsigned long long Dp[8 * NDO * PsiPairs<K>::value];
     __shared__ unsigned long long stg[2 * NDO * kRedThreads];
@@ -2063,7 +2063,7 @@ __global__ void __launch_bounds__(256) k_push4(const PushParams<float> p, int g)
 // moments are recomputed from the last sweep's angular fluxes (as k_reduce_psi
 // forms them, two cells per thread), then pushed as in k_push4.
 template <int NDO, int K>
-__global__ void __launch_bounds__(256) k_push_psi(const PushParams<float> p, int g, const float* __restrict__ Dt)
+__global__ void __launch_bounds__(256, 4) k_push_psi(const PushParams<float> p, int g, const float* __restrict__ Dt)
 {
     __shared__ __align__(16) unsigned long long Dp[8 * NDO * PsiPairs<K>::value];
     __shared__ unsigned long long stg[2 * NDO * 256];
