@@ -1674,8 +1674,8 @@ __device__ inline bool ray_lengths(const RayParams& p, int v, const double* s7, 
     init(p.x0, p.nx, p.dx, Px, dx, cx, ix, sx, cx0, cx1, tx);
     init(p.y0, p.ny, p.dy, Py, dy, cy, iy, sy, cy0, cy1, ty);
     init(p.z0, p.nz, p.dz, Pz, dz, cz, iz, sz, cz0, cz1, tz);
-    // The crossing parameters lie in [0, 2] (2 marks an axis the ray does not cross), so their order is
-    // that of their bit patterns as signed 64-bit integers: the selection below runs on the integer
+    // The crossing parameters are non-negative (2 marks an axis the ray does not cross), so their order
+    // is that of their bit patterns as signed 64-bit integers: the selection below runs on the integer
     // pipes instead of the FP64 pipe (a small fraction of the FP32 rate on this part). A crossing that
     // rounds to -0 or just below 0 sorts first, as its value does; its segment is empty either way.
     const long long one = __double_as_longlong(1.0);
