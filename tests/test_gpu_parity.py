@@ -285,6 +285,27 @@ def test_full_size_batch96_fp32(ora):
             assert np.allclose(unc[:, v], pu, rtol=1e-12, atol=0)
 
 
+def test_full_size_precision128_fp32_vs_fp64(ora):
+    # the 128^3 reduced-precision configuration at full size, each form converged to its own tolerance:
+    # FP32 against the FP64 form on the GPU (which the tests above hold to the oracle), and the
+    # uncollided fluence of both against the oracle on sampled voxels
+    w = inputs.precision_128()
+    p32, st32 = _gpu(w, precision=dts.PREC_FP32, tile=(8, 4, 4))
+    assert st32.converged == 1
+    p64, st64 = _gpu(w, precision=dts.PREC_FP64, tol=1e-8, tile=(8, 8, 8))
+    assert st64.converged == 1
+    a, b = p32.fluence(0, dts.TOTAL), p64.fluence(0, dts.TOTAL)
+    assert rel_l2(a, b) <= TOL_FP32_L2
+    for g in range(w.n_groups):
+        assert rel_l2(a[g], b[g]) <= TOL_FP32_L2, g
+    u32, u64 = p32.fluence(0, dts.UNCOLLIDED), p64.fluence(0, dts.UNCOLLIDED)
+    rng = np.random.default_rng(128)
+    for v in rng.integers(0, w.n_voxels, size=24):
+        pu, _ = ora.uncollided_voxel(w, w.sources[0], int(v))
+        assert np.allclose(u64[:, v], pu, rtol=1e-12, atol=0)
+        assert np.allclose(u32[:, v], pu, rtol=1e-12, atol=0)
+
+
 @pytest.mark.parametrize("tile", [(8, 4, 4), (4, 4, 4)])
 def test_batched_fp32_with_density_scales(ora, tile):
     # per-voxel density scales on sigma_t and sigma_s (CT-derived densities): the FP32 forms round
