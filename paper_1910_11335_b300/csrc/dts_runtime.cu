@@ -7,6 +7,7 @@
 // stages of the sweep, the Eq. 3 reduction and the residual), replayed for
 // every iteration of every group.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <array>
@@ -698,8 +699,17 @@ void launch_push(dts_problem* p, int g)
     k_push<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g);
 }
 
+// NVTX range for profilers (a no-op unless a tool is attached): the solve, each group, each iteration
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 dts_status run_solve(dts_problem* p, dts_solve_stats* st)
 {
+    NvtxRange solve_range("dts_solve");
     const int B = p->B, G = p->G;
     const int W1 = p->W + 1;
     TRY(ensure_ring(p));
@@ -741,6 +751,9 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
     const int64_t u_per_sweep = (int64_t)p->V * p->nd;
     std::vector<double> best(B), last_improve(B);
     for (int g = 0; g < G; ++g) {
+        char gname[32];
+        snprintf(gname, sizeof gname, "group %d", g);
+        NvtxRange group_range(gname);
         const int slot = g % W1;
         k_set_ctl<<<1, 1, 0, p->stream>>>(p->ctl, g, slot);
         if (p->fp64) {
@@ -761,6 +774,7 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         CK(cudaGetLastError());
         int n_active = B;
         for (int it = 1; it <= p->d.max_iters && n_active > 0; ++it) {
+            NvtxRange iter_range("source iteration");
             CK(cudaEventRecord(p->eva, p->stream));
             CK(cudaGraphLaunch(p->graph, p->stream));
             CK(cudaEventRecord(p->evb, p->stream));
