@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "splitbf16", "tf32"],
+                    help="arithmetic of the FP32-batched form's scatter-source contraction")
     return ap.parse_args()
 
 
@@ -243,7 +245,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     w = make_workload(args, rank)
     fp32 = args.workload != "hetero64"
-    prec = dts.PREC_FP32 if fp32 else dts.PREC_FP64
+    prec = {"auto": dts.PREC_FP32, "fp32": dts.PREC_FP32, "splitbf16": dts.PREC_FP32_SPLITBF16,
+            "tf32": dts.PREC_FP32_TF32}[args.precision] if fp32 else dts.PREC_FP64
     tol = args.tol if args.tol is not None else w.tol
     tuned = None
     if args.tile == "auto":

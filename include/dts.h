@@ -47,18 +47,31 @@ typedef enum {
     DTS_ERR_OOM = 3,            /* device or host allocation failed */
     DTS_ERR_CUDA = 4,           /* a CUDA runtime call failed */
     DTS_ERR_NOT_CONVERGED = 5,  /* max_iters reached above tol; results are usable */
-    DTS_ERR_TIMEOUT = 6,        /* reserved: a bounded device wait gave up */
+    DTS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up (tensor-core forms) */
     DTS_ERR_INTERNAL = 7        /* a device-side consistency check failed */
 } dts_status;
 
 /* Arithmetic of the sweep and of the moment<->direction contractions.
  * FP64: everything in FP64.
  * FP32: sweep, scatter-source contraction and per-octant moment partials in
- *       FP32; the Eq. 3 octant sum, the residual, the fixed sources and the
- *       balance in FP64. */
+ *       FP32 on the CUDA cores; the Eq. 3 octant sum of the scalar flux, the
+ *       residual and the balance in FP64.
+ * FP32_SPLITBF16: FP32 sweep; the scatter-source contraction of Eq. 2,
+ *       Q_n = sum_k M[n][k] T_k over the K Legendre moments, runs on the
+ *       tensor cores as a [cells x K] x [K x directions] product with both
+ *       operands split into bf16 high and low parts (hi.hi + hi.lo + lo.hi,
+ *       accumulated in FP32; ~1e-5 relative per term); each source iteration
+ *       materialises Q (one FP32 value per cell and direction) and the sweep
+ *       reads it. Eq. 3 moments from the FP32 angular fluxes, scalar flux,
+ *       residual and balance as in FP32.
+ * FP32_TF32: as FP32_SPLITBF16 with tf32 high and low parts (TF32 tensor
+ *       cores, three products; ~2^-21 relative per term).
+ * The two tensor-core forms need the 8 x 4 x 4 tile (the default for them). */
 typedef enum {
     DTS_PREC_FP64 = 0,
-    DTS_PREC_FP32 = 1
+    DTS_PREC_FP32 = 1,
+    DTS_PREC_FP32_SPLITBF16 = 2,
+    DTS_PREC_FP32_TF32 = 3
 } dts_precision;
 
 typedef enum {

@@ -613,7 +613,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int NDO, int K, int BX, bool PSI = false>
+template <int NDO, int K, int BX, bool PSI = false, bool QIN = false>
 struct BatchShape {
     static constexpr int BY = 4, BZ = 4, BV = BX * BY * BZ, NLINE = BY * BZ;
     static constexpr int SB = 32 / NDO, NL = SB * NDO;  // sources per warp, busy lanes
@@ -627,8 +627,11 @@ struct BatchShape {
     static constexpr bool PRE_CP = NCP <= 4, PRE_C = NJ <= 4;   // keep per-lane offsets in registers
     static constexpr int fxn = BY * BZ, fyn = BX * BZ, fzn = BX * BY;
     // float offsets
-    static constexpr int oT = 0;                        // [SB][TSTR] the line being swept, refilled after phase A
-    static constexpr int oP = oT + SB * TSTR;           // [SB][PSTR]
+    // [SB][TSTR] the line being swept, refilled after phase A; with the Q input instead a ring of
+    // QRING lines of the lanes' sources, [QRING][32][BX]
+    static constexpr int QRING = 3;
+    static constexpr int oT = 0;
+    static constexpr int oP = oT + (QIN ? QRING * 32 * BX : SB * TSTR);   // [SB][PSTR]
     static constexpr int oX = oP + (PSI ? 0 : SB * PSTR);   // [fxn][32] x faces, slot = local line
     static constexpr int oY = oX + fxn * 32;            // [BX][32] y faces of one z-layer, slot = lx
     static constexpr int oZ = oY + BX * 32;             // [fzn][32] z faces, slot = ly * BX + lx
@@ -637,8 +640,8 @@ struct BatchShape {
     static constexpr size_t bytes = sizeof(float) * nF + sizeof(double) * SB;
 };
 
-template <int NDO, int K, int BX, bool PSI>
-__host__ __device__ constexpr size_t sweep_batch_smem() { return BatchShape<NDO, K, BX, PSI>::bytes; }
+template <int NDO, int K, int BX, bool PSI, bool QIN = false>
+__host__ __device__ constexpr size_t sweep_batch_smem() { return BatchShape<NDO, K, BX, PSI, QIN>::bytes; }
 
 // Face buffers of the batched kernel: per (octant, source group, tile column)
 // one block of F slots x 32 lanes, in the octant-local frame of the sweep.
@@ -744,12 +747,13 @@ __device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], flo
     }
 }
 
-template <int NDO, int K, int BX, bool PSI, bool NX>
+template <int NDO, int K, int BX, bool PSI, bool NX, bool QIN>
 __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, const int oct, const int grp,
                                                  const int ta, const int tb, const int tc, const unsigned okmask,
                                                  const float (&mrow)[K], const float (&arow)[3])
 {
-    using S = BatchShape<NDO, K, BX, PSI>;
+    using S = BatchShape<NDO, K, BX, PSI, QIN>;
+    static_assert(!QIN || PSI, "the per-direction source input goes with the angular-flux output");
     constexpr int BY = S::BY, BZ = S::BZ, BV = S::BV, SB = S::SB, NL = S::NL, NQ = S::NQ;
     constexpr int TSTR = S::TSTR, PSTR = S::PSTR, NH = S::NH, NJ = S::NJ, NCP = S::NCP;
     constexpr int fxn = S::fxn, fyn = S::fyn, fzn = S::fzn;
@@ -784,7 +788,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         dst = il * TSTR + k * BX + 4 * h;
     };
     int csrc[S::PRE_CP ? NCP : 1], cdst[S::PRE_CP ? NCP : 1];
-    if constexpr (S::PRE_CP) {
+    if constexpr (S::PRE_CP && !QIN) {
 #pragma unroll
         for (int c = 0; c < NCP; ++c) chunk(c, csrc[c], cdst[c]);
     }
@@ -806,22 +810,38 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         }
         cp_async_commit();
     };
-    stage_line(0, 0);
+    if constexpr (!QIN) stage_line(0, 0);
 
     // phase A/B lane: (source bl, direction d)
     const int bl = lane / NDO, d = lane - bl * NDO;
     const bool srcok = lane < NL && (okmask >> bl & 1u);
-    unsigned long long m2[K];
+    unsigned long long m2[QIN ? 1 : K];
+    if constexpr (!QIN) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float m = srcok ? mrow[k] : 0.f;
-        m2[k] = f2pack(m, m);
+        for (int k = 0; k < K; ++k) {
+            const float m = srcok ? mrow[k] : 0.f;
+            m2[k] = f2pack(m, m);
+        }
     }
     const float ax = srcok ? arow[0] : 0.f, ay = srcok ? arow[1] : 0.f, az = srcok ? arow[2] : 0.f;
     const float asum = ax + ay + az;
     const float* trow = Tst + (srcok ? bl : 0) * TSTR;
     float* prow = Ps + (srcok ? bl : 0) * PSTR + d * BX;
-    float* psi_lane = p.part + ((((size_t)(b0 + (srcok ? bl : 0)) * 8 + oct) * p.NT + tile) * NDO + d) * BV;
+    const size_t lane_ofs = ((((size_t)(b0 + (srcok ? bl : 0)) * 8 + oct) * p.NT + tile) * NDO + d) * BV;
+    float* psi_lane = p.part + lane_ofs;
+    // Q input: the lane's per-direction source Q[b][oct][tile][d][cell] of a line (BX floats),
+    // copied two lines ahead into the lane's slot of a three-line ring
+    const float* q_lane = p.T + lane_ofs;
+    auto stage_q = [&](int line) {
+        if (!srcok) return;
+        const int ly = line % BY, lz = line / BY;
+        const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
+        const float* src = q_lane + (sz * BY + sy) * BX;
+        float* dst = Tst + ((line % S::QRING) * 32 + lane) * BX;
+#pragma unroll
+        for (int h = 0; h < BX / 4; ++h) cp_async16(dst + 4 * h, src + 4 * h);
+    };
+    if constexpr (QIN) stage_q(0);   // committed with the prologue's copies
 
     // phase C lane: (moment kc, group h); items (source il, quad qd) = h + NH * j
     const int kc = lane % K, hc = lane / K;
@@ -864,6 +884,10 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     batch_faces_in_async<BX>(fy, gy, tb > 0);    // z-layer 0; later layers stream in with the lines
     batch_faces_in_async<fzn>(fz, gz, tc > 0);
     cp_async_commit();
+    if constexpr (QIN) {
+        stage_q(1);
+        cp_async_commit();
+    }
 
     const int nvx = p.nx - tx * BX, nvy = p.ny - ty * BY, nvz = p.nz - tz * BZ;
     constexpr unsigned FULL = (1u << BX) - 1u;
@@ -873,14 +897,28 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 
 #pragma unroll 1
     for (int line = 0; line < S::NLINE; ++line) {
-        cp_async_wait0();   // this line's sources (copied during the previous line's walk)
+        // this line's sources (copied during the previous line's walk; with the Q input two lines
+        // ago, the latest group -- the next line's -- may still be in flight)
+        if constexpr (QIN) cp_async_wait1();
+        else cp_async_wait0();
         __syncwarp();
         const int ly = line % BY, lz = line / BY;
         const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
 
         // A: Q for the line's cells, two cells per packed FMA, storage x order
+        // (Q input: the line's sources were loaded during the previous line's walk)
         float qv[BX];
-        {
+        if constexpr (QIN) {
+            const float* src = Tst + ((line % S::QRING) * 32 + lane) * BX;
+#pragma unroll
+            for (int h = 0; h < BX / 4; ++h) {
+                const float4 v = *reinterpret_cast<const float4*>(src + 4 * h);
+                qv[4 * h] = v.x;
+                qv[4 * h + 1] = v.y;
+                qv[4 * h + 2] = v.z;
+                qv[4 * h + 3] = v.w;
+            }
+        } else {
             const float* tr = trow;
 #pragma unroll
             for (int qd = 0; qd < NQ; ++qd) {
@@ -902,7 +940,12 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         // the layer's y-faces went to registers during line ly = 0; the next layer's land in the
         // same buffer with the next line's sources
         if (ly == 1 && lz + 1 < BZ) batch_faces_in_async<BX>(fy, gy + (size_t)(lz + 1) * BX * 32, tb > 0);
-        if (line + 1 < S::NLINE) stage_line(line + 1, 0);
+        if constexpr (!QIN) {
+            if (line + 1 < S::NLINE) stage_line(line + 1, 0);
+        } else {
+            if (line + 2 < S::NLINE) stage_q(line + 2);   // into the slot of the line before this one
+            cp_async_commit();                           // one group per line, empty at the end
+        }
 
         // B: walk the line
         if (ly == 0) {
@@ -997,10 +1040,10 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 
 // s0, cnt: the stage's first entry in stage_tiles and its tile count (kernel
 // arguments, so a CTA's first dependent global load is its tile)
-template <int NDO, int K, int BX, bool PSI>
+template <int NDO, int K, int BX, bool PSI, bool QIN = false>
 __global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float> p, const int s0, const int cnt)
 {
-    using S = BatchShape<NDO, K, BX, PSI>;
+    using S = BatchShape<NDO, K, BX, PSI, QIN>;
     int bid = blockIdx.x;
     const int tl = bid % cnt;
     bid /= cnt;
@@ -1011,7 +1054,7 @@ __global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float>
     const bool dl = lane < S::NL;
     float mrow[K], arow[3];
 #pragma unroll
-    for (int k = 0; k < K; ++k) mrow[k] = dl ? p.M[(oct * NDO + d) * K + k] : 0.f;
+    for (int k = 0; k < K; ++k) mrow[k] = (dl && !QIN) ? p.M[(oct * NDO + d) * K + k] : 0.f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) arow[j] = dl ? p.A[(oct * NDO + d) * 3 + j] : 0.f;
     const int nb = min(S::SB, p.B - b0);
@@ -1020,9 +1063,47 @@ __global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float>
         if (p.active[b0 + i]) okmask |= 1u << i;
     if (okmask == 0) return;
     const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
-    if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
-    else sweep_batch_body<NDO, K, BX, PSI, false>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+    if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+    else sweep_batch_body<NDO, K, BX, PSI, false, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
 }
+
+// Error-free FP32 accumulation (Knuth's two-sum): s + e carries the exact sum
+// of the FP32 terms added so far (to within rounding of the small e), so the
+// FP64 scalar flux (double)s + (double)e equals the octant sum to ~2^-48.
+struct TwoSum {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
+
+// The per-cell tail of the FP32 reductions: store the FP64 scalar flux, form
+// T_0 = F_0 + sigma_s0 phi_00 in FP32, and accumulate this thread's residual
+// and balance terms in FP32 (summed across a warp in FP32, across warps and
+// blocks in FP64).
+struct RedTail {
+    float ds = 0.f, ns = 0.f, sr = 0.f, ab = 0.f;
+    // s0 = (double)ts.s + (double)ts.e rounds to the same FP32 value as the pair's FP32 sum (the
+    // FP64 sum is exact unless e is below 2^-29 of s, and then both round to s); the old flux
+    // enters only the balance term, where its FP32 value may be off by an ulp
+    __device__ __forceinline__ float cell(const TwoSum& ts, double s0, double old, float f0, float sl0, float st)
+    {
+        const float s0f = __fadd_rn(ts.s, ts.e), dd = (float)(s0 - old), oldf = s0f - dd;
+        ds = fmaf(dd, dd, ds);
+        ns = fmaf(s0f, s0f, ns);
+        ab = fmaf(st, s0f, ab);
+        sr += fmaf(sl0, oldf, f0);
+        return fmaf(sl0, s0f, f0);
+    }
+};
+
+// moment pairs of the Eq. 3 operator rows (an even count, so pairs of pairs load as 16 bytes)
+template <int K> struct PsiPairs { static constexpr int value = ((K + 1) / 2 + 1) & ~1; };   // even
 
 // Translation units that only launch the sweep define DTS_SWEEP_KERNEL_ONLY so
 // that the solver's other (non-template) kernels are defined once per library.
@@ -1105,41 +1186,6 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedParams<R> p)
         o[3] = ab;
     }
 }
-
-// Error-free FP32 accumulation (Knuth's two-sum): s + e carries the exact sum
-// of the FP32 terms added so far (to within rounding of the small e), so the
-// FP64 scalar flux (double)s + (double)e equals the octant sum to ~2^-48.
-struct TwoSum {
-    float s = 0.f, e = 0.f;
-    __device__ __forceinline__ void add(float x)
-    {
-        const float t = __fadd_rn(s, x);
-        const float bp = __fsub_rn(t, s);
-        e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s + (double)e; }
-};
-
-// The per-cell tail of the FP32 reductions: store the FP64 scalar flux, form
-// T_0 = F_0 + sigma_s0 phi_00 in FP32, and accumulate this thread's residual
-// and balance terms in FP32 (summed across a warp in FP32, across warps and
-// blocks in FP64).
-struct RedTail {
-    float ds = 0.f, ns = 0.f, sr = 0.f, ab = 0.f;
-    // s0 = (double)ts.s + (double)ts.e rounds to the same FP32 value as the pair's FP32 sum (the
-    // FP64 sum is exact unless e is below 2^-29 of s, and then both round to s); the old flux
-    // enters only the balance term, where its FP32 value may be off by an ulp
-    __device__ __forceinline__ float cell(const TwoSum& ts, double s0, double old, float f0, float sl0, float st)
-    {
-        const float s0f = __fadd_rn(ts.s, ts.e), dd = (float)(s0 - old), oldf = s0f - dd;
-        ds = fmaf(dd, dd, ds);
-        ns = fmaf(s0f, s0f, ns);
-        ab = fmaf(st, s0f, ab);
-        sr += fmaf(sl0, oldf, f0);
-        return fmaf(sl0, s0f, f0);
-    }
-};
 
 // The block's four partial sums: FP32 butterflies within each warp (FP64 runs
 // at a small fraction of the FP32 rate on this part), one barrier, then the
@@ -1243,7 +1289,6 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce4(const RedParams<float> 
 // FMAs. Each octant's directions are summed in FP32; the scalar flux takes
 // those octant sums exactly (two-sum) in octant order 0..7, the higher
 // moments stay in FP32.
-template <int K> struct PsiPairs { static constexpr int value = ((K + 1) / 2 + 1) & ~1; };   // even
 
 // the first octant's copies of psi_moments (buffer 0), for callers that start them early
 template <int NDO>

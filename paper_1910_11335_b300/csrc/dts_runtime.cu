@@ -23,6 +23,8 @@
 #include "../../include/dts.h"
 #include "dts_kernels.cuh"
 #include "dts_adjoint.cuh"
+#include "dts_tc.cuh"
+#include "dts_tc_launch.h"
 
 using namespace dts;
 
@@ -60,6 +62,15 @@ struct dts_problem {
     int line_warps = 2;               // warps per CTA of the line sweep kernel
     bool fp64 = true;
     bool psi_mode = false;   // batched FP32 sweep writes angular fluxes; moments formed by k_reduce_psi
+    // tensor-core forms: k_moments_q turns the angular fluxes into the next per-direction source Q
+    // (scatter-source contraction on tcgen05), which the batched sweep reads
+    bool q_mode = false;
+    int q_kind = 0;                   // 0 split BF16, 1 TF32
+    int q_grid = 0;                   // persistent CTAs of k_moments_q
+    void* Qbuf = nullptr;             // [B][8][NT][N_d/8][TV] FP32
+    float* Mop = nullptr;             // operator parts M' = 4 pi M, [parts][NP][16]
+    int* dev_err = nullptr;           // device error word of the bounded waits
+    int* h_err = nullptr;             // pinned copy, read after every iteration
     size_t rsz = 8;                   // sizeof(R)
     std::vector<int> stage_off_h;     // [n_stages+1]
     std::vector<double> mu, eta, xi, w;
@@ -352,6 +363,7 @@ bool batch_tile(const dts_problem* p)
     return !p->fp64 && p->TY == 4 && p->TZ == 4 && (p->TX == 8 || p->TX == 4);
 }
 
+// sources per warp of the batched kernels (lanes = source x direction pairs)
 int batch_sources_per_warp(const dts_problem* p) { return 32 / p->ndo; }
 
 // the direct-output form pays N_d angular fluxes per cell instead of 8 K octant
@@ -410,6 +422,7 @@ BatchFn batch_fn_x(int ndo, int K)
 
 BatchFn batch_fn(const dts_problem* p)
 {
+    if (p->q_mode) return dts_internal_qsweep_fn(p->ndo);
     if (p->psi_mode) return p->TX == 8 ? batch_fn_x<8, true>(p->ndo, p->K) : batch_fn_x<4, true>(p->ndo, p->K);
     return p->TX == 8 ? batch_fn_x<8, false>(p->ndo, p->K) : batch_fn_x<4, false>(p->ndo, p->K);
 }
@@ -477,6 +490,7 @@ RedFn<float> reduce4_fn(int K)
 size_t sweep_smem(const dts_problem* p)
 {
     if (batch_tile(p)) {
+        if (p->q_mode) return dts_internal_qsweep_smem(p->ndo);
         if (p->psi_mode) return p->TX == 8 ? batch_smem_x<8, true>(p->ndo, p->K) : batch_smem_x<4, true>(p->ndo, p->K);
         return p->TX == 8 ? batch_smem_x<8, false>(p->ndo, p->K) : batch_smem_x<4, false>(p->ndo, p->K);
     }
@@ -511,6 +525,19 @@ CellParams cell_params(const dts_problem* p)
     return c;
 }
 
+// arguments of k_moments_q: init = 1 forms Q = M F of the group's fixed source (phi = 0)
+QParams q_params(const dts_problem* p, int init)
+{
+    QParams q;
+    q.B = p->B; q.NT = p->NT; q.TV = p->TV; q.NC = p->NC; q.nitems = p->B * p->NT; q.init = init;
+    q.psi = (const float*)p->part; q.Q = (float*)p->Qbuf; q.phi00 = p->phi00;
+    q.F = (const float*)p->F; q.Fstride = p->Fstride; q.ctl = p->ctl;
+    q.sigs = (const float*)p->sigs; q.sigt = (const float*)p->sigt_r; q.mat_t = p->mat_t;
+    q.active = p->active; q.Dt = (const float*)p->Dt; q.Mop = p->Mop;
+    q.vol = p->d.dx * p->d.dy * p->d.dz; q.blk = p->blk; q.err = p->dev_err;
+    return q;
+}
+
 template <typename R>
 dts_status record_sweep(dts_problem* p)
 {
@@ -522,7 +549,7 @@ dts_status record_sweep(dts_problem* p)
     sp.stage_tiles = p->stage_tiles; sp.stage_off = p->stage_off;
     sp.diag_cells = p->diag_cells; sp.diag_off = p->diag_off;
     sp.M = (const R*)p->Mt; sp.Dt = (const R*)p->Dt; sp.A = (const R*)p->At; sp.Lw = p->Lw;
-    sp.T = (const R*)p->T; sp.sigt = (const R*)p->sigt_r; sp.part = (R*)p->part;
+    sp.T = (const R*)(p->q_mode ? p->Qbuf : p->T); sp.sigt = (const R*)p->sigt_r; sp.part = (R*)p->part;
     sp.xf = (R*)p->xf; sp.yf = (R*)p->yf; sp.zf = (R*)p->zf;
     sp.active = p->active; sp.leak = p->leak;
     const size_t smem = sweep_smem(p);
@@ -564,7 +591,10 @@ dts_status record_reduce(dts_problem* p)
     rp.blk = p->blk;
     int nblk = p->nblk;
     if constexpr (sizeof(R) == 4) {
-        if (p->psi_mode) {      // moments from the angular fluxes, two cells per thread
+        if (p->q_mode) {        // moments from the angular fluxes, then Q = M T on the tensor cores
+            nblk = p->NT;
+            CK(dts_internal_q_launch(p->ndo, p->K, p->q_kind, q_params(p, 0), p->q_grid, p->stream));
+        } else if (p->psi_mode) {      // moments from the angular fluxes, two cells per thread
             nblk = (p->NC / 2 + kRedThreads - 1) / kRedThreads;
             RedPsiFn rf;
             PushPsiFn uf;
@@ -584,6 +614,7 @@ dts_status record_reduce(dts_problem* p)
     p->graph_launches = p->n_stages + 2;
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(double) * 4 * p->B, cudaMemcpyDeviceToHost,
                        p->stream));
+    if (p->q_mode) CK(cudaMemcpyAsync(p->h_err, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     return DTS_OK;
 }
 
@@ -657,6 +688,10 @@ void launch_group_xs(dts_problem* p, int g)
 template <typename R>
 dts_status launch_group_init(dts_problem* p, int slot)
 {
+    if (p->q_mode) {   // Q = M F on the tensor cores
+        CK(dts_internal_q_launch(p->ndo, p->K, p->q_kind, q_params(p, 1), p->q_grid, p->stream));
+        return DTS_OK;
+    }
     const size_t total = (size_t)p->B * p->NC * p->K;
     CK(cudaMemcpyAsync(p->T, (const R*)p->F + (size_t)slot * p->Fstride, total * sizeof(R), cudaMemcpyDeviceToDevice,
                        p->stream));
@@ -714,6 +749,10 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
     const int W1 = p->W + 1;
     TRY(ensure_ring(p));
     TRY(build_graph(p));
+    if (p->q_mode) {
+        CK(cudaMemsetAsync(p->dev_err, 0, sizeof(int), p->stream));
+        *p->h_err = 0;
+    }
     CK(cudaEventRecord(p->ev0, p->stream));
     // A1: uncollided fluence, all sources and groups
     {
@@ -756,13 +795,6 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
         NvtxRange group_range(gname);
         const int slot = g % W1;
         k_set_ctl<<<1, 1, 0, p->stream>>>(p->ctl, g, slot);
-        if (p->fp64) {
-            launch_group_xs<double>(p, g);
-            TRY(launch_group_init<double>(p, slot));
-        } else {
-            launch_group_xs<float>(p, g);
-            TRY(launch_group_init<float>(p, slot));
-        }
         CK(cudaMemsetAsync(p->phi00, 0, sizeof(double) * B * p->NC, p->stream));
         for (int b = 0; b < B; ++b) {
             p->h_active[b] = 1;
@@ -770,7 +802,16 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
             best[b] = INFINITY;
             last_improve[b] = 0;
         }
+        // every member is active again before the group's first source is formed (the
+        // tensor-core forms' Q = M F skips inactive members)
         CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+        if (p->fp64) {
+            launch_group_xs<double>(p, g);
+            TRY(launch_group_init<double>(p, slot));
+        } else {
+            launch_group_xs<float>(p, g);
+            TRY(launch_group_init<float>(p, slot));
+        }
         CK(cudaGetLastError());
         int n_active = B;
         for (int it = 1; it <= p->d.max_iters && n_active > 0; ++it) {
@@ -781,6 +822,8 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
             CK(cudaGraphLaunch(p->graph_red, p->stream));
             CK(cudaEventRecord(p->evc, p->stream));
             CK(cudaStreamSynchronize(p->stream));
+            if (p->q_mode && *p->h_err)
+                return fail(p, DTS_ERR_TIMEOUT, "k_moments_q: a bounded wait on a bulk copy or the tensor cores gave up");
             launches += p->graph_launches;
             sweep_launches += p->n_stages;
             {
@@ -880,7 +923,7 @@ void choose_tile(dts_problem* p)
     // batched kernel's 8 x 4 x 4 tile; otherwise 32 x-lines (4 in y, 8 in z)
     // per tile for the warp-synchronous kernel, 8 cells long in x (measured
     // fastest of 4..32 on the 96^3 S8 P3 batch)
-    const bool batched = p->d.precision == DTS_PREC_FP32 && p->d.batch >= 32 / p->ndo &&
+    const bool batched = (p->q_mode || (p->d.precision == DTS_PREC_FP32 && p->d.batch >= 32 / p->ndo)) &&
                          batch_offsets_fit(p, 8, 4, 4);
     p->TX = 8;
     p->TY = 4;
@@ -969,6 +1012,39 @@ dts_status upload_tables(dts_problem* p, const std::vector<double>& Dkn, const s
     return DTS_OK;
 }
 
+// FP32 value of x rounded to nearest-even at `drop` low mantissa bits (16: bf16, 13: tf32)
+float round_mantissa(double x, int drop)
+{
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t half = (1u << (drop - 1)) - 1u + ((u >> drop) & 1u);
+    u = (u + half) & ~((1u << drop) - 1u);
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Operand parts of the tensor-core contraction: M' = 4 pi M padded to [NP][16]
+// (N_d rounded up to a multiple of 16, K up to 16), stored as the parts
+// (hi, lo) with hi = r(M'), lo = r(M' - hi), r the rounding to bf16 (split
+// BF16) or to tf32 (split TF32).
+dts_status upload_qop(dts_problem* p, const std::vector<double>& Mnk)
+{
+    const int nd = p->nd, K = p->K, NP = (nd + 15) / 16 * 16;
+    const int drop = p->q_kind == 0 ? 16 : 13;
+    std::vector<float> op((size_t)2 * NP * 16, 0.f);
+    for (int n = 0; n < nd; ++n)
+        for (int k = 0; k < K; ++k) {
+            const double m = 4.0 * kPi * Mnk[(size_t)n * K + k];
+            const float hi = round_mantissa(m, drop);
+            op[(size_t)n * 16 + k] = hi;
+            op[(size_t)NP * 16 + (size_t)n * 16 + k] = round_mantissa(m - (double)hi, drop);
+        }
+    TRY(dalloc_t(p, &p->Mop, op.size()));
+    CK(cudaMemcpy(p->Mop, op.data(), op.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return DTS_OK;
+}
+
 dts_status create(const dts_problem_desc* desc, dts_problem* p)
 {
     p->d = *desc;
@@ -983,7 +1059,8 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     if (d.legendre_order < 0 || d.legendre_order > 3)
         return fail(p, DTS_ERR_INVALID_ARG, "legendre_order must be in 0..3");
     if (d.batch < 1) return fail(p, DTS_ERR_INVALID_ARG, "batch must be >= 1");
-    if (d.precision != DTS_PREC_FP64 && d.precision != DTS_PREC_FP32)
+    if (d.precision != DTS_PREC_FP64 && d.precision != DTS_PREC_FP32 && d.precision != DTS_PREC_FP32_SPLITBF16 &&
+        d.precision != DTS_PREC_FP32_TF32)
         return fail(p, DTS_ERR_INVALID_ARG, "unknown precision");
     if (!(d.tol >= 0.0) || !isfin(d.tol)) return fail(p, DTS_ERR_INVALID_ARG, "tol must be finite and >= 0");
     if (d.max_iters < 1) return fail(p, DTS_ERR_INVALID_ARG, "max_iters must be >= 1");
@@ -1002,8 +1079,12 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     p->B = d.batch;
     p->fp64 = d.precision == DTS_PREC_FP64;
     p->rsz = p->fp64 ? sizeof(double) : sizeof(float);
+    p->q_mode = d.precision == DTS_PREC_FP32_SPLITBF16 || d.precision == DTS_PREC_FP32_TF32;
+    p->q_kind = d.precision == DTS_PREC_FP32_TF32 ? 1 : 0;
     choose_tile(p);
-    p->psi_mode = psi_form(p);
+    if (p->q_mode && !(p->TX == 8 && p->TY == 4 && p->TZ == 4))
+        return fail(p, DTS_ERR_INVALID_ARG, "the tensor-core precisions need the 8 x 4 x 4 tile");
+    p->psi_mode = p->q_mode || psi_form(p);
 
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));
@@ -1012,11 +1093,22 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, d.device));
     p->n_sm = prop.multiProcessorCount;
-    if (p->psi_mode) {
+    if (p->psi_mode && !p->q_mode) {
         RedPsiFn rf;
         PushPsiFn uf;
         psi_fns(p, rf, uf);
         if (!rf) p->psi_mode = false;   // octant partials instead
+    }
+    if (p->q_mode) {
+        const int qs = dts_internal_q_smem(p->ndo, p->K, p->q_kind);
+        if (qs < 0 || (size_t)qs > prop.sharedMemPerBlockOptin)
+            return fail(p, DTS_ERR_INVALID_ARG, "no tensor-core moment kernel for this (S_N, P_L)");
+        CK(dts_internal_q_prepare(p->ndo, p->K, p->q_kind));
+        int per_sm = 0;
+        CK(dts_internal_q_occupancy(p->ndo, p->K, p->q_kind, &per_sm));
+        // every resident CTA holds kQTmemCols of the SM's 512 tensor-memory columns
+        per_sm = std::max(1, std::min(per_sm, 512 / kQTmemCols));
+        p->q_grid = per_sm * p->n_sm;
     }
     if (sweep_smem(p) > prop.sharedMemPerBlockOptin)
         return fail(p, DTS_ERR_INVALID_ARG, "wavefront tile needs more shared memory than a CTA has");
@@ -1040,10 +1132,18 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     TRY(dalloc_t(p, &p->mat_t, NC));
     TRY(dalloc_t(p, &p->mat_nat, V));
     TRY(dalloc_t(p, &p->phi00, B * NC));
-    TRY(dalloc(p, &p->T, B * NC * K * p->rsz));
+    TRY(dalloc(p, &p->T, p->q_mode ? 16 : B * NC * K * p->rsz));
     // octant partials [8][B][NT][K][TV], or in the direct-output form the
     // angular fluxes [B][8][NT][N_d/8][TV]
     TRY(dalloc(p, &p->part, 8 * B * NC * (p->psi_mode ? (size_t)p->ndo : (size_t)K) * p->rsz));
+    if (p->q_mode) {
+        TRY(dalloc(p, &p->Qbuf, 8 * B * NC * (size_t)p->ndo * sizeof(float)));
+        TRY(upload_qop(p, M));
+        TRY(dalloc_t(p, &p->dev_err, 1));
+        CK(cudaMemset(p->dev_err, 0, sizeof(int)));
+        CK(cudaMallocHost((void**)&p->h_err, sizeof(int)));
+        *p->h_err = 0;
+    }
     const size_t nf = (size_t)p->ndo;
     size_t fxs = 8 * B * (size_t)p->NTy * p->NTz * nf * p->TY * p->TZ * p->rsz;
     size_t fys = 8 * B * (size_t)p->NTx * p->NTz * nf * p->TX * p->TZ * p->rsz;
@@ -1069,7 +1169,7 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     TRY(dalloc_t(p, &p->spec, B * G));
     TRY(dalloc_t(p, &p->leak, B));
     p->nblk = (p->NC + kRedThreads - 1) / kRedThreads;
-    TRY(dalloc_t(p, &p->blk, B * p->nblk * 4));
+    TRY(dalloc_t(p, &p->blk, B * std::max(p->nblk, p->NT) * 4));   // k_moments_q: one partial per tile
     TRY(dalloc_t(p, &p->status, B * 4));
     TRY(dalloc_t(p, &p->active, B));
     TRY(dalloc_t(p, &p->ctl, 4));
@@ -1108,6 +1208,7 @@ void destroy(dts_problem* p)
     p->allocs.clear();
     if (p->h_status) cudaFreeHost(p->h_status);
     if (p->h_active) cudaFreeHost(p->h_active);
+    if (p->h_err) cudaFreeHost(p->h_err);
     for (cudaEvent_t e : {p->ev0, p->ev1, p->eva, p->evb, p->evc})
         if (e) cudaEventDestroy(e);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -1809,12 +1910,12 @@ dts_status dts_tune_tile(dts_problem_desc* desc, double* best_updates_per_s)
         }
     }
     std::vector<std::array<int, 3>> cand;
-    if (desc->precision == DTS_PREC_FP32) {
-        cand.push_back({8, 4, 4});
-        cand.push_back({4, 4, 4});
-    }
-    for (auto t : std::vector<std::array<int, 3>>{{8, 4, 8}, {4, 4, 8}, {16, 4, 8}, {8, 8, 4}, {8, 8, 8}, {4, 4, 4}})
-        cand.push_back(t);
+    const bool tc = desc->precision == DTS_PREC_FP32_SPLITBF16 || desc->precision == DTS_PREC_FP32_TF32;
+    if (desc->precision == DTS_PREC_FP32 || tc) cand.push_back({8, 4, 4});
+    if (desc->precision == DTS_PREC_FP32) cand.push_back({4, 4, 4});
+    if (!tc)
+        for (auto t : std::vector<std::array<int, 3>>{{8, 4, 8}, {4, 4, 8}, {16, 4, 8}, {8, 8, 4}, {8, 8, 8}, {4, 4, 4}})
+            cand.push_back(t);
     // probe: one group, homogeneous scatterer, unit volumetric source, two iterations
     const int L = desc->legendre_order, V = desc->nx * desc->ny * desc->nz;
     const double h = std::min(desc->dx, std::min(desc->dy, desc->dz));

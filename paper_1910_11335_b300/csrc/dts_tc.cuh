@@ -1,0 +1,556 @@
+// dts_tc.cuh -- the Eq. 3 reduction fused with the scatter-source contraction
+// on the fifth-generation tensor cores (tcgen05, sm_103a).
+//
+// One source iteration of the tensor-core forms is
+//   sweep:   Q[b][o][tile][d][cell]  ->  psi[b][o][tile][d][cell]   (k_sweep_batch, Q input)
+//   moments: psi -> phi_lm (Eq. 3, CUDA cores), T = F + sigma_s phi (Eq. 2),
+//            Q = M T on the tensor cores                           (k_moments_q)
+// so the sweep no longer contracts moments to directions itself: its
+// per-update source arrives as one FP32 value per (cell, direction).
+//
+// The contraction of one (source, tile) item is the dense product
+//   Q[128 cells x N_d] = T[128 cells x K] . M^T[K x N_d]
+// with K = (L+1)^2 <= 16 moments, padded to 16, and N_d directions padded to a
+// multiple of 16: one tcgen05.mma of M = 128 rows per (product, K step), the
+// FP32 accumulator in tensor memory (one TMEM lane per cell), read back with
+// tcgen05.ld and stored as coalesced 128-byte rows of Q.
+//
+// Operand precisions (dts_precision):
+//   split BF16: T' = T_hi + T_lo and M' = M_hi + M_lo with bf16 parts, three
+//               products hi.hi + hi.lo + lo.hi accumulated in FP32 (the
+//               dropped lo.lo term and the rounding of the lo parts are
+//               ~2^-17 of each term);
+//   split TF32: the same three products with tf32 parts (10 explicit mantissa
+//               bits each, round to nearest), ~2^-21 of each term; a single
+//               TF32 product (T and M rounded once, ~2^-12 relative per
+//               operand) measured 1.2e-4 relative L2 on the scalar fluence of
+//               a small cone-beam case, above the 1e-4 gate of the
+//               reduced-precision forms, so it is not offered.
+// In both, the operator is scaled as M' = 4 pi M and the moments as
+// T' = T / (4 pi), so that the isotropic column M'[n][0] = 1 is exact and the
+// rounding of the operator adds no bias to the dominant l = 0 term.
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "dts_kernels.cuh"
+
+namespace dts {
+
+// --------------------------------------------------------------------------
+// PTX wrappers: mbarrier, bulk copy, tcgen05
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase: false when the phase did not complete
+// within the limit (the caller records an error and stops using the barrier).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    constexpr int kLimit = 1 << 22;   // try_wait suspends for a while per call: seconds in total
+    for (int i = 0; i < kLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// global -> shared bulk copy (TMA, no tensor map); bytes and both addresses multiples of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// whole warp: allocate ncols (power of two >= 32) TMEM columns, address written to *slot
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: the operand is
+// tiled into core matrices of 8 rows x 16 bytes (128 contiguous bytes); lbo
+// is the byte distance between core matrices adjacent along K, sbo between
+// core matrices adjacent along M (or N).
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((smem_addr(p) & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of the fifth-generation tensor cores
+    return d;                 // base offset 0, no swizzle
+}
+
+// Instruction descriptor of kind::f16 / kind::tf32: FP32 accumulator, A and B
+// of format fmt (1 = BF16, 2 = TF32), both K-major, M x N.
+__host__ __device__ constexpr uint32_t mma_idesc(uint32_t fmt, int M, int N)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int MODE>   // 0: kind::f16 (bf16 operands), 1: kind::tf32
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    if constexpr (MODE == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+// arrive on *bar once every tcgen05.mma issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (thread i: lane base + i)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t tf32_rn(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// --------------------------------------------------------------------------
+// k_moments_q
+// --------------------------------------------------------------------------
+constexpr int kQCells = 128;     // cells of an 8 x 4 x 4 tile = rows of the MMA = TMEM lanes
+constexpr int kQThreads = 256;   // two threads per cell: octants 0-3 and 4-7, Q columns split alike
+constexpr int kQTmemCols = 128;  // >= the padded direction count (<= 80)
+
+struct QParams {
+    int B, NT, TV, NC;
+    int nitems;                  // B * NT
+    int init;                    // 1: Q = M F (first iteration of a group; phi = 0, no psi read)
+    const float* psi;            // [B][8][NT][NDO][TV]
+    float* Q;                    // [B][8][NT][NDO][TV]
+    double* phi00;               // [B][NC]
+    const float* F;              // fixed-source ring, [slot][B][NT][K][TV]
+    size_t Fstride;
+    const int* ctl;              // [1] = ring slot of the group
+    const float* sigs;           // [L+1][NC]
+    const float* sigt;           // [NC]
+    const int* mat_t;            // [NC]
+    const int* active;           // [B]
+    const float* Dt;             // [N_d][K] moment operator
+    const float* Mop;            // [2][NP][16] operator parts M' = hi + lo (bf16 or tf32 values)
+    double vol;
+    double* blk;                 // [B][NT][4] residual and balance partials per item
+    int* err;                    // device error word (1: a bounded wait gave up)
+};
+
+template <int NDO, int K, int MODE>
+struct QShape {
+    static constexpr int ND = 8 * NDO;
+    static constexpr int NP = (ND + 15) / 16 * 16;            // N of the MMA
+    static constexpr int NCH = NP / 8;                        // 8-column TMEM chunks
+    static constexpr int KP = PsiPairs<K>::value;             // moment pairs of the Eq. 3 operator
+    static constexpr int PSI_STAGE = ND * kQCells * 4;        // bytes of one item's angular fluxes
+    static constexpr int XCH = 4 + 1 + 2 * KP;                // floats one upper-half thread hands over
+    static constexpr int ROWB = MODE == 0 ? 32 : 64;          // bytes of one 16-moment operand row
+    static constexpr int SBO = 8 * ROWB;                      // bytes between 8-row groups
+    static constexpr int A_BYTES = kQCells * ROWB;            // one operand part of T
+    static constexpr int B_BYTES = NP * ROWB;                 // one operand part of M'
+    // the hand-over goes through the consumed flux stage when it fits (N_d >= 48), else its own region
+    static constexpr bool XIN = XCH * kQCells * 4 <= PSI_STAGE;
+    // byte offsets in dynamic shared memory
+    static constexpr int oPsi = 0;                            // [2][ND][128] float
+    static constexpr int oA = oPsi + 2 * PSI_STAGE;           // A parts (hi, lo)
+    static constexpr int oB = oA + 2 * A_BYTES;               // B parts (hi, lo)
+    static constexpr int oD = oB + 2 * B_BYTES;               // [ND][KP] moment pairs (8 B each)
+    static constexpr int oRed = oD + ND * KP * 8;             // [8 warps][4] double
+    static constexpr int oBar = oRed + 32 * 8;                // 3 mbarriers
+    static constexpr int oSlot = oBar + 3 * 8;                // TMEM address
+    static constexpr int oX = oSlot + 16;                     // [XCH][128] float unless XIN
+    static constexpr int bytes = oX + (XIN ? 0 : XCH * kQCells * 4);
+};
+
+template <int NDO, int K, int MODE>
+__host__ __device__ constexpr int moments_q_smem() { return QShape<NDO, K, MODE>::bytes; }
+
+// the byte offset of element (row, k) of a K-major operand part
+template <int ROWB>
+__device__ __forceinline__ int op_offset(int row, int kbyte)
+{
+    return (row >> 3) * (8 * ROWB) + (kbyte >> 4) * 128 + (row & 7) * 16 + (kbyte & 15);
+}
+
+// f(integral_constant<int, i>) for i = B .. E-1, unrolled at compile time
+template <int B, int E, typename Fn>
+__device__ __forceinline__ void static_for(Fn&& f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+// Persistent: each CTA walks the (source, tile) items blockIdx.x, +gridDim.x,
+// ... of active sources, with a two-stage ring of angular-flux tiles loaded by
+// bulk copies one item ahead. Thread t works on cell c = t % 128; half
+// h = t / 128 forms the Eq. 3 partial moments of octants 4h..4h+3 and stores
+// half of the item's Q columns; the lower half combines the partials, forms
+// T, the residual terms and the MMA operand.
+template <int NDO, int K, int MODE>
+__global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
+{
+    using S = QShape<NDO, K, MODE>;
+    constexpr int ND = S::ND, NP = S::NP, KP = S::KP, ROWB = S::ROWB, XCH = S::XCH;
+    extern __shared__ __align__(1024) unsigned char qsm[];
+    float* spsi = reinterpret_cast<float*>(qsm + S::oPsi);
+    unsigned char* sA = qsm + S::oA;
+    unsigned char* sB = qsm + S::oB;
+    unsigned long long* Dp = reinterpret_cast<unsigned long long*>(qsm + S::oD);
+    double* red = reinterpret_cast<double*>(qsm + S::oRed);
+    uint64_t* full = reinterpret_cast<uint64_t*>(qsm + S::oBar);   // [0], [1]: psi stages
+    uint64_t* mbar = full + 2;                                     // MMA completion
+    uint32_t* slot = reinterpret_cast<uint32_t*>(qsm + S::oSlot);
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int c = t & (kQCells - 1), h = t / kQCells;
+
+    if (t == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (w == 0) tmem_alloc(slot, kQTmemCols);
+    // B operand: the scaled operator parts, [n][k] K-major (values exactly representable)
+    for (int i = t; i < 2 * NP * 16; i += kQThreads) {
+        const int part = i / (NP * 16), r = i - part * NP * 16, n = r >> 4, k = r & 15;
+        const float v = p.Mop[i];
+        unsigned char* base = sB + part * S::B_BYTES;
+        if constexpr (MODE == 0)
+            *reinterpret_cast<__nv_bfloat16*>(base + op_offset<ROWB>(n, 2 * k)) = __float2bfloat16_rn(v);
+        else
+            *reinterpret_cast<float*>(base + op_offset<ROWB>(n, 4 * k)) = v;
+    }
+    if (!p.init) {   // moment pairs (D[n][2j], D[n][2j+1]) of the Eq. 3 operator
+        for (int i = t; i < ND * KP; i += kQThreads) {
+            const int n = i / KP, j = i - n * KP;
+            const float lo = 2 * j < K ? p.Dt[n * K + 2 * j] : 0.f, hi = 2 * j + 1 < K ? p.Dt[n * K + 2 * j + 1] : 0.f;
+            Dp[i] = f2pack(lo, hi);
+        }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+
+    // the active items of this CTA, in order
+    auto next_item = [&](int it) {
+        for (; it < p.nitems; it += gridDim.x)
+            if (p.active[it / p.NT]) return it;
+        return p.nitems;
+    };
+    auto issue = [&](int it, int stage) {   // one item's psi: 8 octant blocks of ND/8 x 128 floats
+        const int b = it / p.NT, tile = it - b * p.NT;
+        constexpr uint32_t ob = NDO * kQCells * 4;
+        mbar_expect_tx(&full[stage], (uint32_t)S::PSI_STAGE);
+        for (int o = 0; o < 8; ++o)
+            bulk_load(reinterpret_cast<unsigned char*>(spsi) + stage * S::PSI_STAGE + o * ob,
+                      p.psi + (((size_t)b * 8 + o) * p.NT + tile) * (size_t)(NDO * kQCells), ob, &full[stage]);
+    };
+
+    int it = next_item(blockIdx.x);
+    if (!p.init && t == 0 && it < p.nitems) issue(it, 0);
+    uint32_t phase_full[2] = {0u, 0u}, phase_mma = 0u;
+    bool failed = false;
+    constexpr float kInv4Pi = 0.0795774715459476679f;
+    constexpr uint32_t idesc = mma_idesc(MODE == 0 ? 1u : 2u, kQCells, NP);
+    constexpr int NLEG = K == 1 ? 1 : K == 4 ? 2 : K == 9 ? 3 : 4;
+
+    for (int n_done = 0; it < p.nitems; ++n_done) {
+        const int stage = n_done & 1;
+        const int b = it / p.NT, tile = it - b * p.NT;
+        const int nxt = next_item(it + gridDim.x);
+        if (!p.init && t == 0 && nxt < p.nitems) issue(nxt, stage ^ 1);   // its stage was read last item
+        const int ct = tile * p.TV + c;
+        // the lower half's per-cell operands (loaded after the moment loop, which needs the registers)
+        float f[K], sl[NLEG], stc = 0.f;
+        int mat = -1;
+        double old = 0.0;
+        double* ph = p.phi00 + (size_t)b * p.NC + ct;
+        auto load_cell = [&]() {
+            const float* __restrict__ F = p.F + (size_t)p.ctl[1] * p.Fstride +
+                                          ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
+#pragma unroll
+            for (int k = 0; k < K; ++k) f[k] = F[(size_t)k * p.TV];
+#pragma unroll
+            for (int l = 0; l < NLEG; ++l) sl[l] = p.sigs[(size_t)l * p.NC + ct];
+            stc = p.sigt[ct];
+            mat = p.mat_t[ct];
+            if (!p.init) old = *ph;
+        };
+        float T[K];
+        RedTail tl;
+        if (p.init) {
+            if (h == 0) {
+                load_cell();
+#pragma unroll
+                for (int k = 0; k < K; ++k) T[k] = f[k];
+            }
+        } else {
+            // the block agrees on the outcome, so that no thread leaves while others wait at a barrier
+            if (__syncthreads_or(!mbar_wait(&full[stage], phase_full[stage]))) {
+                failed = true;
+                break;
+            }
+            phase_full[stage] ^= 1u;
+            float* sp = spsi + stage * (S::PSI_STAGE / 4);
+            float os[4];   // moment 0 of each of this half's octants (FP32 sums of its directions)
+            float m1 = 0.f;
+            unsigned long long acc[KP];
+#pragma unroll
+            for (int j = 0; j < KP; ++j) acc[j] = 0ull;
+#pragma unroll 1
+            for (int oo = 0; oo < 4; ++oo) {
+                const int o = 4 * h + oo;
+                unsigned long long f0 = 0ull;   // moments (0, 1) of this octant
+#pragma unroll 2
+                for (int d = 0; d < NDO; ++d) {
+                    const float v = sp[(o * NDO + d) * kQCells + c];
+                    const unsigned long long a = f2pack(v, v);
+                    const ulonglong2* dq = reinterpret_cast<const ulonglong2*>(Dp + (o * NDO + d) * KP);
+#pragma unroll
+                    for (int j = 0; j < KP / 2; ++j) {
+                        const ulonglong2 dd = dq[j];
+                        if (j == 0) f0 = ffma2(dd.x, a, f0);
+                        else acc[2 * j] = ffma2(dd.x, a, acc[2 * j]);
+                        acc[2 * j + 1] = ffma2(dd.y, a, acc[2 * j + 1]);
+                    }
+                }
+                float hi;
+                f2unpack(f0, os[oo], hi);
+                m1 += hi;
+            }
+            __syncthreads();   // the flux stage is consumed: the upper half hands over through it
+            float* xch = (S::XIN ? sp : reinterpret_cast<float*>(qsm + S::oX)) + c;   // [XCH][128]
+            if (h == 1) {
+#pragma unroll
+                for (int oo = 0; oo < 4; ++oo) xch[oo * kQCells] = os[oo];
+                xch[4 * kQCells] = m1;
+#pragma unroll
+                for (int j = 0; j < KP; ++j) {
+                    float lo, hi;
+                    f2unpack(acc[j], lo, hi);
+                    xch[(5 + 2 * j) * kQCells] = lo;
+                    xch[(6 + 2 * j) * kQCells] = hi;
+                }
+            }
+            if (h == 0) load_cell();
+            __syncthreads();
+            if (h == 0) {
+                TwoSum s0;   // the scalar flux: the eight octant sums added exactly, in octant order
+#pragma unroll
+                for (int oo = 0; oo < 4; ++oo) s0.add(os[oo]);
+#pragma unroll
+                for (int oo = 0; oo < 4; ++oo) s0.add(xch[oo * kQCells]);
+                m1 += xch[4 * kQCells];
+#pragma unroll
+                for (int j = 0; j < KP; ++j)
+                    acc[j] = fadd2(acc[j], f2pack(xch[(5 + 2 * j) * kQCells], xch[(6 + 2 * j) * kQCells]));
+                if (mat < 0) {
+                    *ph = 0.0;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) T[k] = 0.f;
+                } else {
+                    const double phi = s0.value();
+                    T[0] = tl.cell(s0, phi, old, f[0], sl[0], stc);
+                    *ph = phi;
+#pragma unroll
+                    for (int k = 1; k < K; ++k) {
+                        float mk;
+                        if (k == 1) {
+                            mk = m1;
+                        } else {
+                            float lo, hi;
+                            f2unpack(acc[k / 2], lo, hi);
+                            mk = (k & 1) ? hi : lo;
+                        }
+                        T[k] = fmaf(sl[l_of_k(k)], mk, f[k]);
+                    }
+                }
+            }
+        }
+        // A operand row c: T' = T / (4 pi), padded to 16 moments, as (hi, lo) parts
+        if (h == 0) {
+            if constexpr (MODE == 0) {
+                uint32_t hw[8], lw[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float a0 = 2 * j < K ? T[2 * j] * kInv4Pi : 0.f;
+                    const float a1 = 2 * j + 1 < K ? T[2 * j + 1] * kInv4Pi : 0.f;
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(a0 - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(a1 - __bfloat162float(h1));
+                    hw[j] = bf16x2_bits(h0, h1);
+                    lw[j] = bf16x2_bits(l0, l1);
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    *reinterpret_cast<uint4*>(sA + op_offset<ROWB>(c, 16 * q)) =
+                        make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                    *reinterpret_cast<uint4*>(sA + S::A_BYTES + op_offset<ROWB>(c, 16 * q)) =
+                        make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                }
+            } else {
+                uint32_t hv[16], lv[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const float a = k < K ? T[k] * kInv4Pi : 0.f;
+                    hv[k] = tf32_rn(a);
+                    lv[k] = tf32_rn(a - __uint_as_float(hv[k]));
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    *reinterpret_cast<uint4*>(sA + op_offset<ROWB>(c, 16 * q)) =
+                        make_uint4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+                    *reinterpret_cast<uint4*>(sA + S::A_BYTES + op_offset<ROWB>(c, 16 * q)) =
+                        make_uint4(lv[4 * q], lv[4 * q + 1], lv[4 * q + 2], lv[4 * q + 3]);
+                }
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();   // A complete; the last item's TMEM reads are done
+        if (t == 0) {
+            tc_fence_after();
+            // products hi.hi, hi.lo, lo.hi; bf16 takes K = 16 per instruction, tf32 K = 8 (two
+            // core matrices along K, so the second K step starts 256 bytes further)
+            constexpr int KSTEPS = MODE == 0 ? 1 : 2;
+            const unsigned char* As[3] = {sA, sA, sA + S::A_BYTES};
+            const unsigned char* Bs[3] = {sB, sB + S::B_BYTES, sB};
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+                for (int ks = 0; ks < KSTEPS; ++ks)
+                    mma_issue<MODE>(tmem, smem_desc(As[pr] + ks * 256, 128, S::SBO),
+                                    smem_desc(Bs[pr] + ks * 256, 128, S::SBO), idesc,
+                                    (pr | ks) ? 1u : 0u);
+            mma_commit(mbar);
+        }
+        // residual and balance partials of the item while the MMA runs (the upper half adds zeros)
+        if (!p.init) {
+            float v[4] = {tl.ds, tl.ns, tl.sr, tl.ab};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+            if (lane == 0)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) red[w * 4 + i] = (double)v[i];
+        }
+        // one barrier: the MMA wait's outcome is shared, and red[] is visible to the threads below
+        if (__syncthreads_or(!mbar_wait(mbar, phase_mma))) {
+            failed = true;
+            break;
+        }
+        phase_mma ^= 1u;
+        tc_fence_after();
+        {
+            // half h stores the 8-column chunks [h C0, ...): column n = o NDO + d of cell c goes to
+            // Q[b][o][tile][d][c]; the chunk ranges are compile-time so that n, o, d are constants
+            constexpr int C0 = (S::NCH + 1) / 2;
+            float* qb = p.Q + ((size_t)b * 8 * p.NT + tile) * (size_t)(NDO * p.TV) + c;
+            const size_t ostr = (size_t)p.NT * (NDO * p.TV);
+            const uint32_t lanes = tmem + ((uint32_t)(32 * (w & 3)) << 16);
+            auto store_chunk = [&](auto chv) {
+                constexpr int ch = decltype(chv)::value;
+                uint32_t r[8];
+                tmem_ld8(lanes + (uint32_t)(8 * ch), r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    constexpr int nb = 8 * ch;
+                    const int n = nb + i;
+                    if (n < ND) qb[(size_t)(n / NDO) * ostr + (n % NDO) * p.TV] = __uint_as_float(r[i]);
+                }
+            };
+            if (h == 0) static_for<0, C0>(store_chunk);
+            else static_for<C0, S::NCH>(store_chunk);
+        }
+        if (!p.init && t < 4) {
+            double a = 0.0;
+#pragma unroll
+            for (int i = 0; i < kQThreads / 32; ++i) a += red[i * 4 + t];
+            p.blk[((size_t)b * p.NT + tile) * 4 + t] = t < 2 ? a : p.vol * a;
+        }
+        it = nxt;
+    }
+    if (failed && t == 0) atomicExch(p.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) tmem_free(tmem, kQTmemCols);
+}
+
+}  // namespace dts

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libdts.so")
 
 DTS_OK, DTS_ERR_INVALID_ARG, DTS_ERR_STATE, DTS_ERR_OOM, DTS_ERR_CUDA, DTS_ERR_NOT_CONVERGED, \
     DTS_ERR_TIMEOUT, DTS_ERR_INTERNAL = range(8)
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32_SPLITBF16, PREC_FP32_TF32 = 0, 1, 2, 3
 UNCOLLIDED, COLLIDED, TOTAL = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
@@ -159,9 +159,26 @@ def sweep_once_noalloc(nx, ny, nz, dx, dy, dz, sn_order, legendre_order, src_mom
     """One FP64 source iteration (sweep + moments) of one group using only the
     library's fixed device scratch array, for callers that must not allocate.
     src_moments [K][V], sigma_t [V] and phi [K][V] are contiguous float64 CUDA
-    tensors; work is enqueued on `stream` (a cudaStream_t handle or None)."""
-    for t in (src_moments, sigma_t, phi):
-        assert t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous()
+    tensors on the current device; work is enqueued on `stream` (a
+    cudaStream_t handle or None). Raises ValueError before any device work
+    when a tensor is not such a tensor or is too short."""
+    import torch
+    K, V = (legendre_order + 1) ** 2, nx * ny * nz
+    need = {"src_moments": K * V, "sigma_t": V, "phi": K * V}
+    tensors = {"src_moments": src_moments, "sigma_t": sigma_t, "phi": phi}
+    for name, t in tensors.items():
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < need[name]:
+            raise ValueError(f"{name} holds {t.numel()} elements, needs {need[name]}")
+    cur = torch.cuda.current_device()
+    for name, t in tensors.items():
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
     _check(lib().dts_sweep_once_noalloc(nx, ny, nz, dx, dy, dz, sn_order, legendre_order,
                                         C.c_void_p(src_moments.data_ptr()),
                                         C.c_void_p(sigma_t.data_ptr()), C.c_void_p(phi.data_ptr()),
