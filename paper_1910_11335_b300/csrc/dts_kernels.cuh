@@ -629,11 +629,13 @@ struct BatchShape {
     // float offsets
     // [SB][TSTR] the line being swept, refilled after phase A; with the Q input instead a ring of
     // QRING lines of the lanes' sources, [QRING][32][BX]
-    static constexpr int QRING = 3;
+    static constexpr int QRING = 2;
     static constexpr int oT = 0;
     static constexpr int oP = oT + (QIN ? QRING * 32 * BX : SB * TSTR);   // [SB][PSTR]
-    static constexpr int oX = oP + (PSI ? 0 : SB * PSTR);   // [fxn][32] x faces, slot = local line
-    static constexpr int oY = oX + fxn * 32;            // [BX][32] y faces of one z-layer, slot = lx
+    // [fxn][32] x faces, slot = local line (with the Q input the x-faces stay in registers and go
+    // to and from the face block line by line)
+    static constexpr int oX = oP + (PSI ? 0 : SB * PSTR);
+    static constexpr int oY = oX + (QIN ? 0 : fxn * 32);    // [BX][32] y faces of one z-layer, slot = lx
     static constexpr int oZ = oY + BX * 32;             // [fzn][32] z faces, slot = ly * BX + lx
     static constexpr int oS = oZ + fzn * 32;            // [NLINE][BX] sigma_t, local line, storage x
     static constexpr int nF = (oS + BV + 3) & ~3;
@@ -830,7 +832,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     const size_t lane_ofs = ((((size_t)(b0 + (srcok ? bl : 0)) * 8 + oct) * p.NT + tile) * NDO + d) * BV;
     float* psi_lane = p.part + lane_ofs;
     // Q input: the lane's per-direction source Q[b][oct][tile][d][cell] of a line (BX floats),
-    // copied two lines ahead into the lane's slot of a three-line ring
+    // copied one line ahead into the lane's slot of a two-line ring
     const float* q_lane = p.T + lane_ofs;
     auto stage_q = [&](int line) {
         if (!srcok) return;
@@ -880,14 +882,12 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     float* gx = p.xf + ((og * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * fxn) * 32;
     float* gy = p.yf + ((og * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * fyn) * 32;
     float* gz = p.zf + ((og * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * fzn) * 32;
-    batch_faces_in_async<fxn>(fx, gx, ta > 0);   // land with the first line's sources
+    if constexpr (!QIN) batch_faces_in_async<fxn>(fx, gx, ta > 0);   // land with the first line's sources
     batch_faces_in_async<BX>(fy, gy, tb > 0);    // z-layer 0; later layers stream in with the lines
     batch_faces_in_async<fzn>(fz, gz, tc > 0);
     cp_async_commit();
-    if constexpr (QIN) {
-        stage_q(1);
-        cp_async_commit();
-    }
+    float xn = 0.f, xsum = 0.f;   // Q input: the next line's incoming x-face; the outgoing ones' sum
+    if constexpr (QIN) xn = ta > 0 ? gx[lane] : 0.f;
 
     const int nvx = p.nx - tx * BX, nvy = p.ny - ty * BY, nvz = p.nz - tz * BZ;
     constexpr unsigned FULL = (1u << BX) - 1u;
@@ -897,10 +897,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 
 #pragma unroll 1
     for (int line = 0; line < S::NLINE; ++line) {
-        // this line's sources (copied during the previous line's walk; with the Q input two lines
-        // ago, the latest group -- the next line's -- may still be in flight)
-        if constexpr (QIN) cp_async_wait1();
-        else cp_async_wait0();
+        cp_async_wait0();   // this line's sources (copied during the previous line's walk)
         __syncwarp();
         const int ly = line % BY, lz = line / BY;
         const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
@@ -943,8 +940,8 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         if constexpr (!QIN) {
             if (line + 1 < S::NLINE) stage_line(line + 1, 0);
         } else {
-            if (line + 2 < S::NLINE) stage_q(line + 2);   // into the slot of the line before this one
-            cp_async_commit();                           // one group per line, empty at the end
+            if (line + 1 < S::NLINE) stage_q(line + 1);   // into the slot of the line before this one
+            cp_async_commit();
         }
 
         // B: walk the line
@@ -956,10 +953,21 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
             const unsigned vm = (sy < nvy && sz < nvz) ? vxs : 0u;
             float* zrow = fz + ly * BX * 32 + lane;
             const float* srow = sg + line * BX;
-            float xin = fx[line * 32 + lane];
+            float xin;
+            if constexpr (QIN) {
+                xin = xn;
+                if (line + 1 < S::NLINE) xn = ta > 0 ? gx[(line + 1) * 32 + lane] : 0.f;
+            } else {
+                xin = fx[line * 32 + lane];
+            }
             if (vm == FULL) batch_line<BX, NX, false>(qv, yv, zrow, srow, xin, vm, ax, ay, az, asum);
             else batch_line<BX, NX, true>(qv, yv, zrow, srow, xin, vm, ax, ay, az, asum);
-            fx[line * 32 + lane] = xin;
+            if constexpr (QIN) {
+                gx[line * 32 + lane] = xin;   // outgoing x-face, in place in the face block
+                xsum += xin;
+            } else {
+                fx[line * 32 + lane] = xin;
+            }
         }
         if (ly == BY - 1) {
 #pragma unroll
@@ -1015,7 +1023,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     }
 
     // outgoing faces; the lane's own faces leaving the grid are its leakage
-    batch_faces_out<fxn>(fx, gx);
+    if constexpr (!QIN) batch_faces_out<fxn>(fx, gx);
     batch_faces_out<fzn>(fz, gz);
     const bool lbx = NX ? tx == 0 : tx == p.NTx - 1;
     const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
@@ -1023,8 +1031,11 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     if (lbx || lby || lbz) {
         if (srcok) {
             float sx_ = 0.f, sy_ = 0.f, sz_ = 0.f;
-            if (lbx)
-                for (int e = 0; e < fxn; ++e) sx_ += fx[e * 32 + lane];
+            if (lbx) {
+                if constexpr (QIN) sx_ = xsum;
+                else
+                    for (int e = 0; e < fxn; ++e) sx_ += fx[e * 32 + lane];
+            }
             if (lby)
                 sy_ = ysum;
             if (lbz)
