@@ -68,7 +68,8 @@ struct dts_problem {
     int q_kind = 0;                   // 0 split BF16, 1 TF32
     int q_grid = 0;                   // persistent CTAs of k_moments_q
     void* Qbuf = nullptr;             // [B][8][NT][N_d/8][TV] FP32
-    float* Mop = nullptr;             // operator parts M' = 4 pi M, [parts][NP][16]
+    float* Mop = nullptr;             // operator parts M' = 4 pi M, [2][NP][16]
+    float* Dop = nullptr;             // Eq. 3 operator parts D, [2][16][N_d] (N_d a multiple of 16)
     int* dev_err = nullptr;           // device error word of the bounded waits
     int* h_err = nullptr;             // pinned copy, read after every iteration
     size_t rsz = 8;                   // sizeof(R)
@@ -533,7 +534,7 @@ QParams q_params(const dts_problem* p, int init)
     q.psi = (const float*)p->part; q.Q = (float*)p->Qbuf; q.phi00 = p->phi00;
     q.F = (const float*)p->F; q.Fstride = p->Fstride; q.ctl = p->ctl;
     q.sigs = (const float*)p->sigs; q.sigt = (const float*)p->sigt_r; q.mat_t = p->mat_t;
-    q.active = p->active; q.Dt = (const float*)p->Dt; q.Mop = p->Mop;
+    q.active = p->active; q.Dt = (const float*)p->Dt; q.Mop = p->Mop; q.Dop = p->Dop;
     q.vol = p->d.dx * p->d.dy * p->d.dz; q.blk = p->blk; q.err = p->dev_err;
     return q;
 }
@@ -1024,11 +1025,12 @@ float round_mantissa(double x, int drop)
     return f;
 }
 
-// Operand parts of the tensor-core contraction: M' = 4 pi M padded to [NP][16]
-// (N_d rounded up to a multiple of 16, K up to 16), stored as the parts
-// (hi, lo) with hi = r(M'), lo = r(M' - hi), r the rounding to bf16 (split
-// BF16) or to tf32 (split TF32).
-dts_status upload_qop(dts_problem* p, const std::vector<double>& Mnk)
+// Operand parts of the tensor-core contractions, stored as (hi, lo) with
+// hi = r(x), lo = r(x - hi): the source operator M' = 4 pi M padded to
+// [NP][16] (N_d rounded up to a multiple of 16, K up to 16; r the rounding to
+// bf16 for split BF16, to tf32 for split TF32), and, when N_d is a multiple of
+// 16, the Eq. 3 operator D padded to [16][N_d] (r the rounding to bf16).
+dts_status upload_qop(dts_problem* p, const std::vector<double>& Dkn, const std::vector<double>& Mnk)
 {
     const int nd = p->nd, K = p->K, NP = (nd + 15) / 16 * 16;
     const int drop = p->q_kind == 0 ? 16 : 13;
@@ -1042,6 +1044,18 @@ dts_status upload_qop(dts_problem* p, const std::vector<double>& Mnk)
         }
     TRY(dalloc_t(p, &p->Mop, op.size()));
     CK(cudaMemcpy(p->Mop, op.data(), op.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (nd % 16 == 0) {
+        std::vector<float> dop((size_t)2 * 16 * nd, 0.f);
+        for (int k = 0; k < K; ++k)
+            for (int n = 0; n < nd; ++n) {
+                const double v = Dkn[(size_t)k * nd + n];
+                const float hi = round_mantissa(v, 16);
+                dop[(size_t)k * nd + n] = hi;
+                dop[(size_t)16 * nd + (size_t)k * nd + n] = round_mantissa(v - (double)hi, 16);
+            }
+        TRY(dalloc_t(p, &p->Dop, dop.size()));
+        CK(cudaMemcpy(p->Dop, dop.data(), dop.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     return DTS_OK;
 }
 
@@ -1138,7 +1152,7 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     TRY(dalloc(p, &p->part, 8 * B * NC * (p->psi_mode ? (size_t)p->ndo : (size_t)K) * p->rsz));
     if (p->q_mode) {
         TRY(dalloc(p, &p->Qbuf, 8 * B * NC * (size_t)p->ndo * sizeof(float)));
-        TRY(upload_qop(p, M));
+        TRY(upload_qop(p, D, M));
         TRY(dalloc_t(p, &p->dev_err, 1));
         CK(cudaMemset(p->dev_err, 0, sizeof(int)));
         CK(cudaMallocHost((void**)&p->h_err, sizeof(int)));

@@ -175,8 +175,8 @@ __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat16 lo, __nv_bfloat16 
 // k_moments_q
 // --------------------------------------------------------------------------
 constexpr int kQCells = 128;     // cells of an 8 x 4 x 4 tile = rows of the MMA = TMEM lanes
-constexpr int kQThreads = 256;   // two threads per cell: octants 0-3 and 4-7, Q columns split alike
-constexpr int kQTmemCols = 128;  // >= the padded direction count (<= 80)
+constexpr int kQThreads = 128;   // one thread per cell; 4 warps reach the 128 TMEM lanes
+constexpr int kQTmemCols = 128;  // >= the padded direction count (<= 80) + 16 moment columns
 
 struct QParams {
     int B, NT, TV, NC;
@@ -194,6 +194,7 @@ struct QParams {
     const int* active;           // [B]
     const float* Dt;             // [N_d][K] moment operator
     const float* Mop;            // [2][NP][16] operator parts M' = hi + lo (bf16 or tf32 values)
+    const float* Dop;            // [2][16][N_d] Eq. 3 operator parts D = hi + lo (bf16 values), N_d % 16 == 0
     double vol;
     double* blk;                 // [B][NT][4] residual and balance partials per item
     int* err;                    // device error word (1: a bounded wait gave up)
@@ -202,33 +203,40 @@ struct QParams {
 template <int NDO, int K, int MODE>
 struct QShape {
     static constexpr int ND = 8 * NDO;
-    static constexpr int NP = (ND + 15) / 16 * 16;            // N of the MMA
+    static constexpr int NP = (ND + 15) / 16 * 16;            // N of the contraction to directions
     static constexpr int NCH = NP / 8;                        // 8-column TMEM chunks
-    static constexpr int KP = PsiPairs<K>::value;             // moment pairs of the Eq. 3 operator
+    // the Eq. 3 moments on the tensor cores too when the directions fill whole bf16 K steps (S6, S8):
+    // [128 cells x N_d] x [N_d x 16 moments], split-BF16 parts of the fluxes written in place of the
+    // consumed flux stage (the two parts take exactly its bytes)
+    static constexpr bool TC1 = ND % 16 == 0;
+    static constexpr int KP = PsiPairs<K>::value;             // moment pairs of the CUDA-core Eq. 3 operator
     static constexpr int PSI_STAGE = ND * kQCells * 4;        // bytes of one item's angular fluxes
-    static constexpr int XCH = 4 + 1 + 2 * KP;                // floats one upper-half thread hands over
     static constexpr int ROWB = MODE == 0 ? 32 : 64;          // bytes of one 16-moment operand row
     static constexpr int SBO = 8 * ROWB;                      // bytes between 8-row groups
     static constexpr int A_BYTES = kQCells * ROWB;            // one operand part of T
     static constexpr int B_BYTES = NP * ROWB;                 // one operand part of M'
-    // the hand-over goes through the consumed flux stage when it fits (N_d >= 48), else its own region
-    static constexpr bool XIN = XCH * kQCells * 4 <= PSI_STAGE;
+    static constexpr int SBO1 = ND / 8 * 128;                 // Eq. 3 operands: K = N_d bf16 per row
+    static constexpr int A1_BYTES = kQCells * ND * 2;         // one part of the fluxes (hi or lo)
+    static constexpr int B1_BYTES = 16 * ND * 2;              // one part of the Eq. 3 operator
     // byte offsets in dynamic shared memory
-    static constexpr int oPsi = 0;                            // [2][ND][128] float
-    static constexpr int oA = oPsi + 2 * PSI_STAGE;           // A parts (hi, lo)
-    static constexpr int oB = oA + 2 * A_BYTES;               // B parts (hi, lo)
-    static constexpr int oD = oB + 2 * B_BYTES;               // [ND][KP] moment pairs (8 B each)
-    static constexpr int oRed = oD + ND * KP * 8;             // [8 warps][4] double
-    static constexpr int oBar = oRed + 32 * 8;                // 3 mbarriers
+    static constexpr int oPsi = 0;                            // [ND][128] float: one item's fluxes
+    static constexpr int oA = oPsi + PSI_STAGE;               // A parts (hi, lo) of T
+    static constexpr int oB = oA + 2 * A_BYTES;               // B parts (hi, lo) of M'
+    static constexpr int oB1 = oB + 2 * B_BYTES;              // TC1: B parts (hi, lo) of D
+    static constexpr int oW = oB1 + (TC1 ? 2 * B1_BYTES : 0); // TC1: [ND] quadrature weights
+    static constexpr int oD = oW + (TC1 ? ND * 4 : 0);        // !TC1: [ND][KP] moment pairs (8 B each)
+    static constexpr int oRed = oD + (TC1 ? 0 : ND * KP * 8); // [4 warps][4] double
+    static constexpr int oBar = oRed + 16 * 8;                // 3 mbarriers
     static constexpr int oSlot = oBar + 3 * 8;                // TMEM address
-    static constexpr int oX = oSlot + 16;                     // [XCH][128] float unless XIN
-    static constexpr int bytes = oX + (XIN ? 0 : XCH * kQCells * 4);
+    static constexpr int bytes = oSlot + 16;
+    static_assert(!TC1 || 2 * A1_BYTES == PSI_STAGE, "the flux parts replace their stage");
+    static_assert(NP + 16 <= kQTmemCols, "the Eq. 3 accumulator sits after the direction columns");
 };
 
 template <int NDO, int K, int MODE>
 __host__ __device__ constexpr int moments_q_smem() { return QShape<NDO, K, MODE>::bytes; }
 
-// the byte offset of element (row, k) of a K-major operand part
+// the byte offset of element (row, k) of a K-major operand part with 16-moment rows of ROWB bytes
 template <int ROWB>
 __device__ __forceinline__ int op_offset(int row, int kbyte)
 {
@@ -253,37 +261,48 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
                  : "r"(taddr));
 }
 
+// (hi, lo) bf16 parts of the pair (a, b): hi = bf16(x), lo = bf16(x - hi)
+__device__ __forceinline__ void bf16_split2(float a, float b, uint32_t& hi, uint32_t& lo)
+{
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    hi = bf16x2_bits(ha, hb);
+    lo = bf16x2_bits(__float2bfloat16_rn(a - __bfloat162float(ha)), __float2bfloat16_rn(b - __bfloat162float(hb)));
+}
+
 // Persistent: each CTA walks the (source, tile) items blockIdx.x, +gridDim.x,
-// ... of active sources, with a two-stage ring of angular-flux tiles loaded by
-// bulk copies one item ahead. Thread t works on cell c = t % 128; half
-// h = t / 128 forms the Eq. 3 partial moments of octants 4h..4h+3 and stores
-// half of the item's Q columns; the lower half combines the partials, forms
-// T, the residual terms and the MMA operand.
+// ... of active sources; thread t works on cell t of the item's tile. The
+// item's angular fluxes arrive by bulk copies into one stage, whose next copy
+// is issued as soon as the stage is consumed (after the Eq. 3 contraction), so
+// it lands while the item's source is formed, contracted and stored; several
+// CTAs per SM overlap their items.
 template <int NDO, int K, int MODE>
-__global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
+__global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
 {
     using S = QShape<NDO, K, MODE>;
-    constexpr int ND = S::ND, NP = S::NP, KP = S::KP, ROWB = S::ROWB, XCH = S::XCH;
+    constexpr int ND = S::ND, NP = S::NP, KP = S::KP, ROWB = S::ROWB;
+    constexpr bool TC1 = S::TC1;
     extern __shared__ __align__(1024) unsigned char qsm[];
     float* spsi = reinterpret_cast<float*>(qsm + S::oPsi);
     unsigned char* sA = qsm + S::oA;
     unsigned char* sB = qsm + S::oB;
+    unsigned char* sB1 = qsm + S::oB1;
+    float* sw = reinterpret_cast<float*>(qsm + S::oW);
     unsigned long long* Dp = reinterpret_cast<unsigned long long*>(qsm + S::oD);
     double* red = reinterpret_cast<double*>(qsm + S::oRed);
-    uint64_t* full = reinterpret_cast<uint64_t*>(qsm + S::oBar);   // [0], [1]: psi stages
-    uint64_t* mbar = full + 2;                                     // MMA completion
+    uint64_t* full = reinterpret_cast<uint64_t*>(qsm + S::oBar);   // the flux stage has landed
+    uint64_t* mbar = full + 1;                                     // contraction to directions done
+    uint64_t* mbar1 = full + 2;                                    // Eq. 3 contraction done
     uint32_t* slot = reinterpret_cast<uint32_t*>(qsm + S::oSlot);
-    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    const int c = t & (kQCells - 1), h = t / kQCells;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31, c = t;
 
     if (t == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        mbar_init(full, 1);
         mbar_init(mbar, 1);
+        mbar_init(mbar1, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (w == 0) tmem_alloc(slot, kQTmemCols);
-    // B operand: the scaled operator parts, [n][k] K-major (values exactly representable)
+    // B operand of the contraction to directions: the scaled operator parts, [n][k] K-major
     for (int i = t; i < 2 * NP * 16; i += kQThreads) {
         const int part = i / (NP * 16), r = i - part * NP * 16, n = r >> 4, k = r & 15;
         const float v = p.Mop[i];
@@ -293,11 +312,21 @@ __global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
         else
             *reinterpret_cast<float*>(base + op_offset<ROWB>(n, 4 * k)) = v;
     }
-    if (!p.init) {   // moment pairs (D[n][2j], D[n][2j+1]) of the Eq. 3 operator
-        for (int i = t; i < ND * KP; i += kQThreads) {
-            const int n = i / KP, j = i - n * KP;
-            const float lo = 2 * j < K ? p.Dt[n * K + 2 * j] : 0.f, hi = 2 * j + 1 < K ? p.Dt[n * K + 2 * j + 1] : 0.f;
-            Dp[i] = f2pack(lo, hi);
+    if (!p.init) {
+        if constexpr (TC1) {
+            // B operand of the Eq. 3 contraction: D parts [k][n], K-major over the directions
+            for (int i = t; i < 2 * 16 * ND; i += kQThreads) {
+                const int part = i / (16 * ND), r = i - part * 16 * ND, k = r / ND, n = r - k * ND;
+                *reinterpret_cast<__nv_bfloat16*>(sB1 + part * S::B1_BYTES + (k >> 3) * S::SBO1 + (n >> 3) * 128 +
+                                                  (k & 7) * 16 + (n & 7) * 2) = __float2bfloat16_rn(p.Dop[i]);
+            }
+            for (int n = t; n < ND; n += kQThreads) sw[n] = p.Dt[n * K];   // D[0][n] = w_n
+        } else {   // moment pairs (D[n][2j], D[n][2j+1]) of the Eq. 3 operator
+            for (int i = t; i < ND * KP; i += kQThreads) {
+                const int n = i / KP, j = i - n * KP;
+                const float lo = 2 * j < K ? p.Dt[n * K + 2 * j] : 0.f, hi = 2 * j + 1 < K ? p.Dt[n * K + 2 * j + 1] : 0.f;
+                Dp[i] = f2pack(lo, hi);
+            }
         }
     }
     fence_async_smem();
@@ -305,6 +334,7 @@ __global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *slot;
+    const uint32_t lanes = tmem + ((uint32_t)(32 * w) << 16);   // this warp's TMEM lanes
 
     // the active items of this CTA, in order
     auto next_item = [&](int it) {
@@ -312,30 +342,28 @@ __global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
             if (p.active[it / p.NT]) return it;
         return p.nitems;
     };
-    auto issue = [&](int it, int stage) {   // one item's psi: 8 octant blocks of ND/8 x 128 floats
+    auto issue = [&](int it) {   // one item's psi: 8 octant blocks of ND/8 x 128 floats
         const int b = it / p.NT, tile = it - b * p.NT;
         constexpr uint32_t ob = NDO * kQCells * 4;
-        mbar_expect_tx(&full[stage], (uint32_t)S::PSI_STAGE);
+        mbar_expect_tx(full, (uint32_t)S::PSI_STAGE);
         for (int o = 0; o < 8; ++o)
-            bulk_load(reinterpret_cast<unsigned char*>(spsi) + stage * S::PSI_STAGE + o * ob,
-                      p.psi + (((size_t)b * 8 + o) * p.NT + tile) * (size_t)(NDO * kQCells), ob, &full[stage]);
+            bulk_load(reinterpret_cast<unsigned char*>(spsi) + o * ob,
+                      p.psi + (((size_t)b * 8 + o) * p.NT + tile) * (size_t)(NDO * kQCells), ob, full);
     };
 
     int it = next_item(blockIdx.x);
-    if (!p.init && t == 0 && it < p.nitems) issue(it, 0);
-    uint32_t phase_full[2] = {0u, 0u}, phase_mma = 0u;
+    if (!p.init && t == 0 && it < p.nitems) issue(it);
+    uint32_t phase_full = 0u, phase_mma = 0u, phase_mma1 = 0u;
     bool failed = false;
     constexpr float kInv4Pi = 0.0795774715459476679f;
     constexpr uint32_t idesc = mma_idesc(MODE == 0 ? 1u : 2u, kQCells, NP);
+    constexpr uint32_t idesc1 = mma_idesc(1u, kQCells, 16);
     constexpr int NLEG = K == 1 ? 1 : K == 4 ? 2 : K == 9 ? 3 : 4;
 
-    for (int n_done = 0; it < p.nitems; ++n_done) {
-        const int stage = n_done & 1;
+    while (it < p.nitems) {
         const int b = it / p.NT, tile = it - b * p.NT;
         const int nxt = next_item(it + gridDim.x);
-        if (!p.init && t == 0 && nxt < p.nitems) issue(nxt, stage ^ 1);   // its stage was read last item
         const int ct = tile * p.TV + c;
-        // the lower half's per-cell operands (loaded after the moment loop, which needs the registers)
         float f[K], sl[NLEG], stc = 0.f;
         int mat = -1;
         double old = 0.0;
@@ -354,135 +382,156 @@ __global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
         float T[K];
         RedTail tl;
         if (p.init) {
-            if (h == 0) {
-                load_cell();
+            load_cell();
 #pragma unroll
-                for (int k = 0; k < K; ++k) T[k] = f[k];
-            }
+            for (int k = 0; k < K; ++k) T[k] = f[k];
         } else {
             // the block agrees on the outcome, so that no thread leaves while others wait at a barrier
-            if (__syncthreads_or(!mbar_wait(&full[stage], phase_full[stage]))) {
+            if (__syncthreads_or(!mbar_wait(full, phase_full))) {
                 failed = true;
                 break;
             }
-            phase_full[stage] ^= 1u;
-            float* sp = spsi + stage * (S::PSI_STAGE / 4);
-            float os[4];   // moment 0 of each of this half's octants (FP32 sums of its directions)
-            float m1 = 0.f;
-            unsigned long long acc[KP];
+            phase_full ^= 1u;
+            float os[8];   // moment 0 of each octant (FP32 sums of its directions)
+            float mk[16];  // the cell's moments 1..K-1
+            if constexpr (TC1) {
+                uint32_t hw[ND / 2], lw[ND / 2];
 #pragma unroll
-            for (int j = 0; j < KP; ++j) acc[j] = 0ull;
+                for (int o = 0; o < 8; ++o) {
+                    float v[NDO];
+#pragma unroll
+                    for (int d = 0; d < NDO; ++d) v[d] = spsi[(o * NDO + d) * kQCells + c];
+                    float s = 0.f;
+#pragma unroll
+                    for (int d = 0; d < NDO; ++d) s = fmaf(sw[o * NDO + d], v[d], s);
+                    os[o] = s;
+#pragma unroll
+                    for (int j = 0; j < NDO / 2; ++j)
+                        bf16_split2(v[2 * j], v[2 * j + 1], hw[o * (NDO / 2) + j], lw[o * (NDO / 2) + j]);
+                }
+                __syncthreads();   // the stage is read: its bytes become the fluxes' operand parts
+                unsigned char* a1 = reinterpret_cast<unsigned char*>(spsi);
+#pragma unroll
+                for (int q = 0; q < ND / 8; ++q) {
+                    const int ofs = (c >> 3) * S::SBO1 + q * 128 + (c & 7) * 16;
+                    *reinterpret_cast<uint4*>(a1 + ofs) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                    *reinterpret_cast<uint4*>(a1 + S::A1_BYTES + ofs) =
+                        make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                if (t == 0) {
+                    tc_fence_after();
+                    const unsigned char* As[3] = {a1, a1, a1 + S::A1_BYTES};
+                    const unsigned char* Bs[3] = {sB1, sB1 + S::B1_BYTES, sB1};
+#pragma unroll
+                    for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+                        for (int ks = 0; ks < ND / 16; ++ks)
+                            mma_issue<0>(tmem + NP, smem_desc(As[pr] + ks * 256, 128, S::SBO1),
+                                         smem_desc(Bs[pr] + ks * 256, 128, S::SBO1), idesc1,
+                                         (pr | ks) ? 1u : 0u);
+                    mma_commit(mbar1);
+                }
+                load_cell();
+                if (__syncthreads_or(!mbar_wait(mbar1, phase_mma1))) {
+                    failed = true;
+                    break;
+                }
+                phase_mma1 ^= 1u;
+                tc_fence_after();
+                if (t == 0 && nxt < p.nitems) issue(nxt);   // the stage's operand parts are consumed
+                uint32_t r[16];
+                tmem_ld16(lanes + (uint32_t)NP, r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) mk[k] = __uint_as_float(r[k]);
+            } else {
+                float m1 = 0.f;
+                unsigned long long acc[KP];
+#pragma unroll
+                for (int j = 0; j < KP; ++j) acc[j] = 0ull;
 #pragma unroll 1
-            for (int oo = 0; oo < 4; ++oo) {
-                const int o = 4 * h + oo;
-                unsigned long long f0 = 0ull;   // moments (0, 1) of this octant
-#pragma unroll 2
-                for (int d = 0; d < NDO; ++d) {
-                    const float v = sp[(o * NDO + d) * kQCells + c];
-                    const unsigned long long a = f2pack(v, v);
-                    const ulonglong2* dq = reinterpret_cast<const ulonglong2*>(Dp + (o * NDO + d) * KP);
+                for (int o = 0; o < 8; ++o) {
+                    unsigned long long f0 = 0ull;   // moments (0, 1) of this octant
 #pragma unroll
-                    for (int j = 0; j < KP / 2; ++j) {
-                        const ulonglong2 dd = dq[j];
-                        if (j == 0) f0 = ffma2(dd.x, a, f0);
-                        else acc[2 * j] = ffma2(dd.x, a, acc[2 * j]);
-                        acc[2 * j + 1] = ffma2(dd.y, a, acc[2 * j + 1]);
-                    }
-                }
-                float hi;
-                f2unpack(f0, os[oo], hi);
-                m1 += hi;
-            }
-            __syncthreads();   // the flux stage is consumed: the upper half hands over through it
-            float* xch = (S::XIN ? sp : reinterpret_cast<float*>(qsm + S::oX)) + c;   // [XCH][128]
-            if (h == 1) {
+                    for (int d = 0; d < NDO; ++d) {
+                        const float v = spsi[(o * NDO + d) * kQCells + c];
+                        const unsigned long long a = f2pack(v, v);
+                        const ulonglong2* dq = reinterpret_cast<const ulonglong2*>(Dp + (o * NDO + d) * KP);
 #pragma unroll
-                for (int oo = 0; oo < 4; ++oo) xch[oo * kQCells] = os[oo];
-                xch[4 * kQCells] = m1;
-#pragma unroll
-                for (int j = 0; j < KP; ++j) {
-                    float lo, hi;
-                    f2unpack(acc[j], lo, hi);
-                    xch[(5 + 2 * j) * kQCells] = lo;
-                    xch[(6 + 2 * j) * kQCells] = hi;
-                }
-            }
-            if (h == 0) load_cell();
-            __syncthreads();
-            if (h == 0) {
-                TwoSum s0;   // the scalar flux: the eight octant sums added exactly, in octant order
-#pragma unroll
-                for (int oo = 0; oo < 4; ++oo) s0.add(os[oo]);
-#pragma unroll
-                for (int oo = 0; oo < 4; ++oo) s0.add(xch[oo * kQCells]);
-                m1 += xch[4 * kQCells];
-#pragma unroll
-                for (int j = 0; j < KP; ++j)
-                    acc[j] = fadd2(acc[j], f2pack(xch[(5 + 2 * j) * kQCells], xch[(6 + 2 * j) * kQCells]));
-                if (mat < 0) {
-                    *ph = 0.0;
-#pragma unroll
-                    for (int k = 0; k < K; ++k) T[k] = 0.f;
-                } else {
-                    const double phi = s0.value();
-                    T[0] = tl.cell(s0, phi, old, f[0], sl[0], stc);
-                    *ph = phi;
-#pragma unroll
-                    for (int k = 1; k < K; ++k) {
-                        float mk;
-                        if (k == 1) {
-                            mk = m1;
-                        } else {
-                            float lo, hi;
-                            f2unpack(acc[k / 2], lo, hi);
-                            mk = (k & 1) ? hi : lo;
+                        for (int j = 0; j < KP / 2; ++j) {
+                            const ulonglong2 dd = dq[j];
+                            if (j == 0) f0 = ffma2(dd.x, a, f0);
+                            else acc[2 * j] = ffma2(dd.x, a, acc[2 * j]);
+                            acc[2 * j + 1] = ffma2(dd.y, a, acc[2 * j + 1]);
                         }
-                        T[k] = fmaf(sl[l_of_k(k)], mk, f[k]);
                     }
+                    float hi;
+                    f2unpack(f0, os[o], hi);
+                    m1 += hi;
                 }
+                __syncthreads();   // the stage is read
+                if (t == 0 && nxt < p.nitems) issue(nxt);
+                load_cell();
+                mk[1] = m1;
+#pragma unroll
+                for (int k = 2; k < 16; ++k) {
+                    if (k >= K) break;
+                    float lo, hi;
+                    f2unpack(acc[k / 2], lo, hi);
+                    mk[k] = (k & 1) ? hi : lo;
+                }
+            }
+            TwoSum s0;   // the scalar flux: the eight FP32 octant sums added exactly, in octant order
+#pragma unroll
+            for (int o = 0; o < 8; ++o) s0.add(os[o]);
+            if (mat < 0) {
+                *ph = 0.0;
+#pragma unroll
+                for (int k = 0; k < K; ++k) T[k] = 0.f;
+            } else {
+                const double phi = s0.value();
+                T[0] = tl.cell(s0, phi, old, f[0], sl[0], stc);
+                *ph = phi;
+#pragma unroll
+                for (int k = 1; k < K; ++k) T[k] = fmaf(sl[l_of_k(k)], mk[k], f[k]);
             }
         }
         // A operand row c: T' = T / (4 pi), padded to 16 moments, as (hi, lo) parts
-        if (h == 0) {
-            if constexpr (MODE == 0) {
-                uint32_t hw[8], lw[8];
+        if constexpr (MODE == 0) {
+            uint32_t hw[8], lw[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float a0 = 2 * j < K ? T[2 * j] * kInv4Pi : 0.f;
-                    const float a1 = 2 * j + 1 < K ? T[2 * j + 1] * kInv4Pi : 0.f;
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(a0 - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 = __float2bfloat16_rn(a1 - __bfloat162float(h1));
-                    hw[j] = bf16x2_bits(h0, h1);
-                    lw[j] = bf16x2_bits(l0, l1);
-                }
+            for (int j = 0; j < 8; ++j)
+                bf16_split2(2 * j < K ? T[2 * j] * kInv4Pi : 0.f, 2 * j + 1 < K ? T[2 * j + 1] * kInv4Pi : 0.f,
+                            hw[j], lw[j]);
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    *reinterpret_cast<uint4*>(sA + op_offset<ROWB>(c, 16 * q)) =
-                        make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-                    *reinterpret_cast<uint4*>(sA + S::A_BYTES + op_offset<ROWB>(c, 16 * q)) =
-                        make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
-                }
-            } else {
-                uint32_t hv[16], lv[16];
+            for (int q = 0; q < 2; ++q) {
+                *reinterpret_cast<uint4*>(sA + op_offset<ROWB>(c, 16 * q)) =
+                    make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                *reinterpret_cast<uint4*>(sA + S::A_BYTES + op_offset<ROWB>(c, 16 * q)) =
+                    make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+            }
+        } else {
+            uint32_t hv[16], lv[16];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float a = k < K ? T[k] * kInv4Pi : 0.f;
-                    hv[k] = tf32_rn(a);
-                    lv[k] = tf32_rn(a - __uint_as_float(hv[k]));
-                }
+            for (int k = 0; k < 16; ++k) {
+                const float a = k < K ? T[k] * kInv4Pi : 0.f;
+                hv[k] = tf32_rn(a);
+                lv[k] = tf32_rn(a - __uint_as_float(hv[k]));
+            }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    *reinterpret_cast<uint4*>(sA + op_offset<ROWB>(c, 16 * q)) =
-                        make_uint4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
-                    *reinterpret_cast<uint4*>(sA + S::A_BYTES + op_offset<ROWB>(c, 16 * q)) =
-                        make_uint4(lv[4 * q], lv[4 * q + 1], lv[4 * q + 2], lv[4 * q + 3]);
-                }
+            for (int q = 0; q < 4; ++q) {
+                *reinterpret_cast<uint4*>(sA + op_offset<ROWB>(c, 16 * q)) =
+                    make_uint4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+                *reinterpret_cast<uint4*>(sA + S::A_BYTES + op_offset<ROWB>(c, 16 * q)) =
+                    make_uint4(lv[4 * q], lv[4 * q + 1], lv[4 * q + 2], lv[4 * q + 3]);
             }
         }
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();   // A complete; the last item's TMEM reads are done
+        __syncthreads();   // A complete; this item's and the last item's TMEM reads are done
         if (t == 0) {
             tc_fence_after();
             // products hi.hi, hi.lo, lo.hi; bf16 takes K = 16 per instruction, tf32 K = 8 (two
@@ -499,7 +548,7 @@ __global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
                                     (pr | ks) ? 1u : 0u);
             mma_commit(mbar);
         }
-        // residual and balance partials of the item while the MMA runs (the upper half adds zeros)
+        // residual and balance partials of the item while the MMA runs
         if (!p.init) {
             float v[4] = {tl.ds, tl.ns, tl.sr, tl.ab};
 #pragma unroll
@@ -518,13 +567,10 @@ __global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
         phase_mma ^= 1u;
         tc_fence_after();
         {
-            // half h stores the 8-column chunks [h C0, ...): column n = o NDO + d of cell c goes to
-            // Q[b][o][tile][d][c]; the chunk ranges are compile-time so that n, o, d are constants
-            constexpr int C0 = (S::NCH + 1) / 2;
+            // column n = o NDO + d of cell c goes to Q[b][o][tile][d][c]
             float* qb = p.Q + ((size_t)b * 8 * p.NT + tile) * (size_t)(NDO * p.TV) + c;
             const size_t ostr = (size_t)p.NT * (NDO * p.TV);
-            const uint32_t lanes = tmem + ((uint32_t)(32 * (w & 3)) << 16);
-            auto store_chunk = [&](auto chv) {
+            static_for<0, S::NCH>([&](auto chv) {
                 constexpr int ch = decltype(chv)::value;
                 uint32_t r[8];
                 tmem_ld8(lanes + (uint32_t)(8 * ch), r);
@@ -535,9 +581,7 @@ __global__ void __launch_bounds__(kQThreads, 2) k_moments_q(const QParams p)
                     const int n = nb + i;
                     if (n < ND) qb[(size_t)(n / NDO) * ostr + (n % NDO) * p.TV] = __uint_as_float(r[i]);
                 }
-            };
-            if (h == 0) static_for<0, C0>(store_chunk);
-            else static_for<C0, S::NCH>(store_chunk);
+            });
         }
         if (!p.init && t < 4) {
             double a = 0.0;
