@@ -272,6 +272,14 @@ const char *dts_status_string(dts_status s);
 /* ABI version, incremented on incompatible changes. */
 int dts_version(void);
 
+/* Test hook for the out-of-memory path (host-side fault injection; the paper
+ * has no counterpart): the device allocation that follows `after` further
+ * successful ones in this process fails once as if the device were full, so
+ * the call making it returns DTS_ERR_OOM with "injected" in its message and
+ * releases everything it had allocated (dts_create_problem leaves *out NULL).
+ * after < 0 disarms the hook. No device work. */
+void dts_debug_fail_allocation(int after);
+
 /*
  * Host-side helpers (no device work; usable without a GPU).
  * dts_quadrature: the level-symmetric set the solver uses (Sec. II.E), with
@@ -321,14 +329,19 @@ long long dts_subsweep_size(int nx, int ny, int nz, int S);
  *   src_moments [K][V] device, T_k per voxel (x fastest)
  *   sigma_t     [V]    device, total cross section per voxel, > 0
  *   phi         [K][V] device output
- *   cuda_stream        stream to enqueue on (NULL = legacy default stream);
- *                      the call returns without waiting, phi is ready when
- *                      the stream reaches it
- * The first call on a device looks up the device address of the scratch
- * array (with that device current); make that first call before any stream
- * capture. All calls share the array: calls whose work overlaps on the GPU
- * (different streams, or devices sharing nothing but the same process are
- * fine only if their streams are ordered) race and give wrong results.
+ *   cuda_stream        stream to enqueue on (NULL = legacy default stream)
+ * Timing: the first call on a device looks up the device address of the
+ * scratch array (with that device current); make that first call before any
+ * stream capture. The schedule and direction tables of a call's shape (grid,
+ * pitch, S_N and Legendre order) are kept at the start of the array: a call
+ * whose shape differs from the previous call's on that device first waits
+ * until the device is idle and then copies its tables from host memory
+ * (blocking); a call repeating the shape copies nothing, enqueues its kernels
+ * on cuda_stream and returns without waiting -- phi is ready when the stream
+ * reaches it.
+ * Sharing: calls on one device share its array, so two calls on one device
+ * whose work is not ordered on one stream race and give wrong results; calls
+ * on different devices use different arrays and never race.
  * Errors: DTS_ERR_INVALID_ARG for bad sizes or when the grid needs more
  * scratch than DTS_NOALLOC_SCRATCH_BYTES (about 1.2 KB per voxel at L = 3,
  * 80 bytes at L = 0; message in dts_last_error(NULL)); DTS_ERR_CUDA.

@@ -138,7 +138,7 @@ struct SweepParams {
     R* yf;
     R* zf;
     const int* active;             // [B]
-    double* leak;                  // [B]
+    double* leak;                  // [B][8][NT] leakage of each (source, octant, tile) sweep, or null
 };
 
 template <typename R, int NDO, int K>
@@ -287,8 +287,9 @@ k_sweep_stage(const SweepParams<R> p, const int stage)
     for (int i = tid; i < NDO * fxn; i += nth) gx[i] = fx[i];
     for (int i = tid; i < NDO * fyn; i += nth) gy[i] = fy[i];
     for (int i = tid; i < NDO * fzn; i += nth) gz[i] = fz[i];
+    // every (source, octant, tile) of a sweep owns one slot: a fixed-order sum per source later
     leak = block_sum(leak, red);
-    if (tid == 0 && leak != 0.0) atomicAdd(&p.leak[b], leak);
+    if (tid == 0 && p.leak) p.leak[((size_t)b * 8 + oct) * p.NT + tile] = leak;
 }
 
 // ---------------------------------------------------------------------------
@@ -548,10 +549,8 @@ k_sweep_lines(const SweepParams<R> p, const int stage)
         gz[i] = fz[i];
         if (lbz) leak += Lw[(i / fzn) * 3 + 2] * (double)fz[i];
     }
-    if (lbx || lby || lbz) {
-        leak = block_sum(leak, red);
-        if (tid == 0 && leak != 0.0) atomicAdd(&p.leak[b], leak);
-    }
+    if (lbx || lby || lbz) leak = block_sum(leak, red);
+    if (tid == 0 && p.leak) p.leak[((size_t)b * 8 + oct) * p.NT + tile] = (lbx || lby || lbz) ? leak : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -639,7 +638,7 @@ struct BatchShape {
     static constexpr int oZ = oY + BX * 32;             // [fzn][32] z faces, slot = ly * BX + lx
     static constexpr int oS = oZ + fzn * 32;            // [NLINE][BX] sigma_t, local line, storage x
     static constexpr int nF = (oS + BV + 3) & ~3;
-    static constexpr size_t bytes = sizeof(float) * nF + sizeof(double) * SB;
+    static constexpr size_t bytes = sizeof(float) * nF;
 };
 
 template <int NDO, int K, int BX, bool PSI, bool QIN = false>
@@ -766,7 +765,6 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     float* fy = smf + S::oY;
     float* fz = smf + S::oZ;
     float* sg = smf + S::oS;
-    double* leak_sh = reinterpret_cast<double*>(smf + S::nF);
 
     const int lane = threadIdx.x;
     const int b0 = grp * SB, nb = min(SB, p.B - b0);
@@ -868,7 +866,6 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         for (int j = 0; j < NJ; ++j) citem(j, cp_[j], co_[j]);
     }
 
-    if (lane < SB) leak_sh[lane] = 0.0;
     {
         const float* st = p.sigt + (size_t)tile * BV;
         for (int i = lane; i < BV / 4; i += 32) {
@@ -1028,25 +1025,26 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     const bool lbx = NX ? tx == 0 : tx == p.NTx - 1;
     const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
     const bool lbz = negz ? tz == 0 : tz == p.NTz - 1;
-    if (lbx || lby || lbz) {
-        if (srcok) {
-            float sx_ = 0.f, sy_ = 0.f, sz_ = 0.f;
-            if (lbx) {
-                if constexpr (QIN) sx_ = xsum;
-                else
-                    for (int e = 0; e < fxn; ++e) sx_ += fx[e * 32 + lane];
-            }
-            if (lby)
-                sy_ = ysum;
-            if (lbz)
-                for (int e = 0; e < fzn; ++e) sz_ += fz[e * 32 + lane];
-            const double lk = p.Lw[(n0 + d) * 3] * (double)sx_ + p.Lw[(n0 + d) * 3 + 1] * (double)sy_ +
-                              p.Lw[(n0 + d) * 3 + 2] * (double)sz_;
-            if (lk != 0.0) atomicAdd(&leak_sh[bl], lk);
+    double lk = 0.0;
+    if ((lbx || lby || lbz) && srcok) {
+        float sx_ = 0.f, sy_ = 0.f, sz_ = 0.f;
+        if (lbx) {
+            if constexpr (QIN) sx_ = xsum;
+            else
+                for (int e = 0; e < fxn; ++e) sx_ += fx[e * 32 + lane];
         }
-        __syncwarp();
-        if (lane < nb && (okmask >> lane & 1u) && leak_sh[lane] != 0.0) atomicAdd(&p.leak[b0 + lane], leak_sh[lane]);
+        if (lby) sy_ = ysum;
+        if (lbz)
+            for (int e = 0; e < fzn; ++e) sz_ += fz[e * 32 + lane];
+        lk = p.Lw[(n0 + d) * 3] * (double)sx_ + p.Lw[(n0 + d) * 3 + 1] * (double)sy_ +
+             p.Lw[(n0 + d) * 3 + 2] * (double)sz_;
     }
+    // the source's leakage from this (octant, tile): its direction lanes summed in direction order
+    // into its slot (zero off the boundary), so that the per-source total is reproducible
+    double tot = 0.0;
+#pragma unroll
+    for (int dd = 0; dd < NDO; ++dd) tot += __shfl_sync(0xffffffffu, lk, (srcok ? bl : 0) * NDO + dd);
+    if (srcok && d == 0 && p.leak) p.leak[((size_t)(b0 + bl) * 8 + oct) * p.NT + tile] = tot;
 }
 
 // s0, cnt: the stage's first entry in stage_tiles and its tile count (kernel
@@ -1454,13 +1452,14 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_psi(const RedParams<f
     red_tail_store(p, tl, red, b, blockIdx.x, gridDim.x);
 }
 
-// per source: residual = sqrt(sum dphi^2 / sum phi^2), balance terms, leakage
-// (then cleared for the next sweep); fixed summation order
-__global__ void k_resid_final(const double* blk, int nblk, double* leak, double* status)
+// per source: residual = sqrt(sum dphi^2 / sum phi^2), balance terms and the
+// leakage of the last sweep from its nleak (octant, tile) slots; fixed
+// summation order, so the results do not depend on the order the CTAs ran in
+__global__ void k_resid_final(const double* blk, int nblk, const double* leak, int nleak, double* status)
 {
     __shared__ double red[32];
     const int b = blockIdx.x;
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
         const double* o = blk + ((size_t)b * nblk + i) * 4;
         a[0] += o[0];
@@ -1468,14 +1467,14 @@ __global__ void k_resid_final(const double* blk, int nblk, double* leak, double*
         a[2] += o[2];
         a[3] += o[3];
     }
-    for (int j = 0; j < 4; ++j) a[j] = block_sum(a[j], red);
+    for (int i = threadIdx.x; i < nleak; i += blockDim.x) a[4] += leak[(size_t)b * nleak + i];
+    for (int j = 0; j < 5; ++j) a[j] = block_sum(a[j], red);
     if (threadIdx.x == 0) {
         double* s = status + (size_t)b * 4;
         s[0] = a[1] > 0.0 ? sqrt(a[0] / a[1]) : 0.0;
         s[1] = a[2];
         s[2] = a[3];
-        s[3] = leak[b];
-        leak[b] = 0.0;
+        s[3] = a[4];
     }
 }
 

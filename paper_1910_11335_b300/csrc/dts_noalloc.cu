@@ -36,6 +36,19 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mu;
 void* g_scratch_ptr[256] = {};   // device address of g_scratch, per device ordinal
 
+// the shape whose tables (schedule, direction operators) sit at the start of a
+// device's scratch array; a call with the same shape reuses them
+struct Shape {
+    int nx = 0, ny = 0, nz = 0, sn = 0, L = -1;
+    double dx = 0, dy = 0, dz = 0;
+    bool operator==(const Shape& o) const
+    {
+        return nx == o.nx && ny == o.ny && nz == o.nz && sn == o.sn && L == o.L && dx == o.dx && dy == o.dy &&
+               dz == o.dz;
+    }
+};
+Shape g_tables[256];
+
 dts_status err(dts_status s, const std::string& m)
 {
     dts_internal_set_thread_error(m.c_str());
@@ -162,7 +175,6 @@ extern "C" dts_status dts_sweep_once_noalloc(int nx, int ny, int nz, double dx, 
     plan.take<double>(nul, 8 * fy);
     plan.take<double>(nul, 8 * fz);
     plan.take<int>(nul, 1);
-    plan.take<double>(nul, 1);
     if (plan.off > kScratchBytes) {
         char m[256];
         snprintf(m, sizeof m,
@@ -172,14 +184,19 @@ extern "C" dts_status dts_sweep_once_noalloc(int nx, int ny, int nz, double dx, 
         return err(DTS_ERR_INVALID_ARG, m);
     }
 
-    // once per device: the device address of the scratch array
+    // once per device: the device address of the scratch array; per device the shape of the tables
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return err(DTS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= 256) return err(DTS_ERR_INVALID_ARG, "dts_sweep_once_noalloc: device ordinal >= 256");
     unsigned char* base;
+    Shape shape;
+    shape.nx = nx; shape.ny = ny; shape.nz = nz; shape.sn = sn_order; shape.L = legendre_order;
+    shape.dx = dx; shape.dy = dy; shape.dz = dz;
+    bool upload;
     {
         std::lock_guard<std::mutex> lk(g_mu);
+        upload = !(g_tables[dev] == shape);
         if (!g_scratch_ptr[dev]) {
             void* ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_scratch);
@@ -242,11 +259,10 @@ extern "C" dts_status dts_sweep_once_noalloc(int nx, int ny, int nz, double dx, 
     double* d_yf = cv.take<double>(base, 8 * fy);
     double* d_zf = cv.take<double>(base, 8 * fz);
     int* d_active = cv.take<int>(base, 1);
-    double* d_leak = cv.take<double>(base, 1);
     sp.stage_tiles = d_tiles; sp.stage_off = d_soff; sp.diag_cells = d_cells; sp.diag_off = d_doff;
     sp.M = d_M; sp.Dt = d_Dt; sp.A = d_A; sp.Lw = d_Lw;
     sp.T = d_T; sp.sigt = d_st; sp.part = d_part; sp.xf = d_xf; sp.yf = d_yf; sp.zf = d_zf;
-    sp.active = d_active; sp.leak = d_leak;
+    sp.active = d_active; sp.leak = nullptr;   // no leakage tally: the call returns moments only
 
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 #define CKN(call)                                                                              \
@@ -256,16 +272,21 @@ extern "C" dts_status dts_sweep_once_noalloc(int nx, int ny, int nz, double dx, 
             return err(DTS_ERR_CUDA, std::string("dts_sweep_once_noalloc: " #call ": ") +      \
                                          cudaGetErrorString(e_));                              \
     } while (0)
-    CKN(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(unsigned) * NT, cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_soff, soff.data(), sizeof(int) * (n_stages + 1), cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_cells, cells.data(), sizeof(unsigned) * TV, cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_doff, doff.data(), sizeof(int) * (nsub + 1), cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_M, M.data(), sizeof(double) * nd * K, cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_Dt, Dt.data(), sizeof(double) * nd * K, cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_A, A.data(), sizeof(double) * nd * 3, cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_Lw, Lw.data(), sizeof(double) * nd * 3, cudaMemcpyHostToDevice, st));
-    // the leakage word is accumulated by the sweep; clear it so every call starts at zero
-    CKN(cudaMemsetAsync(d_leak, 0, sizeof(double), st));
+    if (upload) {
+        // a new shape on this device: wait until no earlier call's work can still read the old
+        // tables, then copy the new ones (blocking copies from host memory)
+        CKN(cudaDeviceSynchronize());
+        CKN(cudaMemcpy(d_tiles, tiles.data(), sizeof(unsigned) * NT, cudaMemcpyHostToDevice));
+        CKN(cudaMemcpy(d_soff, soff.data(), sizeof(int) * (n_stages + 1), cudaMemcpyHostToDevice));
+        CKN(cudaMemcpy(d_cells, cells.data(), sizeof(unsigned) * TV, cudaMemcpyHostToDevice));
+        CKN(cudaMemcpy(d_doff, doff.data(), sizeof(int) * (nsub + 1), cudaMemcpyHostToDevice));
+        CKN(cudaMemcpy(d_M, M.data(), sizeof(double) * nd * K, cudaMemcpyHostToDevice));
+        CKN(cudaMemcpy(d_Dt, Dt.data(), sizeof(double) * nd * K, cudaMemcpyHostToDevice));
+        CKN(cudaMemcpy(d_A, A.data(), sizeof(double) * nd * 3, cudaMemcpyHostToDevice));
+        CKN(cudaMemcpy(d_Lw, Lw.data(), sizeof(double) * nd * 3, cudaMemcpyHostToDevice));
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_tables[dev] = shape;
+    }
     k_to_tiled<<<(NC + 255) / 256, 256, 0, st>>>(nx, ny, nz, NTx, NTy, K, NC, src_moments, sigma_t,
                                                  d_T, d_st, d_active);
     CKN(cudaGetLastError());

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -156,10 +157,25 @@ dts_status fail(dts_problem* p, dts_status s, const std::string& msg)
         if (s_ != DTS_OK) return s_;       \
     } while (0)
 
+// host-side fault injection (dts_debug_fail_allocation): successful device allocations still to
+// pass before one fails as out-of-memory; negative = disarmed
+std::atomic<long long> g_fail_alloc_after{-1};
+
 dts_status dalloc(dts_problem* p, void** ptr, size_t bytes)
 {
     *ptr = nullptr;
     if (bytes == 0) bytes = 16;
+    for (long long n = g_fail_alloc_after.load(); n >= 0;) {
+        if (g_fail_alloc_after.compare_exchange_weak(n, n - 1)) {
+            if (n == 0) {
+                char buf[160];
+                snprintf(buf, sizeof buf, "cudaMalloc(%zu bytes): injected allocation failure "
+                                          "(dts_debug_fail_allocation)", bytes);
+                return fail(p, DTS_ERR_OOM, buf);
+            }
+            break;
+        }
+    }
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
@@ -611,7 +627,7 @@ dts_status record_reduce(dts_problem* p)
     } else {
         reduce_fn<R>(p->K)<<<dim3(nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
     }
-    k_resid_final<<<p->B, 256, 0, p->stream>>>(p->blk, nblk, p->leak, p->status);
+    k_resid_final<<<p->B, 256, 0, p->stream>>>(p->blk, nblk, p->leak, 8 * p->NT, p->status);
     p->graph_launches = p->n_stages + 2;
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(double) * 4 * p->B, cudaMemcpyDeviceToHost,
                        p->stream));
@@ -1181,13 +1197,13 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
     if (d.keep_moments) TRY(dalloc_t(p, &p->mom, B * G * K * V));
     TRY(dalloc_t(p, &p->src, B * 8));
     TRY(dalloc_t(p, &p->spec, B * G));
-    TRY(dalloc_t(p, &p->leak, B));
+    TRY(dalloc_t(p, &p->leak, B * 8 * p->NT));   // one slot per (source, octant, tile)
     p->nblk = (p->NC + kRedThreads - 1) / kRedThreads;
     TRY(dalloc_t(p, &p->blk, B * std::max(p->nblk, p->NT) * 4));   // k_moments_q: one partial per tile
     TRY(dalloc_t(p, &p->status, B * 4));
     TRY(dalloc_t(p, &p->active, B));
     TRY(dalloc_t(p, &p->ctl, 4));
-    CK(cudaMemset(p->leak, 0, sizeof(double) * B));
+    CK(cudaMemset(p->leak, 0, sizeof(double) * B * 8 * p->NT));
     CK(cudaMemset(p->col, 0, sizeof(double) * B * G * V));
     CK(cudaMallocHost((void**)&p->h_status, sizeof(double) * 4 * B));
     CK(cudaMallocHost((void**)&p->h_active, sizeof(int) * B));
@@ -1405,7 +1421,7 @@ dts_status run_adjoint(dts_problem* p, int b)
                 adj<<<(unsigned)cnt * 8u, kSweepThreads, smem, p->stream>>>(sp, s);
             }
             rf<<<dim3(p->nblk, 1), kRedThreads, 0, p->stream>>>(rp);
-            k_resid_final<<<1, 256, 0, p->stream>>>(p->adj_blk, p->nblk, p->adj_leak, p->adj_status);
+            k_resid_final<<<1, 256, 0, p->stream>>>(p->adj_blk, p->nblk, p->adj_leak, 1, p->adj_status);
             CK(cudaMemcpyAsync(p->h_status, p->adj_status, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                p->stream));
             CK(cudaStreamSynchronize(p->stream));
@@ -1864,6 +1880,8 @@ const char* dts_status_string(dts_status s)
 }
 
 int dts_version(void) { return 1; }
+
+void dts_debug_fail_allocation(int after) { g_fail_alloc_after.store(after < 0 ? -1 : (long long)after); }
 
 dts_status dts_quadrature(int sn_order, double* mu, double* eta, double* xi, double* w, int* n_dirs)
 {

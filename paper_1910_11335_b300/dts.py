@@ -68,7 +68,7 @@ EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_sol
            "dts_get_balance", "dts_last_error", "dts_destroy_problem", "dts_status_string",
            "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size",
            "dts_sweep_once_noalloc", "dts_solve_adjoint", "dts_get_adjoint_iterations",
-           "dts_tune_tile", "dts_set_source_cones", "dts_get_dose")
+           "dts_tune_tile", "dts_set_source_cones", "dts_get_dose", "dts_debug_fail_allocation")
 
 
 def lib():
@@ -97,6 +97,7 @@ def lib():
         "dts_destroy_problem": ([C.c_void_p], None),
         "dts_status_string": ([C.c_int], C.c_char_p),
         "dts_version": ([], C.c_int),
+        "dts_debug_fail_allocation": ([C.c_int], None),
         "dts_quadrature": ([C.c_int, _dp, _dp, _dp, _dp, C.POINTER(C.c_int)], C.c_int),
         "dts_moment_tables": ([C.c_int, C.c_int, _dp, _dp], C.c_int),
         "dts_subsweep_size": ([C.c_int, C.c_int, C.c_int, C.c_int], C.c_longlong),
@@ -183,6 +184,12 @@ def sweep_once_noalloc(nx, ny, nz, dx, dy, dz, sn_order, legendre_order, src_mom
                                         C.c_void_p(src_moments.data_ptr()),
                                         C.c_void_p(sigma_t.data_ptr()), C.c_void_p(phi.data_ptr()),
                                         stream))
+
+
+def debug_fail_allocation(after: int):
+    """Test hook: the device allocation after `after` more successful ones fails once as
+    out-of-memory (DTS_ERR_OOM); a negative value disarms it."""
+    lib().dts_debug_fail_allocation(int(after))
 
 
 def tune_tile(w: inputs.Workload, precision=PREC_FP64, batch=None, device=0):

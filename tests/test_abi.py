@@ -77,3 +77,36 @@ def test_create_without_usable_device_fails_loudly(lib):
     with pytest.raises(dts.DTSError) as e:
         dts.Problem(nx=4, ny=4, nz=4, dx=1.0, dy=1.0, dz=1.0)
     assert e.value.status in (dts.DTS_ERR_CUDA, dts.DTS_ERR_INVALID_ARG)
+
+
+class _FakeCudaTensor:
+    """Just enough of a CUDA tensor for the binding's argument checks (no device needed)."""
+
+    def __init__(self, n, dtype=None):
+        import torch
+        self.is_cuda = True
+        self.dtype = dtype or torch.float64
+        self._n = n
+        self.device = type("D", (), {"index": 0})()
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):   # pragma: no cover - reaching it would be the failure
+        raise AssertionError("the binding must reject the call before touching device memory")
+
+
+def test_noalloc_binding_rejects_short_or_wrong_tensors_before_any_launch():
+    import torch
+    n, K = 5, 4                                # 5^3 voxels at P1
+    V = n ** 3
+    good_src, sig = _FakeCudaTensor(K * V), _FakeCudaTensor(V)
+    for src, st, phi, what in ((good_src, sig, _FakeCudaTensor(K * V - 1), "phi"),
+                               (_FakeCudaTensor(K * V - 1), sig, _FakeCudaTensor(K * V), "src_moments"),
+                               (good_src, _FakeCudaTensor(V - 1), _FakeCudaTensor(K * V), "sigma_t"),
+                               (good_src, sig, _FakeCudaTensor(K * V, torch.float32), "phi")):
+        with pytest.raises(ValueError, match=what):
+            dts.sweep_once_noalloc(n, n, n, 1.0, 1.0, 1.0, 4, 1, src, st, phi)

@@ -53,12 +53,15 @@ def _detector_loss(w, phi, target):
 def test_adjoint_64_central_differences():
     """Differentiation form: 64^3, 8 groups, S6, P1; squared detector-response
     error against a seeded target; central differences (step 1e-6 relative,
-    FP64 solves) on 20 seeded voxels, 10 for sigma_t and 10 for sigma_s."""
+    FP64 solves converged to 1e-14) on 20 seeded voxels, 10 for sigma_t and 10
+    for sigma_s. On a B300 the largest relative deviation measured was 5.3e-7
+    (both one-sided differences agreeing to ~2e-6, so no fixup active set
+    changed within +-h); the bound is 2e-6."""
     w = inputs.adjoint_64()
     tol = 1e-14
     one = np.ones(w.n_voxels)
     p = _problem(w, tol)
-    p.solve(allow_not_converged=True)
+    assert p.solve().converged == 1
     phi = p.fluence(0, dts.TOTAL)
     _, resp0 = _detector_loss(w, phi, 0.0)
     target = resp0 * inputs.detector_target_noise(resp0.size)
@@ -77,19 +80,19 @@ def test_adjoint_64_central_differences():
 
     def loss(st, ss):
         q = _problem(w, tol, scale_t=st, scale_s=ss)
-        q.solve(allow_not_converged=True)
+        assert q.solve().converged == 1
         return _detector_loss(w, q.fluence(0, dts.TOTAL), target)[0]
 
     for v in vt:
         e = np.zeros(w.n_voxels)
         e[v] = h
         fd = (loss(one + e, one) - loss(one - e, one)) / (2 * h)
-        assert abs(fd - gt[v]) <= 2e-4 * abs(gt[v]), (v, fd, gt[v])
+        assert abs(fd - gt[v]) <= 2e-6 * abs(gt[v]), (v, fd, gt[v])
     for v in vs:
         e = np.zeros(w.n_voxels)
         e[v] = h
         fd = (loss(one, one + e) - loss(one, one - e)) / (2 * h)
-        assert abs(fd - gs[v]) <= 2e-4 * abs(gs[v]), (v, fd, gs[v])
+        assert abs(fd - gs[v]) <= 2e-6 * abs(gs[v]), (v, fd, gs[v])
 
 
 def test_autograd_function_matches_adjoint():

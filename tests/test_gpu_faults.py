@@ -1,0 +1,33 @@
+"""Failure paths, injected on the host (no device fault, hang or trap): an
+out-of-memory device allocation turns into DTS_ERR_OOM, the failed call
+releases what it had allocated, and the library keeps working afterwards."""
+import numpy as np
+import pytest
+
+from paper_1910_11335_b300 import dts, inputs
+from parity_util import TOL_FP64, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("after", [0, 3, 12])
+def test_injected_allocation_failure_is_oom_and_leaks_nothing(ora, after):
+    import torch
+    w = inputs.small_cone(9, 8, 7, n_groups=2, sn_order=4, legendre_order=1)
+    dts.problem_from_workload(w, tol=0.0, max_iters=2).close()   # warm the context and the library
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    dts.debug_fail_allocation(after)
+    try:
+        with pytest.raises(dts.DTSError) as e:
+            dts.problem_from_workload(w, tol=0.0, max_iters=2)
+    finally:
+        dts.debug_fail_allocation(-1)
+    assert e.value.status == dts.DTS_ERR_OOM
+    assert "injected" in str(e.value)
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (4 << 20)
+    p = dts.problem_from_workload(w, tol=0.0, max_iters=3)   # the next call is unaffected
+    p.solve()
+    r = ora.solve(w, tol=0.0, max_iters=3)
+    assert rel_max(p.fluence(0, dts.TOTAL), r.total) <= TOL_FP64

@@ -44,7 +44,7 @@ def test_noalloc_sweep_matches_solver_on_calls_in_a_row():
                                  seed_index=1301, thin=False)
     b = inputs.random_volumetric(6, 11, 5, n_groups=1, sn_order=4, legendre_order=1,
                                  seed_index=1302, thin=False)
-    for w in (a, b, a):
+    for w in (a, a, b, a):   # a repeated shape reuses the tables; a new shape uploads its own
         ref = _solver_moments(w)
         got = _noalloc_moments(w)
         assert np.all(np.isfinite(got))
