@@ -2,23 +2,26 @@
 
 Default workload: the batched cone-beam form -- 96^3 voxels of 1/3 cm (the
 32 cm water-cylinder phantom with bone and air inserts), 19 groups, S8
-(80 directions), P3, 32 CT source positions on a 50 cm circle -- solved in FP32
-(sweep, contraction and octant partials) with FP64 accumulation, residual and
-balance. One step = one full dts_solve of the batch (ray trace, first-collision
-source, every group's source iteration to tol, downscatter), inputs already
-resident in HBM. The FP64 plain form runs one source of the same workload for
-the "FP32-batched vs FP64 plain" comparison and the 1e-4 relative L2 gate.
+(80 directions), P3, 32 CT source positions on a 50 cm circle -- with an FP32
+sweep, the scatter-source contraction and the Eq. 3 moments on the tensor cores
+(split BF16, FP32 accumulation; the fastest form measured) and FP64 scalar
+flux, residual and balance. One step = one full dts_solve of the batch (ray
+trace, first-collision source, every group's source iteration to tol,
+downscatter), inputs already resident in HBM. Beside it: the FP64 plain form on
+one source of the same workload ("FP32-batched vs FP64 plain", and the 1e-4
+relative L2 gate), the CUDA-core FP32 form on the same batch, the end-to-end
+rate through the C ABI with host buffers, and the CPU oracle on a sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank solves its own batch of 32 source positions (weak
-scaling; no collective on the data path) and rank 0 prints one JSON line.
+Under torchrun one ring of 32 N source positions is partitioned over the N
+ranks (32 per GPU, weak scaling, no collective on the data path); rank 0
+gathers the per-source results on the host and prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -42,12 +45,16 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch96", choices=["batch96", "hetero64", "precision128"])
     ap.add_argument("--sources", type=int, default=32)
+    ap.add_argument("--voxels", type=int, default=96,
+                    help="batch96 only: the phantom at N^3 voxels (profiling cases; the benchmark is 96)")
+    ap.add_argument("--groups", type=int, default=19, help="batch96 only: energy groups (19)")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--max-iters", type=int, default=None)
     ap.add_argument("--tile", default="auto", help="tx,ty,tz or 'auto' (dts_tune_tile)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the CUDA-core FP32 comparison")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "splitbf16", "tf32"],
                     help="arithmetic of the FP32-batched form's scatter-source contraction")
     return ap.parse_args()
@@ -59,19 +66,22 @@ def dist_env():
 
 
 def make_workload(args, rank=0):
-    from paper_1910_11335_b300 import inputs
+    """The rank's share of the workload. batch96: one ring of sources x world
+    CT source positions (2 pi k / n on the 50 cm circle), partitioned over the
+    ranks (rank r solves positions r, r + world, ...), so every GPU solves
+    `sources` independent projections of one scan; one GPU solves the ring of
+    `sources` positions."""
+    from paper_1910_11335_b300 import inputs, shard
     if args.workload == "batch96":
-        w = inputs.batch_96(args.sources)
-        if rank:
-            # rank r rotates its ring by r/world of one source spacing
-            world = dist_env()[2]
-            w.sources = inputs.ring_sources(w.sources[0].spectrum, args.sources)
-            rot = 2 * math.pi * rank / (world * args.sources)
-            for s in w.sources:
-                x, y, z = s.pos
-                c, sn = math.cos(rot), math.sin(rot)
-                s.pos = (c * x - sn * y, sn * x + c * y, z)
-                s.axis = (-s.pos[0] / 50.0, -s.pos[1] / 50.0, 0.0)
+        if getattr(args, "voxels", 96) == 96 and getattr(args, "groups", 19) == 19:
+            w = inputs.batch_96(args.sources)
+        else:
+            w = inputs.cone_beam(args.voxels, args.groups, 8, 3, args.sources, seed_index=1, tol=1e-6,
+                                 name=f"cone{args.voxels}_s8p3_{args.groups}g_x{args.sources}")
+        world = dist_env()[2]
+        if world > 1:
+            ring = inputs.ring_sources(w.sources[0].spectrum, args.sources * world)
+            w.sources = [ring[k] for k in shard.partition(len(ring), world, rank)]
         return w
     if args.workload == "hetero64":
         return inputs.hetero_64()
@@ -130,38 +140,38 @@ def measured_peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "of measured"
     except Exception:
-        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "of fallback"
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "of fallback"
 
 
-def direct_output(tile, fp32, K, ndo):
-    """Whether the library's batched kernel writes angular fluxes (N_d per cell)
-    instead of 8 K octant moment partials: FP32 batched tiles with 8 K > N_d."""
-    return sweep_kernel_name(tile, fp32) == "k_sweep_batch" and 8 * K > 8 * ndo   # 8 K > N_d
+def cpu_info():
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
-def sweep_bytes_per_update(K, ndo, rsz, psi=False):
-    """Algorithmic bytes of the sweep kernel per cell-direction update: per
-    (cell, octant) it reads K source moments and sigma_t, shared by the
-    octant's ndo directions; it writes K octant moment partials per (cell,
-    octant), or in the direct-output form one angular flux per update."""
-    if psi:
-        return (K + 1) * rsz / ndo + rsz
-    return (2 * K + 1) * rsz / ndo
-
-
-def cpu_sample(w, seconds_hint=True):
+def cpu_sample(w, threads):
     """The oracle, as it stands, on a bounded sample of the workload: source 0,
     group 0, one source iteration (ray trace, first-collision source and one
-    full sweep of all directions)."""
+    full sweep of all directions) on `threads` host threads."""
     import oracle
     from paper_1910_11335_b300.inputs import first_groups, with_sources
     t = first_groups(with_sources(w, [0]), 1)
-    threads = min(8, os.cpu_count() or 1)
     t0 = time.perf_counter()
     oracle.solve(t, 0, tol=0.0, max_iters=1, n_threads=threads)
     dt = time.perf_counter() - t0
-    u = t.n_voxels * t.n_dirs
-    return u / dt, threads, dt
+    return t.n_voxels * t.n_dirs / dt, dt
+
+
+def oracle_threads():
+    """Threads the oracle can use: it runs the eight octants of a sweep in parallel."""
+    return min(8, os.cpu_count() or 1)
 
 
 def run_reference(args):
@@ -169,9 +179,10 @@ def run_reference(args):
     if rank != 0:
         return
     w = make_workload(args)
+    threads = oracle_threads()
     vals = []
     for i in range(args.warmup + args.steps):
-        v, threads, dt = cpu_sample(w)
+        v, dt = cpu_sample(w, threads)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
@@ -183,39 +194,83 @@ def run_reference(args):
             "data": "synthetic", "scaling": "weak", "vs_baseline": None,
             "config": {"workload": w.name, "oracle": "plain FP64 C, gcc -O2, OpenMP over octants"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, **cpu_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes of the sweep kernel from one ncu capture at full size
-# (profiles/k_sweep_batch_batch96_s8p3.md: dram__bytes_read.sum + dram__bytes_write.sum of three
-# mid-sweep launches over their algorithmic bytes). The ratio is only used while the batched kernel's
-# source is the one that was profiled; any change to it makes "traffic" null until it is re-measured.
-MEASURED_TRAFFIC = {
-    ("k_sweep_batch", "batch96_s8p3_19g_x32", (8, 4, 4)): {
-        "dram_over_algorithmic": 1.33,
-        "source_sha256": "f53287b3d101fe2b58b18602fd4d49ee50f1132d46e9cc1f42b2468f8087e835",
-    },
-}
+# Per-kernel constants measured with ncu on a small case (48^3, 32 sources, S8 P3, 8 x 4 x 4 tiles:
+# profiles/k_sweep_batch_qin_cone48_s8p3_x32.md, profiles/k_moments_q_cone48_s8p3_x32.md), used while
+# the kernels' source is the one that was profiled (a hash of the kernel files), else reported null:
+#   inst_per_update      warp instructions issued per cell-direction update (smsp__inst_executed.sum)
+#   dram_over_design     dram__bytes_read.sum + dram__bytes_write.sum over the design's bytes per update
+#   fma_pipe             sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active / 100
+MEASURED = {}
 
 
-def batched_kernel_sha256():
-    """Hash of the batched sweep kernel's source block (what the traffic ratio was measured on)."""
+def kernel_sources_sha256():
     import hashlib
-    src = open(os.path.join(ROOT, "paper_1910_11335_b300", "csrc", "dts_kernels.cuh")).read()
-    a = src.index("// A3 + A4, batched form (FP32)")
-    b = src.index("// Translation units that only launch the sweep define DTS_SWEEP_KERNEL_ONLY so")
-    return hashlib.sha256(src[a:b].encode()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("dts_kernels.cuh", "dts_tc.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1910_11335_b300", "csrc", name), "rb").read())
+    return h.hexdigest()
 
 
-def sweep_kernel_name(tile, fp32):
-    """The sweep kernel the library launches for a tile shape."""
-    if fp32 and tuple(tile) in ((8, 4, 4), (4, 4, 4)):
-        return "k_sweep_batch"
-    if tile[1] * tile[2] == 32 and tile[1] in (4, 8):
-        return "k_sweep_lines"
-    return "k_sweep_stage"
+def roofline(stats, ms_step, steps, K, ndo, tc, peaks, which, n_sm):
+    """The dominant kernel's roofline and the HBM accounting of the iteration.
+
+    The wavefront sweep takes most of a step. It moves per update (design of the
+    tensor-core forms, SURVEY 8(d) route beta) the per-direction source Q it
+    reads (4 B) and the angular flux it writes (4 B) plus sigma_t shared by the
+    octant's directions; the fused CUDA-core form reads the K source moments per
+    (cell, octant) instead of Q. It is bound by instruction issue and latency,
+    not by HBM, so its roofline is the SM issue rate: achieved = measured warp
+    instructions per update x updates per second of sweep time (CUDA events
+    around the sweep graph), peak = 4 warp instructions per cycle per SM x SMs x
+    maximum SM clock. The HBM fractions are reported beside it: on the method's
+    algorithmic minimum (2K+1) x 4 / N_d bytes per update, on the
+    design's bytes, and on the DRAM bytes ncu measured; the moment kernel
+    (Eq. 3 + scatter-source contraction), which is HBM-bound, gets its own."""
+    updates = sum(s["updates"] for s in stats)
+    sweep_s = sum(s["sweep_ms"] for s in stats) / 1e3
+    red_s = sum(s["reduce_ms"] for s in stats) / 1e3
+    n_launch = sum(s["sweep_launches"] for s in stats)
+    ups = updates / sweep_s
+    hbm = peaks["hbm_gbs"]
+    bpu_alg = (2 * K + 1) * 4.0 / (8 * ndo)
+    bpu_sweep = 8.0 + 4.0 / ndo if tc else (K + 1) * 4.0 / ndo + 4.0
+    # moment kernel: psi read, Q written (tensor-core forms) or T written, F read, scalar flux in and out
+    bpu_mom = (4.0 + 4.0 if tc else 4.0 + K * 4.0 / (8 * ndo)) + K * 4.0 / (8 * ndo) + 16.0 / (8 * ndo)
+    kname = "k_sweep_batch (Q input)" if tc else "k_sweep_batch"
+    meas = MEASURED.get(kname) if MEASURED.get("sha256") == kernel_sources_sha256() else None
+    mom = MEASURED.get("k_moments_q") if meas else None
+    peak_inst = 4.0 * n_sm * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e9   # G warp instructions / s
+    out = {"bound": "alu", "unit": "Ginst/s", "peak": peak_inst, "kernel": kname,
+           "peak_source": f"4 warp instructions per cycle x {n_sm} SMs x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz",
+           "achieved": None, "frac": None, "traffic": None,
+           "sweep_updates_per_s": ups, "sweep_share_of_step": sweep_s * 1e3 / (ms_step * steps)}
+    if meas:
+        out["achieved"] = meas["inst_per_update"] * ups / 1e9
+        out["frac"] = out["achieved"] / peak_inst
+        # per launch, like the timing: the average launch's design bytes times the measured ratio
+        out["traffic"] = meas["dram_over_design"] * bpu_sweep * updates / n_launch
+        out["fma_pipe_utilization"] = meas["fma_pipe"]
+        out["inst_per_update"] = meas["inst_per_update"]
+    out["hbm"] = {
+        "peak_gbs": hbm, "peak_source": which,
+        "algorithmic_bytes_per_update": bpu_alg,
+        "frac_algorithmic": ups * bpu_alg / 1e9 / hbm,
+        "sweep_design_bytes_per_update": bpu_sweep,
+        "sweep_frac_design": ups * bpu_sweep / 1e9 / hbm,
+        "sweep_frac_dram_measured": (ups * bpu_sweep * meas["dram_over_design"] / 1e9 / hbm) if meas else None,
+        "moment_kernel": "k_moments_q" if tc else "k_reduce_psi",
+        "moment_bytes_per_update": bpu_mom,
+        "moment_frac_design": updates / red_s * bpu_mom / 1e9 / hbm,
+        "iteration_frac_dram_measured": (
+            (updates * bpu_sweep * meas["dram_over_design"] + updates * bpu_mom * mom["dram_over_design"])
+            / (sweep_s + red_s) / 1e9 / hbm) if (meas and mom) else None,
+    }
+    return out
 
 
 def aggregate(ms: float, updates: float, world: int, device=None):
@@ -235,7 +290,7 @@ def aggregate(ms: float, updates: float, world: int, device=None):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_1910_11335_b300 import build, dts
+    from paper_1910_11335_b300 import build, dts, shard
     build.build()
     rank, local, world = dist_env()
     if world > 1:
@@ -248,6 +303,7 @@ def run_ours(args):
     # auto: the fastest measured form of this workload, the split-BF16 tensor-core contraction
     prec = {"auto": dts.PREC_FP32_SPLITBF16, "fp32": dts.PREC_FP32, "splitbf16": dts.PREC_FP32_SPLITBF16,
             "tf32": dts.PREC_FP32_TF32}[args.precision] if fp32 else dts.PREC_FP64
+    tc = prec in (dts.PREC_FP32_SPLITBF16, dts.PREC_FP32_TF32)
     tol = args.tol if args.tol is not None else w.tol
     tuned = None
     if args.tile == "auto":
@@ -285,41 +341,38 @@ def run_ours(args):
     ms, updates = aggregate(ms, updates, world, dev)
     value = updates / (ms / 1e3)
 
-    # roofline of the dominant kernel (the wavefront sweep), timed live by
-    # CUDA events recorded around its launches inside the iteration graph
     K, ndo = (w.legendre_order + 1) ** 2, w.n_dirs // 8
-    rsz = 4 if fp32 else 8
-    sweep_ms = sum(s["sweep_ms"] for s in stats)
-    psi = direct_output(tile, fp32, K, ndo)
-    bpu = sweep_bytes_per_update(K, ndo, rsz, psi)
     peaks, which = measured_peaks()
-    achieved = (sum(s["updates"] for s in stats) * bpu / 1e9) / (sweep_ms / 1e3)
-    traffic = None
-    kname = sweep_kernel_name(tile, fp32)
-    meas = MEASURED_TRAFFIC.get((kname, w.name, tuple(tile)))
-    n_launch = sum(s["sweep_launches"] for s in stats)
-    if meas and n_launch and batched_kernel_sha256() == meas["source_sha256"]:
-        # per launch, like "achieved": the average launch's algorithmic bytes times the measured ratio
-        traffic = meas["dram_over_algorithmic"] * bpu * sum(s["updates"] for s in stats) / n_launch
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": sweep_kernel_name(tile, fp32), "peak_source": which,
-                "sweep_share_of_step": sweep_ms / ms if ms else None,
-                "bytes_per_update": bpu,
-                "sweep_output": "angular fluxes" if psi else "octant moment partials"}
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = roofline(stats, ms / args.steps if world == 1 else ev0.elapsed_time(ev1) / args.steps,
+                    args.steps, K, ndo, tc, peaks, which, n_sm)
+
+    # the ranks' per-source results gathered to rank 0 on the host (untimed; no device collective)
+    gathered = None
+    if world > 1:
+        mine = shard.partition(args.sources * world, world, rank)
+        local_res = {k: float(p.fluence(i, dts.TOTAL).sum()) for i, k in enumerate(mine)}
+        res = shard.gather_to_root(local_res, world, rank)
+        gathered = len(res) if res is not None else None
 
     extra = {}
     if rank == 0 and fp32 and not args.no_fp64:
         extra = fp64_plain(w, p, dts, local, stream, tol=1e-8)
+    if rank == 0 and fp32 and tc and not args.no_compare:
+        extra["cuda_core_fp32"] = cuda_core_form(w, tol, args, dts, local, stream)
     e2e = None
     if not args.no_e2e:
         e2e = end_to_end(w, prec, tol, args, dts, local, stream, torch)
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, threads, dt = cpu_sample(w)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+        threads = oracle_threads()
+        v1, dt1 = cpu_sample(w, 1)
+        vn, dtn = cpu_sample(w, threads)
+        cpu = {"value": vn, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{w.name}: source 0, group 0, one source iteration "
-                         f"({w.n_voxels * w.n_dirs:.3e} updates, {dt:.1f} s)"}
+                         f"({w.n_voxels * w.n_dirs:.3e} updates; {dtn:.1f} s on {threads} threads, "
+                         f"{dt1:.1f} s on 1)",
+               "single_thread": v1, **cpu_info()}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -329,21 +382,29 @@ def run_ours(args):
             "config": {"workload": w.name, "voxels": [w.nx, w.ny, w.nz], "groups": w.n_groups,
                        "directions": w.n_dirs, "legendre_order": w.legendre_order,
                        "sources_per_gpu": w.batch, "tol": tol,
-                       "precision": "fp32 sweep/contraction, fp64 accumulation" if fp32 else "fp64",
+                       "precision": {dts.PREC_FP32: "fp32 sweep and contraction (CUDA cores), fp64 accumulation",
+                                     dts.PREC_FP32_SPLITBF16: "fp32 sweep, split-bf16 tensor-core contractions "
+                                                              "(fp32 accumulate), fp64 accumulation",
+                                     dts.PREC_FP32_TF32: "fp32 sweep, split-tf32 tensor-core scatter-source "
+                                                         "contraction, fp64 accumulation",
+                                     dts.PREC_FP64: "fp64"}[prec],
                        "tile": [stats[0]["tile_x"], stats[0]["tile_y"], stats[0]["tile_z"]],
                        "tile_choice": "dts_tune_tile" if tuned else "given",
-                       "parallelism": f"weak x{world}, independent source batches",
+                       "parallelism": f"x{world}: one ring of {args.sources * world} source positions "
+                                      f"partitioned over the GPUs, no data-path collective",
                        "l2": "inputs larger than L2 (device state of tens of GB per step)"},
-            "roofline": roofline,
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "clocks": clk,
             "solve": {"sweeps_per_step": stats[0]["sweeps"], "updates_per_step": stats[0]["updates"],
                       "max_residual": stats[-1]["max_residual"], "converged": stats[-1]["converged"],
-                      "sweep_ms_per_step": sweep_ms / args.steps,
+                      "sweep_ms_per_step": sum(s["sweep_ms"] for s in stats) / args.steps,
                       "reduce_ms_per_step": sum(s["reduce_ms"] for s in stats) / args.steps},
         }
+        if gathered is not None:
+            line["gathered_sources"] = gathered
         line.update(extra)
         if extra.get("fp64_plain"):
             line["fp32_batched_over_fp64_plain"] = value / extra["fp64_plain"]["value"]
@@ -351,6 +412,29 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def cuda_core_form(w, tol, args, dts, dev, stream):
+    """The same batch solved once (after a warm-up) in the CUDA-core FP32 form,
+    for the comparison with the tensor-core form: updates/s and the relative L2
+    difference of source 0's total fluence."""
+    import torch
+    tile, _ = dts.tune_tile(w, precision=dts.PREC_FP32, device=dev)
+    q = dts.problem_from_workload(w, precision=dts.PREC_FP32, tol=tol, max_iters=args.max_iters or 1000,
+                                  tile=tile, device=dev, stream=stream.cuda_stream)
+    q.solve(allow_not_converged=True)
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    st = q.solve(allow_not_converged=True)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1)
+    out = {"value": st.updates / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "tile": list(tile),
+           "sweep_ms": st.sweep_ms, "reduce_ms": st.reduce_ms}
+    q.close()
+    return out
 
 
 def fp64_plain(w, p32, dts, dev, stream, tol):
