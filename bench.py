@@ -199,21 +199,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# Per-kernel constants measured with ncu on a small case (48^3, 32 sources, S8 P3, 8 x 4 x 4 tiles:
-# profiles/k_sweep_batch_qin_cone48_s8p3_x32.md, profiles/k_moments_q_cone48_s8p3_x32.md), used while
-# the kernels' source is the one that was profiled (a hash of the kernel files), else reported null:
-#   inst_per_update      warp instructions issued per cell-direction update (smsp__inst_executed.sum)
-#   dram_over_design     dram__bytes_read.sum + dram__bytes_write.sum over the design's bytes per update
-#   fma_pipe             sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active / 100
-MEASURED = {}
+# Per-kernel constants measured with ncu on a small case (48^3, 32 sources, S8 P3, 2 groups, 8 x 4 x 4
+# tiles; profiles/k_sweep_batch_cone48_s8p3_x32.md, profiles/k_moments_q_cone48_s8p3_x32.md), used while
+# the kernel's source block is the one that was profiled (its SHA-256), else reported null:
+#   inst_per_update    warp instructions issued per cell-direction update (smsp__inst_executed.sum)
+#   dram_over_design   dram__bytes_read.sum + dram__bytes_write.sum over the design's bytes per update
+#   fma_pipe           sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active / 100
+# The DRAM ratios are a 48^3 case's; at 96^3 the tile-to-tile faces, which make most of the sweep's
+# excess, are the same bytes per update and only their L2 hit rate can differ.
+MEASURED = {
+    "k_sweep_batch (Q input)": {"inst_per_update": 2.548, "dram_over_design": 1.287, "fma_pipe": 0.1826,
+                                "block": "sweep"},
+    "k_sweep_batch": {"inst_per_update": 2.833, "dram_over_design": 1.146, "fma_pipe": 0.2439, "block": "sweep"},
+    "k_moments_q": {"inst_per_update": 0.570, "dram_over_design": 0.999, "fma_pipe": 0.1415,
+                    "tensor_pipe": 0.0554, "block": "tc"},
+    "k_reduce_psi": {"inst_per_update": 0.603, "dram_over_design": 1.017, "fma_pipe": 0.4856, "block": "reduce_psi"},
+}
+MEASURED_SHA256 = {
+    "sweep": "bf3aca53991c6e7449043cdd85d8fc1dd43baddb87006e391db01c884e7c7634",
+    "tc": "cd7a984236c8ac80342819ab061caf7a6a0cf8d2d87342403cac8b1b1b645bdb",
+    "reduce_psi": "d9572bff6a77c2dd828c58bfcd20e651c3b435258948820752e8abd84880557a",
+}
 
 
-def kernel_sources_sha256():
+def kernel_block_sha256(block):
+    """SHA-256 of the source of a profiled kernel: the batched sweep's block of
+    dts_kernels.cuh, the tensor-core file, or the angular-flux moment kernel's block."""
     import hashlib
-    h = hashlib.sha256()
-    for name in ("dts_kernels.cuh", "dts_tc.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1910_11335_b300", "csrc", name), "rb").read())
-    return h.hexdigest()
+    csrc = os.path.join(ROOT, "paper_1910_11335_b300", "csrc")
+    if block == "tc":
+        src = open(os.path.join(csrc, "dts_tc.cuh")).read()
+    else:
+        src = open(os.path.join(csrc, "dts_kernels.cuh")).read()
+        a, b = {"sweep": ("// A3 + A4, batched form (FP32)", "// Error-free FP32 accumulation"),
+                "reduce_psi": ("// Eq. 3 and its higher moments from the angular fluxes",
+                               "// per source: residual")}[block]
+        src = src[src.index(a):src.index(b)]
+    return hashlib.sha256(src.encode()).hexdigest()
+
+
+def measured(kernel):
+    m = MEASURED.get(kernel)
+    if m and kernel_block_sha256(m["block"]) == MEASURED_SHA256[m["block"]]:
+        return m
+    return None
 
 
 def roofline(stats, ms_step, steps, K, ndo, tc, peaks, which, n_sm):
@@ -242,8 +271,8 @@ def roofline(stats, ms_step, steps, K, ndo, tc, peaks, which, n_sm):
     # moment kernel: psi read, Q written (tensor-core forms) or T written, F read, scalar flux in and out
     bpu_mom = (4.0 + 4.0 if tc else 4.0 + K * 4.0 / (8 * ndo)) + K * 4.0 / (8 * ndo) + 16.0 / (8 * ndo)
     kname = "k_sweep_batch (Q input)" if tc else "k_sweep_batch"
-    meas = MEASURED.get(kname) if MEASURED.get("sha256") == kernel_sources_sha256() else None
-    mom = MEASURED.get("k_moments_q") if meas else None
+    meas = measured(kname)
+    mom = measured("k_moments_q" if tc else "k_reduce_psi")
     peak_inst = 4.0 * n_sm * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e9   # G warp instructions / s
     out = {"bound": "alu", "unit": "Ginst/s", "peak": peak_inst, "kernel": kname,
            "peak_source": f"4 warp instructions per cycle x {n_sm} SMs x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz",
@@ -465,7 +494,8 @@ def fp64_plain(w, p32, dts, dev, stream, tol):
     return {"fp64_plain": {"value": v, "unit": UNIT, "sources": 1, "converged": st.converged,
                            "tile": list(tile),
                            "sweeps": st.sweeps, "ms": ms,
-                           "sweep_achieved_gbs": st.updates * sweep_bytes_per_update(K, ndo, 8) / 1e9
+                           # the method's algorithmic bytes in FP64: (2K+1) 8 / N_d per update
+                           "sweep_achieved_gbs_algorithmic": st.updates * (2 * K + 1) * 8.0 / (8 * ndo) / 1e9
                            / (st.sweep_ms / 1e3)},
             "fp32_batched_over_fp64_plain": None,
             "rel_l2_fp32_vs_fp64": err, "rel_l2_fp32_vs_fp64_max_group": max(errs_g)}

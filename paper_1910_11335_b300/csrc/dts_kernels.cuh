@@ -1467,7 +1467,18 @@ __global__ void k_resid_final(const double* blk, int nblk, const double* leak, i
         a[2] += o[2];
         a[3] += o[3];
     }
-    for (int i = threadIdx.x; i < nleak; i += blockDim.x) a[4] += leak[(size_t)b * nleak + i];
+    {   // four independent accumulators per thread (loads in flight together), added in a fixed order
+        const double* lk = leak + (size_t)b * nleak;
+        const int nt = blockDim.x;
+        double l4[4] = {0.0, 0.0, 0.0, 0.0};
+        int i = threadIdx.x;
+        for (; i + 3 * nt < nleak; i += 4 * nt) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) l4[u] += lk[i + u * nt];
+        }
+        for (; i < nleak; i += nt) l4[0] += lk[i];
+        a[4] = (l4[0] + l4[1]) + (l4[2] + l4[3]);
+    }
     for (int j = 0; j < 5; ++j) a[j] = block_sum(a[j], red);
     if (threadIdx.x == 0) {
         double* s = status + (size_t)b * 4;

@@ -627,7 +627,7 @@ dts_status record_reduce(dts_problem* p)
     } else {
         reduce_fn<R>(p->K)<<<dim3(nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
     }
-    k_resid_final<<<p->B, 256, 0, p->stream>>>(p->blk, nblk, p->leak, 8 * p->NT, p->status);
+    k_resid_final<<<p->B, 1024, 0, p->stream>>>(p->blk, nblk, p->leak, 8 * p->NT, p->status);
     p->graph_launches = p->n_stages + 2;
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(double) * 4 * p->B, cudaMemcpyDeviceToHost,
                        p->stream));
