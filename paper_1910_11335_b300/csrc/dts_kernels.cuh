@@ -1025,25 +1025,27 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     const bool lbx = NX ? tx == 0 : tx == p.NTx - 1;
     const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
     const bool lbz = negz ? tz == 0 : tz == p.NTz - 1;
-    double lk = 0.0;
-    if ((lbx || lby || lbz) && srcok) {
-        float sx_ = 0.f, sy_ = 0.f, sz_ = 0.f;
-        if (lbx) {
-            if constexpr (QIN) sx_ = xsum;
-            else
-                for (int e = 0; e < fxn; ++e) sx_ += fx[e * 32 + lane];
-        }
-        if (lby) sy_ = ysum;
-        if (lbz)
-            for (int e = 0; e < fzn; ++e) sz_ += fz[e * 32 + lane];
-        lk = p.Lw[(n0 + d) * 3] * (double)sx_ + p.Lw[(n0 + d) * 3 + 1] * (double)sy_ +
-             p.Lw[(n0 + d) * 3 + 2] * (double)sz_;
-    }
     // the source's leakage from this (octant, tile): its direction lanes summed in direction order
-    // into its slot (zero off the boundary), so that the per-source total is reproducible
+    // into its slot, so that the per-source total is reproducible; zero away from the boundary
     double tot = 0.0;
+    if (lbx || lby || lbz) {   // uniform across the warp
+        double lk = 0.0;
+        if (srcok) {
+            float sx_ = 0.f, sy_ = 0.f, sz_ = 0.f;
+            if (lbx) {
+                if constexpr (QIN) sx_ = xsum;
+                else
+                    for (int e = 0; e < fxn; ++e) sx_ += fx[e * 32 + lane];
+            }
+            if (lby) sy_ = ysum;
+            if (lbz)
+                for (int e = 0; e < fzn; ++e) sz_ += fz[e * 32 + lane];
+            lk = p.Lw[(n0 + d) * 3] * (double)sx_ + p.Lw[(n0 + d) * 3 + 1] * (double)sy_ +
+                 p.Lw[(n0 + d) * 3 + 2] * (double)sz_;
+        }
 #pragma unroll
-    for (int dd = 0; dd < NDO; ++dd) tot += __shfl_sync(0xffffffffu, lk, (srcok ? bl : 0) * NDO + dd);
+        for (int dd = 0; dd < NDO; ++dd) tot += __shfl_sync(0xffffffffu, lk, (srcok ? bl : 0) * NDO + dd);
+    }
     if (srcok && d == 0 && p.leak) p.leak[((size_t)(b0 + bl) * 8 + oct) * p.NT + tile] = tot;
 }
 
