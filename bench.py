@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the CUDA-core FP32 comparison")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "splitbf16", "tf32"],
                     help="arithmetic of the FP32-batched form's scatter-source contraction")
+    ap.add_argument("--split", type=int, default=4,
+                    help="solve each GPU's sources as this many problems on their own streams "
+                         "(dts_solve_many: one part's moment kernels beside another's sweep); 1 = one problem")
     return ap.parse_args()
 
 
@@ -208,15 +211,15 @@ def run_reference(args):
 # The DRAM ratios are a 48^3 case's; at 96^3 the tile-to-tile faces, which make most of the sweep's
 # excess, are the same bytes per update and only their L2 hit rate can differ.
 MEASURED = {
-    "k_sweep_batch (Q input)": {"inst_per_update": 2.452, "dram_over_design": 1.284, "fma_pipe": 0.1803,
+    "k_sweep_batch (Q input)": {"inst_per_update": 2.244, "dram_over_design": 1.284, "fma_pipe": 0.1742,
                                 "block": "sweep"},
-    "k_sweep_batch": {"inst_per_update": 2.819, "dram_over_design": 1.147, "fma_pipe": 0.2478, "block": "sweep"},
+    "k_sweep_batch": {"inst_per_update": 2.819, "dram_over_design": 1.147, "fma_pipe": 0.2477, "block": "sweep"},
     "k_moments_q": {"inst_per_update": 0.570, "dram_over_design": 0.999, "fma_pipe": 0.1415,
                     "tensor_pipe": 0.0554, "block": "tc"},
     "k_reduce_psi": {"inst_per_update": 0.603, "dram_over_design": 1.017, "fma_pipe": 0.4856, "block": "reduce_psi"},
 }
 MEASURED_SHA256 = {
-    "sweep": "93cc60ab0e4701b08afea398ffad21efa8f51990f0d4f5d8bed04236a376d38b",
+    "sweep": "19edcf2735b7a9ad7f1000edda43cb50564144d4628dda24a84b6126f980b764",
     "tc": "cd7a984236c8ac80342819ab061caf7a6a0cf8d2d87342403cac8b1b1b645bdb",
     "reduce_psi": "d9572bff6a77c2dd828c58bfcd20e651c3b435258948820752e8abd84880557a",
 }
@@ -316,6 +319,50 @@ def aggregate(ms: float, updates: float, world: int, device=None):
     return float(t[0]), float(u[0])
 
 
+class Parts:
+    """The workload's sources as consecutive runs (dts.source_parts), each one
+    problem on its own stream, solved together by dts_solve_many; with one run,
+    one problem on the given stream solved by dts_solve."""
+
+    def __init__(self, w, prec, tol, args, dts, dev, stream, torch, split=None):
+        self.dts = dts
+        self.runs = dts.source_parts(w.batch, args.split if split is None else split, w.sn_order)
+        tile = tuple(int(x) for x in args.tile.split(","))
+        self.streams = [stream] if len(self.runs) == 1 else [torch.cuda.Stream(dev) for _ in self.runs]
+        self.probs = [dts.problem_from_workload(w, precision=prec, tol=tol, max_iters=args.max_iters or 1000,
+                                                tile=tile, device=dev, stream=st.cuda_stream, sources=run)
+                      for run, st in zip(self.runs, self.streams)]
+
+    def solve(self):
+        """One solve of every source; the parts' stats merged into one dict."""
+        if len(self.probs) == 1:
+            sts = [self.probs[0].solve(allow_not_converged=True)]
+        else:
+            sts = self.dts.solve_many(self.probs, allow_not_converged=True)
+        d = [x.as_dict() for x in sts]
+        out = {k: sum(x[k] for x in d) for k in ("updates", "sweeps", "launches", "sweep_launches",
+                                                  "sweep_ms", "reduce_ms")}
+        out.update(max_residual=max(x["max_residual"] for x in d), solve_ms=max(x["solve_ms"] for x in d),
+                   converged=min(x["converged"] for x in d), tile_x=d[0]["tile_x"], tile_y=d[0]["tile_y"],
+                   tile_z=d[0]["tile_z"])
+        return out
+
+    def locate(self, k):
+        """(problem, member) of source k."""
+        for p, run in zip(self.probs, self.runs):
+            if k in run:
+                return p, run.index(k)
+        raise IndexError(k)
+
+    def fluence(self, k, comp, out=None):
+        p, b = self.locate(k)
+        return p.fluence(b, comp, out=out)
+
+    def close(self):
+        for p in self.probs:
+            p.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -338,16 +385,14 @@ def run_ours(args):
     if args.tile == "auto":
         tile, tuned = dts.tune_tile(w, precision=prec, device=local)
         args.tile = ",".join(str(x) for x in tile)
-    tile = tuple(int(x) for x in args.tile.split(","))
-    p = dts.problem_from_workload(w, precision=prec, tol=tol, max_iters=args.max_iters or 1000,
-                                  tile=tile, device=local, stream=stream.cuda_stream)
+    parts = Parts(w, prec, tol, args, dts, local, stream, torch)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
     for _ in range(args.warmup):
-        p.solve(allow_not_converged=True)
+        parts.solve()
     torch.cuda.synchronize(dev)
     barrier()
     clocks = Clocks(local)
@@ -359,8 +404,7 @@ def run_ours(args):
     barrier()
     ev0.record(stream)
     for _ in range(args.steps):
-        st = p.solve(allow_not_converged=True)
-        stats.append(st.as_dict())
+        stats.append(parts.solve())
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -380,15 +424,17 @@ def run_ours(args):
     gathered = None
     if world > 1:
         mine = shard.partition(args.sources * world, world, rank)
-        local_res = {k: float(p.fluence(i, dts.TOTAL).sum()) for i, k in enumerate(mine)}
+        local_res = {k: float(parts.fluence(i, dts.TOTAL).sum()) for i, k in enumerate(mine)}
         res = shard.gather_to_root(local_res, world, rank)
         gathered = len(res) if res is not None else None
 
     extra = {}
     if rank == 0 and fp32 and not args.no_fp64:
-        extra = fp64_plain(w, p, dts, local, stream, tol=1e-8)
+        extra = fp64_plain(w, parts, dts, local, stream, tol=1e-8)
     if rank == 0 and fp32 and tc and not args.no_compare:
         extra["cuda_core_fp32"] = cuda_core_form(w, tol, args, dts, local, stream)
+    split = [len(r) for r in parts.runs]
+    parts.close()
     e2e = None
     if not args.no_e2e:
         e2e = end_to_end(w, prec, tol, args, dts, local, stream, torch)
@@ -419,6 +465,7 @@ def run_ours(args):
                                      dts.PREC_FP64: "fp64"}[prec],
                        "tile": [stats[0]["tile_x"], stats[0]["tile_y"], stats[0]["tile_z"]],
                        "tile_choice": "dts_tune_tile" if tuned else "given",
+                       "split": split,
                        "parallelism": f"x{world}: one ring of {args.sources * world} source positions "
                                       f"partitioned over the GPUs, no data-path collective",
                        "l2": "inputs larger than L2 (device state of tens of GB per step)"},
@@ -447,21 +494,23 @@ def cuda_core_form(w, tol, args, dts, dev, stream):
     """The same batch solved once (after a warm-up) in the CUDA-core FP32 form,
     for the comparison with the tensor-core form: updates/s and the relative L2
     difference of source 0's total fluence."""
+    import copy
     import torch
     tile, _ = dts.tune_tile(w, precision=dts.PREC_FP32, device=dev)
-    q = dts.problem_from_workload(w, precision=dts.PREC_FP32, tol=tol, max_iters=args.max_iters or 1000,
-                                  tile=tile, device=dev, stream=stream.cuda_stream)
-    q.solve(allow_not_converged=True)
+    a = copy.copy(args)
+    a.tile = ",".join(str(x) for x in tile)
+    q = Parts(w, dts.PREC_FP32, tol, a, dts, dev, stream, torch)
+    q.solve()
     torch.cuda.synchronize(dev)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    st = q.solve(allow_not_converged=True)
+    st = q.solve()
     t1.record(stream)
     torch.cuda.synchronize(dev)
     ms = t0.elapsed_time(t1)
-    out = {"value": st.updates / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "tile": list(tile),
-           "sweep_ms": st.sweep_ms, "reduce_ms": st.reduce_ms}
+    out = {"value": st["updates"] / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "tile": list(tile),
+           "split": [len(r) for r in q.runs], "sweep_ms": st["sweep_ms"], "reduce_ms": st["reduce_ms"]}
     q.close()
     return out
 
@@ -484,7 +533,7 @@ def fp64_plain(w, p32, dts, dev, stream, tol):
     t1.record(stream)
     torch.cuda.synchronize(dev)
     ms = t0.elapsed_time(t1)
-    a = p32.fluence(0, dts.TOTAL)
+    a = p32.fluence(0, dts.TOTAL)   # source 0 of the FP32 batch
     b = q.fluence(0, dts.TOTAL)
     err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
     errs_g = [float(np.linalg.norm(a[g] - b[g]) / np.linalg.norm(b[g])) for g in range(w.n_groups)]
@@ -511,25 +560,24 @@ def end_to_end(w, prec, tol, args, dts, dev, stream, torch):
     st_h = torch.from_numpy(np.ascontiguousarray(w.sigma_t)).pin_memory().numpy()
     ss_h = torch.from_numpy(np.ascontiguousarray(w.sigma_s)).pin_memory().numpy()
     out = torch.empty(G * V, dtype=torch.float64).pin_memory().numpy()
-    tile = tuple(int(x) for x in args.tile.split(","))
-    p = dts.problem_from_workload(w, precision=prec, tol=tol, max_iters=args.max_iters or 1000,
-                                  tile=tile, device=dev, stream=stream.cuda_stream)
-    p.solve(allow_not_converged=True)
+    parts = Parts(w, prec, tol, args, dts, dev, stream, torch)
+    parts.solve()
     torch.cuda.synchronize(dev)
-    h2d = mat.nbytes + st_h.nbytes + ss_h.nbytes + B * (8 * 7 + 8 * G)
+    h2d = len(parts.probs) * (mat.nbytes + st_h.nbytes + ss_h.nbytes) + B * (8 * 7 + 8 * G)
     d2h = B * G * V * 8
     updates = 0
     t0 = time.perf_counter()
     for _ in range(steps):
-        p.set_materials(st_h, ss_h, mat)
-        for b, s in enumerate(w.sources):
-            p.set_source(b, s)
-        st = p.solve(allow_not_converged=True)
-        updates += st.updates
-        for b in range(B):
-            p.fluence(b, dts.TOTAL, out=out)
+        for p, run in zip(parts.probs, parts.runs):
+            p.set_materials(st_h, ss_h, mat)
+            for b, k in enumerate(run):
+                p.set_source(b, w.sources[k])
+        st = parts.solve()
+        updates += st["updates"]
+        for k in range(B):
+            parts.fluence(k, dts.TOTAL, out=out)
     dt = time.perf_counter() - t0
-    p.close()
+    parts.close()
     return {"value": updates / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps}
 

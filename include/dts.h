@@ -196,6 +196,30 @@ dts_status dts_set_source_cones(dts_problem *p, int batch_index, int n_cones,
 dts_status dts_solve(dts_problem *p, dts_solve_stats *stats);
 
 /*
+ * Solve n problems together, each as dts_solve would: typically disjoint
+ * source sets of one scan (independent CT projections, Sec. II.E), each
+ * problem with its own batch and stream. The host polls the problems and
+ * enqueues each problem's next source iteration (sweep, Eqs. 6-7 over the
+ * tile wavefront of Eq. 9; then the Eq. 3 reduction and scatter-source
+ * formation) as soon as its previous one is complete, so the problems' sweeps
+ * and moment kernels overlap on the GPU: the sweep is bound by instruction
+ * issue and latency, the moment kernel by HBM. The work and results of each
+ * problem are those of dts_solve on it alone, bit for bit; only the overlap
+ * differs. Problems sharing one stream get no overlap. Blocks until every
+ * problem is solved.
+ * problems: n distinct problems on one device (host array, not kept); stats:
+ * NULL or n structs, stats[i] filled as dts_solve fills it for problems[i]
+ * (its sweep and reduce times are its own, measured while it shared the GPU).
+ * Errors: DTS_ERR_INVALID_ARG (NULL, n < 1, a repeated problem, different
+ * devices); DTS_ERR_STATE (as dts_solve, on that problem); a CUDA, OOM or
+ * TIMEOUT error of one problem stops the scheduling, waits for every
+ * problem's stream and is returned; DTS_ERR_NOT_CONVERGED when some problem
+ * stopped above tol, after all of them have finished (the others' results
+ * are complete). The message of every failure is in dts_last_error(NULL).
+ */
+dts_status dts_solve_many(dts_problem *const *problems, int n, dts_solve_stats *stats);
+
+/*
  * Copy one component of the scalar fluence of batch member batch_index into
  * out[G][V] (photons/cm^2 per source particle). out_len counts doubles and
  * must be >= G*V. Device copies are ordered on the problem's stream; host

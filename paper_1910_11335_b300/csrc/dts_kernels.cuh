@@ -841,7 +841,17 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 #pragma unroll
         for (int h = 0; h < BX / 4; ++h) cp_async16(dst + 4 * h, src + 4 * h);
     };
-    if constexpr (QIN) stage_q(0);   // committed with the prologue's copies
+    if constexpr (QIN) {
+        // a lane without a source sweeps zeros: its ring slots are never copied to
+        if (!srcok) {
+#pragma unroll
+            for (int r = 0; r < S::QRING; ++r)
+#pragma unroll
+                for (int h = 0; h < BX / 4; ++h)
+                    *reinterpret_cast<float4*>(Tst + (r * 32 + lane) * BX + 4 * h) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        stage_q(0);   // committed with the prologue's copies
+    }
 
     // phase C lane: (moment kc, group h); items (source il, quad qd) = h + NH * j
     const int kc = lane % K, hc = lane / K;

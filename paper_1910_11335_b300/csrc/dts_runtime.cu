@@ -12,11 +12,14 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
+#include <thread>
 #include <tuple>
 #include <string>
 #include <vector>
@@ -752,64 +755,85 @@ void launch_push(dts_problem* p, int g)
 }
 
 // NVTX range for profilers (a no-op unless a tool is attached): the solve, each group, each iteration
-struct NvtxRange {
-    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
-    ~NvtxRange() { nvtxRangePop(); }
-    NvtxRange(const NvtxRange&) = delete;
-    NvtxRange& operator=(const NvtxRange&) = delete;
-};
-
-dts_status run_solve(dts_problem* p, dts_solve_stats* st)
-{
-    NvtxRange solve_range("dts_solve");
-    const int B = p->B, G = p->G;
-    const int W1 = p->W + 1;
-    TRY(ensure_ring(p));
-    TRY(build_graph(p));
-    if (p->q_mode) {
-        CK(cudaMemsetAsync(p->dev_err, 0, sizeof(int), p->stream));
-        *p->h_err = 0;
-    }
-    CK(cudaEventRecord(p->ev0, p->stream));
-    // A1: uncollided fluence, all sources and groups
-    {
-        RayParams rp;
-        rp.nx = p->d.nx; rp.ny = p->d.ny; rp.nz = p->d.nz; rp.V = p->V; rp.G = G;
-        rp.dx = p->d.dx; rp.dy = p->d.dy; rp.dz = p->d.dz;
-        rp.x0 = p->d.x0; rp.y0 = p->d.y0; rp.z0 = p->d.z0;
-        rp.mat = p->mat_nat; rp.scale_t = p->scale_t_nat; rp.sigma_t = p->sigma_t;
-        rp.src = p->src; rp.spec = p->spec; rp.unc = p->unc; rp.n_mat = p->n_mat; rp.fan = p->fan;
-        if (p->n_mat <= kRayMats) {
-            k_raytrace_mat<<<dim3((p->V + kRayThreads - 1) / kRayThreads, B), kRayThreads, 0, p->stream>>>(rp);
-        } else {
-            for (int g0 = 0; g0 < G; g0 += kRayGroups)
-                k_raytrace<<<dim3((p->V + 127) / 128, B), 128, 0, p->stream>>>(rp, g0);
-        }
-        if (p->n_uslots > 0) {   // members with several cones
-            if (p->n_mat > kRayMats)
-                return fail(p, DTS_ERR_INVALID_ARG, "combined cone sources need at most 8 materials");
-            ConeParams cp;
-            cp.geo = p->cone_geo; cp.spec = p->cone_spec; cp.n_cones = p->cone_n; cp.slot = p->uslot;
-            cp.U = p->U; cp.cap = p->cone_cap; cp.K = p->K; cp.L = p->L;
-            k_raytrace_cones<<<dim3((p->V + kRayThreads - 1) / kRayThreads, B), kRayThreads, 0, p->stream>>>(rp, cp);
-        }
-        CK(cudaGetLastError());
-    }
-    for (int g = 0; g < std::min(G, W1); ++g) {
-        if (p->fp64) launch_fixed_source<double>(p, g, g % W1);
-        else launch_fixed_source<float>(p, g, g % W1);
-    }
-
-    int64_t updates = 0, sweeps = 0, sweep_launches = 0;
-    int64_t launches = (p->n_mat <= kRayMats ? 1 : (G + kRayGroups - 1) / kRayGroups) + std::min(G, W1);
+// One solve as a sequence of steps, so that several problems can be interleaved
+// (dts_solve_many): start, then per group begin_group, (launch_iteration,
+// complete_iteration) until the group's members stop, end_group; then finish.
+// NVTX ranges are start/end ranges (not a push/pop stack), since the steps of
+// interleaved problems do not nest.
+struct SolveRun {
+    dts_problem* p;
+    int B, G, W1;
+    int g = 0, it = 0, n_active = 0;
+    int64_t updates = 0, sweeps = 0, sweep_launches = 0, launches = 0;
     double max_res = 0.0, sweep_ms = 0.0, reduce_ms = 0.0;
-    bool all_conv = true;
-    const int64_t u_per_sweep = (int64_t)p->V * p->nd;
-    std::vector<double> best(B), last_improve(B);
-    for (int g = 0; g < G; ++g) {
+    bool all_conv = true, done = false;
+    int64_t u_per_sweep;
+    std::vector<double> best, last_improve;
+    nvtxRangeId_t r_solve = 0, r_group = 0, r_iter = 0;
+
+    explicit SolveRun(dts_problem* pp)
+        : p(pp), B(pp->B), G(pp->G), W1(pp->W + 1), u_per_sweep((int64_t)pp->V * pp->nd), best(pp->B),
+          last_improve(pp->B)
+    {
+    }
+    ~SolveRun()
+    {
+        if (r_iter) nvtxRangeEnd(r_iter);
+        if (r_group) nvtxRangeEnd(r_group);
+        if (r_solve) nvtxRangeEnd(r_solve);
+    }
+    SolveRun(const SolveRun&) = delete;
+    SolveRun& operator=(const SolveRun&) = delete;
+
+    // graphs, the first-collision source of every group (A1), the first groups' fixed sources
+    dts_status start()
+    {
+        r_solve = nvtxRangeStartA("dts_solve");
+        TRY(ensure_ring(p));
+        TRY(build_graph(p));
+        if (p->q_mode) {
+            CK(cudaMemsetAsync(p->dev_err, 0, sizeof(int), p->stream));
+            *p->h_err = 0;
+        }
+        CK(cudaEventRecord(p->ev0, p->stream));
+        {
+            RayParams rp;
+            rp.nx = p->d.nx; rp.ny = p->d.ny; rp.nz = p->d.nz; rp.V = p->V; rp.G = G;
+            rp.dx = p->d.dx; rp.dy = p->d.dy; rp.dz = p->d.dz;
+            rp.x0 = p->d.x0; rp.y0 = p->d.y0; rp.z0 = p->d.z0;
+            rp.mat = p->mat_nat; rp.scale_t = p->scale_t_nat; rp.sigma_t = p->sigma_t;
+            rp.src = p->src; rp.spec = p->spec; rp.unc = p->unc; rp.n_mat = p->n_mat; rp.fan = p->fan;
+            if (p->n_mat <= kRayMats) {
+                k_raytrace_mat<<<dim3((p->V + kRayThreads - 1) / kRayThreads, B), kRayThreads, 0, p->stream>>>(rp);
+            } else {
+                for (int g0 = 0; g0 < G; g0 += kRayGroups)
+                    k_raytrace<<<dim3((p->V + 127) / 128, B), 128, 0, p->stream>>>(rp, g0);
+            }
+            if (p->n_uslots > 0) {   // members with several cones
+                if (p->n_mat > kRayMats)
+                    return fail(p, DTS_ERR_INVALID_ARG, "combined cone sources need at most 8 materials");
+                ConeParams cp;
+                cp.geo = p->cone_geo; cp.spec = p->cone_spec; cp.n_cones = p->cone_n; cp.slot = p->uslot;
+                cp.U = p->U; cp.cap = p->cone_cap; cp.K = p->K; cp.L = p->L;
+                k_raytrace_cones<<<dim3((p->V + kRayThreads - 1) / kRayThreads, B), kRayThreads, 0, p->stream>>>(rp, cp);
+            }
+            CK(cudaGetLastError());
+        }
+        for (int gg = 0; gg < std::min(G, W1); ++gg) {
+            if (p->fp64) launch_fixed_source<double>(p, gg, gg % W1);
+            else launch_fixed_source<float>(p, gg, gg % W1);
+        }
+        launches = (p->n_mat <= kRayMats ? 1 : (G + kRayGroups - 1) / kRayGroups) + std::min(G, W1);
+        g = 0;
+        return begin_group();
+    }
+
+    // group g: its cross sections, every member active again, the group's first source
+    dts_status begin_group()
+    {
         char gname[32];
         snprintf(gname, sizeof gname, "group %d", g);
-        NvtxRange group_range(gname);
+        r_group = nvtxRangeStartA(gname);
         const int slot = g % W1;
         k_set_ctl<<<1, 1, 0, p->stream>>>(p->ctl, g, slot);
         CK(cudaMemsetAsync(p->phi00, 0, sizeof(double) * B * p->NC, p->stream));
@@ -830,62 +854,88 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
             TRY(launch_group_init<float>(p, slot));
         }
         CK(cudaGetLastError());
-        int n_active = B;
-        for (int it = 1; it <= p->d.max_iters && n_active > 0; ++it) {
-            NvtxRange iter_range("source iteration");
-            CK(cudaEventRecord(p->eva, p->stream));
-            CK(cudaGraphLaunch(p->graph, p->stream));
-            CK(cudaEventRecord(p->evb, p->stream));
-            CK(cudaGraphLaunch(p->graph_red, p->stream));
-            CK(cudaEventRecord(p->evc, p->stream));
-            CK(cudaStreamSynchronize(p->stream));
-            if (p->q_mode && *p->h_err)
-                return fail(p, DTS_ERR_TIMEOUT, "k_moments_q: a bounded wait on a bulk copy or the tensor cores gave up");
-            launches += p->graph_launches;
-            sweep_launches += p->n_stages;
-            {
-                float a = 0.f, b2 = 0.f;
-                CK(cudaEventElapsedTime(&a, p->eva, p->evb));
-                CK(cudaEventElapsedTime(&b2, p->evb, p->evc));
-                sweep_ms += a;
-                reduce_ms += b2;
-            }
-            bool changed = false;
-            for (int b = 0; b < B; ++b) {
-                if (!p->h_active[b]) continue;
-                const double* s = p->h_status + 4 * b;
-                const size_t bg = (size_t)b * G + g;
-                p->iters[bg] = it;
-                p->resid[bg] = s[0];
-                p->balance[bg * 3 + 0] = s[1];
-                p->balance[bg * 3 + 1] = s[2];
-                p->balance[bg * 3 + 2] = s[3];
-                updates += u_per_sweep;
-                ++sweeps;
-                bool stop = p->d.tol > 0.0 && s[0] < p->d.tol;
-                if (!stop && !p->fp64 && p->d.tol > 0.0) {
-                    // FP32 forms: stop when the residual has stagnated at the rounding floor
-                    if (s[0] < 0.99 * best[b]) {
-                        best[b] = s[0];
-                        last_improve[b] = it;
-                    } else if (it - last_improve[b] >= 10) {
-                        stop = true;
-                    }
-                }
-                if (stop) {
-                    p->h_active[b] = 0;
-                    --n_active;
-                    changed = true;
-                }
-            }
-            if (changed && n_active > 0)
-                CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+        n_active = B;
+        it = 0;
+        return DTS_OK;
+    }
+
+    // the group goes on while a member iterates and the iteration cap is not reached
+    bool group_iterating() const { return n_active > 0 && it < p->d.max_iters; }
+
+    // one source iteration (the sweep graph, then the moment graph) enqueued
+    dts_status launch_iteration()
+    {
+        ++it;
+        r_iter = nvtxRangeStartA("source iteration");
+        CK(cudaEventRecord(p->eva, p->stream));
+        CK(cudaGraphLaunch(p->graph, p->stream));
+        CK(cudaEventRecord(p->evb, p->stream));
+        CK(cudaGraphLaunch(p->graph_red, p->stream));
+        CK(cudaEventRecord(p->evc, p->stream));
+        return DTS_OK;
+    }
+
+    // waits for the launched iteration, records each member's residual and balance, and
+    // retires the members that stopped (A7)
+    dts_status complete_iteration()
+    {
+        CK(cudaEventSynchronize(p->evc));
+        nvtxRangeEnd(r_iter);
+        r_iter = 0;
+        if (p->q_mode && *p->h_err)
+            return fail(p, DTS_ERR_TIMEOUT, "k_moments_q: a bounded wait on a bulk copy or the tensor cores gave up");
+        launches += p->graph_launches;
+        sweep_launches += p->n_stages;
+        {
+            float a = 0.f, b2 = 0.f;
+            CK(cudaEventElapsedTime(&a, p->eva, p->evb));
+            CK(cudaEventElapsedTime(&b2, p->evb, p->evc));
+            sweep_ms += a;
+            reduce_ms += b2;
         }
+        bool changed = false;
+        for (int b = 0; b < B; ++b) {
+            if (!p->h_active[b]) continue;
+            const double* s = p->h_status + 4 * b;
+            const size_t bg = (size_t)b * G + g;
+            p->iters[bg] = it;
+            p->resid[bg] = s[0];
+            p->balance[bg * 3 + 0] = s[1];
+            p->balance[bg * 3 + 1] = s[2];
+            p->balance[bg * 3 + 2] = s[3];
+            updates += u_per_sweep;
+            ++sweeps;
+            bool stop = p->d.tol > 0.0 && s[0] < p->d.tol;
+            if (!stop && !p->fp64 && p->d.tol > 0.0) {
+                // FP32 forms: stop when the residual has stagnated at the rounding floor
+                if (s[0] < 0.99 * best[b]) {
+                    best[b] = s[0];
+                    last_improve[b] = it;
+                } else if (it - last_improve[b] >= 10) {
+                    stop = true;
+                }
+            }
+            if (stop) {
+                p->h_active[b] = 0;
+                --n_active;
+                changed = true;
+            }
+        }
+        if (changed && n_active > 0)
+            CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+        return DTS_OK;
+    }
+
+    // the group's downscatter into the ring (A2) and a later group's fixed source; then the
+    // next group, or the end of the solve
+    dts_status end_group()
+    {
         for (int b = 0; b < B; ++b) {
             const size_t bg = (size_t)b * G + g;
             max_res = std::max(max_res, p->resid[bg]);
             if (p->d.tol > 0.0 && !(p->resid[bg] < p->d.tol)) all_conv = false;
         }
+        const int slot = g % W1;
         if (p->fp64) launch_push<double>(p, g);
         else launch_push<float>(p, g);
         launches += 3;   // set_ctl, group_xs, push (the group's T = F is a copy, not a kernel)
@@ -895,28 +945,53 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
             ++launches;
         }
         CK(cudaGetLastError());
+        nvtxRangeEnd(r_group);
+        r_group = 0;
+        if (++g < G) return begin_group();
+        done = true;
+        return DTS_OK;
     }
-    CK(cudaEventRecord(p->ev1, p->stream));
-    CK(cudaEventSynchronize(p->ev1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
-    p->solved = true;
-    if (st) {
-        st->updates = updates;
-        st->sweeps = sweeps;
-        st->max_residual = max_res;
-        st->solve_ms = ms;
-        st->sweep_ms = sweep_ms;
-        st->reduce_ms = reduce_ms;
-        st->launches = launches;
-        st->sweep_launches = sweep_launches;
-        st->converged = all_conv ? 1 : 0;
-        st->tile_x = p->TX;
-        st->tile_y = p->TY;
-        st->tile_z = p->TZ;
+
+    dts_status finish(dts_solve_stats* st)
+    {
+        CK(cudaEventRecord(p->ev1, p->stream));
+        CK(cudaEventSynchronize(p->ev1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->solved = true;
+        if (st) {
+            st->updates = updates;
+            st->sweeps = sweeps;
+            st->max_residual = max_res;
+            st->solve_ms = ms;
+            st->sweep_ms = sweep_ms;
+            st->reduce_ms = reduce_ms;
+            st->launches = launches;
+            st->sweep_launches = sweep_launches;
+            st->converged = all_conv ? 1 : 0;
+            st->tile_x = p->TX;
+            st->tile_y = p->TY;
+            st->tile_z = p->TZ;
+        }
+        nvtxRangeEnd(r_solve);
+        r_solve = 0;
+        if (!all_conv) return fail(p, DTS_ERR_NOT_CONVERGED, "some (source, group) stopped above tol");
+        return DTS_OK;
     }
-    if (!all_conv) return fail(p, DTS_ERR_NOT_CONVERGED, "some (source, group) stopped above tol");
-    return DTS_OK;
+};
+
+dts_status run_solve(dts_problem* p, dts_solve_stats* st)
+{
+    SolveRun r(p);
+    TRY(r.start());
+    while (!r.done) {
+        while (r.group_iterating()) {
+            TRY(r.launch_iteration());
+            TRY(r.complete_iteration());
+        }
+        TRY(r.end_group());
+    }
+    return r.finish(st);
 }
 
 // the batched kernel addresses one warp's sources with 32-bit offsets
@@ -1710,6 +1785,82 @@ dts_status dts_solve(dts_problem* p, dts_solve_stats* stats)
         if (!p->src_set[b]) return fail(p, DTS_ERR_STATE, "a batch member has no source");
     DevGuard guard(p->d.device);
     return run_solve(p, stats);
+}
+
+// Several problems (disjoint source sets, each on its own stream) solved together.
+// Each problem's next source iteration is enqueued as soon as its last one is
+// complete (the host polls the problems' events), so the problems' sweeps and
+// moment graphs overlap on the GPU as they fall.
+dts_status dts_solve_many(dts_problem* const* problems, int n, dts_solve_stats* stats)
+{
+    // every failure's message also goes to the thread's error (dts_last_error(NULL))
+    auto bad = [](dts_problem* p, dts_status s, const char* msg) {
+        fail(p, s, msg);
+        g_thread_error = msg;
+        return s;
+    };
+    if (!problems || n < 1) return bad(nullptr, DTS_ERR_INVALID_ARG, "problems is NULL or n < 1");
+    for (int i = 0; i < n; ++i) {
+        dts_problem* p = problems[i];
+        if (!p) return bad(nullptr, DTS_ERR_INVALID_ARG, "a problem is NULL");
+        for (int j = 0; j < i; ++j)
+            if (problems[j] == p) return bad(p, DTS_ERR_INVALID_ARG, "a problem appears twice");
+        if (p->d.device != problems[0]->d.device)
+            return bad(p, DTS_ERR_INVALID_ARG, "the problems are on different devices");
+        if (!p->materials_set) return bad(p, DTS_ERR_STATE, "dts_set_materials has not been called");
+        for (int b = 0; b < p->B; ++b)
+            if (!p->src_set[b]) return bad(p, DTS_ERR_STATE, "a batch member has no source");
+    }
+    DevGuard guard(problems[0]->d.device);
+    std::vector<std::unique_ptr<SolveRun>> runs;
+    for (int i = 0; i < n; ++i) runs.emplace_back(new SolveRun(problems[i]));
+    std::vector<char> in_flight(n, 0), finished(n, 0);
+    dts_status first_soft = DTS_OK;   // DTS_ERR_NOT_CONVERGED of some problem: the others still finish
+    // a hard error of problem i: stop scheduling, let every stream drain, return the error
+    auto abort_all = [&](int i, dts_status s) {
+        for (int j = 0; j < n; ++j) cudaStreamSynchronize(problems[j]->stream);
+        g_thread_error = problems[i]->err;
+        return s;
+    };
+    for (int i = 0; i < n; ++i) {
+        const dts_status s = runs[i]->start();
+        if (s != DTS_OK) return abort_all(i, s);
+    }
+    int remaining = n;
+    while (remaining > 0) {
+        bool progressed = false;
+        for (int i = 0; i < n; ++i) {
+            if (finished[i]) continue;
+            SolveRun& r = *runs[i];
+            dts_status s = DTS_OK;
+            if (in_flight[i]) {
+                const cudaError_t q = cudaEventQuery(r.p->evc);
+                if (q == cudaErrorNotReady) continue;
+                in_flight[i] = 0;
+                s = r.complete_iteration();   // a failed query surfaces here
+            }
+            progressed = true;
+            while (s == DTS_OK && !r.done && !r.group_iterating()) s = r.end_group();
+            if (s == DTS_OK && r.done) {
+                finished[i] = 1;
+                --remaining;
+                s = r.finish(stats ? &stats[i] : nullptr);
+                if (s == DTS_ERR_NOT_CONVERGED) {
+                    if (first_soft == DTS_OK) {
+                        first_soft = s;
+                        g_thread_error = r.p->err;
+                    }
+                    continue;
+                }
+            } else if (s == DTS_OK) {
+                s = r.launch_iteration();
+                in_flight[i] = 1;
+            }
+            if (s != DTS_OK) return abort_all(i, s);
+        }
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    return first_soft;
 }
 
 dts_status dts_get_scalar_fluence(dts_problem* p, int batch_index, dts_component comp, double* out,

@@ -68,7 +68,8 @@ EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_sol
            "dts_get_balance", "dts_last_error", "dts_destroy_problem", "dts_status_string",
            "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size",
            "dts_sweep_once_noalloc", "dts_solve_adjoint", "dts_get_adjoint_iterations",
-           "dts_tune_tile", "dts_set_source_cones", "dts_get_dose", "dts_debug_fail_allocation")
+           "dts_tune_tile", "dts_set_source_cones", "dts_get_dose", "dts_debug_fail_allocation",
+           "dts_solve_many")
 
 
 def lib():
@@ -88,6 +89,7 @@ def lib():
         "dts_set_source_cones": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(SourceDesc)], C.c_int),
         "dts_get_dose": ([C.c_void_p, C.c_int, C.c_int, _dp, _dp, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
         "dts_solve": ([C.c_void_p, C.POINTER(SolveStats)], C.c_int),
+        "dts_solve_many": ([C.POINTER(C.c_void_p), C.c_int, C.POINTER(SolveStats)], C.c_int),
         "dts_get_scalar_fluence": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
         "dts_get_moments": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int], C.c_int),
         "dts_get_iterations": ([C.c_void_p, _ip, C.c_size_t], C.c_int),
@@ -349,6 +351,40 @@ class Problem:
         out = np.zeros(self.B * self.G * 3)
         _check(lib().dts_get_balance(self._h, _dptr(out), out.size), self._h)
         return out.reshape(self.B, self.G, 3)
+
+
+def solve_many(problems, allow_not_converged: bool = False):
+    """Solve several problems together (dts_solve_many): disjoint source sets,
+    each problem on its own stream, with one problem's moment kernels running
+    beside another's sweep. Returns one SolveStats per problem."""
+    n = len(problems)
+    hs = (C.c_void_p * n)(*[p._h for p in problems])
+    st = (SolveStats * n)()
+    rc = lib().dts_solve_many(hs, n, st)
+    if not (rc == DTS_ERR_NOT_CONVERGED and allow_not_converged):
+        _check(rc, None)
+    return list(st)
+
+
+def source_parts(n_sources: int, parts: int, sn_order: int):
+    """Split source indices 0..n_sources-1 into `parts` consecutive runs for
+    solve_many. The batched sweep packs 32 // (N(N+2)/8) sources into a warp
+    (3 for S8), so every run but the last is a whole number of warps: the runs
+    together need as many warps per tile as one batch of all the sources."""
+    ndo = sn_order * (sn_order + 2) // 8
+    gran = max(1, 32 // ndo)
+    parts = max(1, min(parts, n_sources))
+    warps = -(-n_sources // gran)
+    if warps < parts:
+        gran, warps = 1, n_sources
+    base, extra = divmod(warps, parts)
+    sizes = [(base + (1 if k >= parts - extra else 0)) * gran for k in range(parts - 1)]
+    sizes.append(n_sources - sum(sizes))
+    out, s0 = [], 0
+    for n in sizes:
+        out.append(list(range(s0, s0 + n)))
+        s0 += n
+    return out
 
 
 def problem_from_workload(w: inputs.Workload, precision=PREC_FP64, tol=None, max_iters=None,
