@@ -196,6 +196,37 @@ dts_status dts_set_source_cones(dts_problem *p, int batch_index, int n_cones,
 dts_status dts_solve(dts_problem *p, dts_solve_stats *stats);
 
 /*
+ * Restart from saved moments: member batch_index's source iteration in every
+ * group g starts from moments[g][k][v] (G x K x V doubles, natural voxel order,
+ * the collided moments dts_get_moments returns; host or device memory per
+ * is_device, copied) instead of from zero. The group's first sweep then sees
+ * T = F + sigma_s phi_guess (the scatter term of Eq. 2 evaluated on the
+ * guess), and its first residual measures the change from the guess, so a
+ * converged guess stops after one iteration. moments NULL clears the member's
+ * guess (zeros, which is exactly the default start). The guess holds for every
+ * later solve of p until cleared; the first call allocates B*G*K*V doubles on
+ * the device (and, in the tensor-core forms, the group's first T as FP32).
+ * Errors: DTS_ERR_INVALID_ARG (index, len < G*K*V, a non-finite host value),
+ * DTS_ERR_OOM, DTS_ERR_CUDA.
+ */
+dts_status dts_set_initial_guess(dts_problem *p, int batch_index, const double *moments, size_t len,
+                                 int is_device);
+
+/*
+ * Per-iteration progress (the paper's progressive display of the iteration,
+ * Sec. II.C): after every source iteration of a solve of p (dts_solve or
+ * dts_solve_many) the library calls fn(user, group, iteration, residuals,
+ * batch) on the solving thread. residuals[b] is member b's relative L2 change
+ * of its scalar fluence in that iteration (the convergence measure of tol), or
+ * NaN for a member that had stopped before it; the array lives for the call
+ * only. iteration counts from 1 in every group. fn must not call the library
+ * on p. fn NULL turns the callback off. Errors: DTS_ERR_INVALID_ARG (p NULL).
+ */
+typedef void (*dts_iteration_fn)(void *user, int group, int iteration, const double *residuals,
+                                 int batch);
+dts_status dts_set_iteration_callback(dts_problem *p, dts_iteration_fn fn, void *user);
+
+/*
  * Solve n problems together, each as dts_solve would: typically disjoint
  * source sets of one scan (independent CT projections, Sec. II.E), each
  * problem with its own batch and stream. The host polls the problems and
@@ -328,10 +359,55 @@ dts_status dts_quadrature(int sn_order, double *mu, double *eta, double *xi, dou
  * volumetric source) and the highest rate of updates per second of sweep plus
  * Eq. 3 reduction time wins. Writes desc->tile_x/y/z; *best_updates_per_s
  * (may be NULL) gets that probe rate.
- * Results are cached per process. Runs on the device; allocates and frees
- * probe problems. Errors: DTS_ERR_INVALID_ARG, DTS_ERR_CUDA.
+ * Results are cached per process and, when a cache file is named (below), on
+ * disk: a hit returns the stored tile and rate without probing. Runs on the
+ * device; allocates and frees probe problems. Errors: DTS_ERR_INVALID_ARG,
+ * DTS_ERR_CUDA.
  */
 dts_status dts_tune_tile(dts_problem_desc *desc, double *best_updates_per_s);
+
+/*
+ * Name the tuner's cache file for this process (path copied; NULL or "" turns
+ * the file off); until this is called the environment variable DTS_TUNE_CACHE
+ * names it. dts_tune_tile looks a shape up there after its per-process cache
+ * and appends each new result as one text line
+ *   dts-tune-v1 <device name, blanks as '_'> <SM count> nx ny nz N L
+ *               <probe batch = min(batch, 16)> <precision> tx ty tz <rate>
+ * (a later line for the same key wins; lines that do not parse are ignored; a
+ * file that cannot be read or written is skipped). Host only; always DTS_OK.
+ */
+dts_status dts_tune_cache_file(const char *path);
+
+/*
+ * The DTS_DEBUG_BOUNDS build (libdts_debug.so, compiled with
+ * -DDTS_DEBUG_BOUNDS): before the batched sweep, the tensor-core moment
+ * kernel, the angular-flux moment kernel and the residual kernel touch a
+ * region of a global buffer, they check the region's end against the
+ * buffer's allocated size; a region that does not fit is skipped and recorded
+ * in a device error word, and the solve returns DTS_ERR_INTERNAL with the
+ * kernel and site in its message after the iteration. This call checks that
+ * machinery: *is_debug_build (may be NULL) is 1 in the debug build, 0
+ * otherwise; in the debug build a one-thread kernel evaluates one bounds
+ * check, failing when plant != 0 (it touches no memory either way), and the
+ * call returns DTS_ERR_INTERNAL with the message in dts_last_error(NULL) when
+ * the check failed, DTS_OK when it passed. The normal build returns DTS_OK
+ * without device work.
+ */
+dts_status dts_debug_bounds_selftest(int plant, int *is_debug_build);
+
+/*
+ * Failure-path test hook of the tensor-core forms, whose moment kernel waits
+ * on mbarriers for its bulk copies and tensor-core results. Every such wait is
+ * bounded: it gives up after about a second, the kernel records the failure in
+ * a device error word, leaves its item loop with no copy or MMA in flight,
+ * frees its tensor memory and returns, and the solve returns DTS_ERR_TIMEOUT
+ * after that iteration. With on != 0 every later solve of p makes the flux-stage
+ * waits expect 16 bytes that no copy delivers, so they run out (no fault, no
+ * trap: the waits end by their bound); on = 0 restores normal operation, and
+ * the problem solves correctly again. Errors: DTS_ERR_INVALID_ARG (p NULL),
+ * DTS_ERR_STATE (not a tensor-core form), DTS_ERR_CUDA.
+ */
+dts_status dts_debug_poison_wait(dts_problem *p, int on);
 dts_status dts_moment_tables(int sn_order, int legendre_order, double *D, double *M);
 long long dts_subsweep_size(int nx, int ny, int nz, int S);
 

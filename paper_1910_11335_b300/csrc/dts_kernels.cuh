@@ -18,6 +18,29 @@
 
 namespace dts {
 
+// ---------------------------------------------------------------------------
+// Index checks of the DTS_DEBUG_BOUNDS build. Before a kernel touches a region
+// of a global buffer it checks the region's end against the buffer's size (an
+// element count carried in the kernel's parameters); a region that does not
+// fit is skipped (loads read nothing, stores are dropped) and the first failing
+// site is recorded in bounds_word as (site << 48) | (end offset, low 48 bits).
+// The host reads the word after every source iteration and returns
+// DTS_ERR_INTERNAL. Each translation unit has its own word. In the normal build
+// DTS_FITS is the constant true and the checks compile away.
+// ---------------------------------------------------------------------------
+#ifdef DTS_DEBUG_BOUNDS
+static __device__ unsigned long long bounds_word;
+__device__ __forceinline__ bool fits(size_t end, size_t size, unsigned site)
+{
+    if (end <= size) return true;
+    atomicCAS(&bounds_word, 0ull, ((unsigned long long)site << 48) | (end & 0xffffffffffffull));
+    return false;
+}
+#define DTS_FITS(end, size, site) ::dts::fits((size_t)(end), (size_t)(size), (site))
+#else
+#define DTS_FITS(end, size, site) true
+#endif
+
 constexpr int kSweepThreads = 256;
 constexpr int kRedThreads = 256;
 constexpr int kPushRing = 4;   // widest downscatter band of the FP32 push kernels (W <= 4)
@@ -139,6 +162,8 @@ struct SweepParams {
     R* zf;
     const int* active;             // [B]
     double* leak;                  // [B][8][NT] leakage of each (source, octant, tile) sweep, or null
+    // element counts of the buffers above (checked in the DTS_DEBUG_BOUNDS build)
+    size_t n_stage_tiles, n_T, n_sigt, n_part, n_xf, n_yf, n_zf, n_leak;
 };
 
 template <typename R, int NDO, int K>
@@ -778,6 +803,29 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     const int NTKB = p.NT * K * BV;                 // stride between sources (fits: checked on the host)
     const float* Tbase = p.T + ((size_t)b0 * p.NT + tile) * (size_t)(K * BV);
     float* obase = p.part + (((size_t)oct * p.B + b0) * p.NT + tile) * (size_t)(K * BV);
+#ifdef DTS_DEBUG_BOUNDS
+    {
+        // every region the warp touches: sigma_t and the faces of the tile, the lanes' rows
+        const int bl_ = lane / NDO, d_ = lane - bl_ * NDO;
+        const bool src_ = lane < NL && (okmask >> bl_ & 1u);
+        const size_t og_ = (size_t)oct * ngrp + grp;
+        bool ok = tx < p.NTx && ty < p.NTy && tz < p.NTz && b0 + nb <= p.B;
+        ok = DTS_FITS((size_t)(tile + 1) * BV, p.n_sigt, 2) && ok;
+        ok = DTS_FITS(((og_ * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * fxn + fxn) * 32, p.n_xf, 3) && ok;
+        ok = DTS_FITS(((og_ * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * fyn + fyn) * 32, p.n_yf, 4) && ok;
+        ok = DTS_FITS(((og_ * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * fzn + fzn) * 32, p.n_zf, 5) && ok;
+        if (src_) {
+            const size_t row = ((((size_t)(b0 + bl_) * 8 + oct) * p.NT + tile) * NDO + d_) * BV;
+            if (PSI) ok = DTS_FITS(row + BV, p.n_part, 6) && ok;
+            if (QIN) ok = DTS_FITS(row + BV, p.n_T, 7) && ok;
+            if (!QIN) ok = DTS_FITS(((size_t)(b0 + bl_) * p.NT + tile + 1) * (size_t)(K * BV), p.n_T, 8) && ok;
+            if (!PSI)
+                ok = DTS_FITS((((size_t)oct * p.B + b0 + bl_) * p.NT + tile + 1) * (size_t)(K * BV), p.n_part, 9) && ok;
+            if (d_ == 0 && p.leak) ok = DTS_FITS(((size_t)(b0 + bl_) * 8 + oct) * p.NT + tile + 1, p.n_leak, 10) && ok;
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+    }
+#endif
 
     // cp.async chunks of one line: u -> (source il, moment k, quad h)
     auto chunk = [&](int c, int& src, int& dst) {
@@ -1070,6 +1118,7 @@ __global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float>
     bid /= cnt;
     const int oct = bid & 7, grp = bid >> 3, b0 = grp * S::SB;
     // the loads that depend on nothing else go first: tile, lane operator row, source flags
+    if (!DTS_FITS(s0 + tl + 1, p.n_stage_tiles, 1)) return;
     const unsigned pk = p.stage_tiles[s0 + tl];
     const int lane = threadIdx.x, d = lane % NDO;
     const bool dl = lane < S::NL;
@@ -1152,6 +1201,8 @@ struct RedParams {
     const int* active;
     double vol;
     double* blk;               // [B][nblk][4]
+    // element counts of part, T, F, phi00, sigs and blk (checked in the DTS_DEBUG_BOUNDS build)
+    size_t n_part, n_T, n_F, n_phi00, n_sigs, n_blk;
 };
 
 template <typename R, int K>
@@ -1413,10 +1464,23 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_psi(const RedParams<f
     __shared__ double red[32];
     const int b = blockIdx.y;
     const int c2 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
-    const bool live = p.active[b] != 0 && c2 < p.NC;
     const int tile = c2 / p.TV, c = c2 - tile * p.TV;
     const size_t ostride = (size_t)p.NT * NDO * p.TV;
     const size_t pofs = (size_t)b * 8 * ostride + (size_t)tile * NDO * p.TV + c;
+    bool live = p.active[b] != 0 && c2 < p.NC;
+#ifdef DTS_DEBUG_BOUNDS
+    if (live) {   // the pair of cells' regions in every buffer
+        const size_t base = ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
+        bool ok = DTS_FITS(pofs + 7 * ostride + (size_t)(NDO - 1) * p.TV + 2, p.n_part, 30);
+        ok = DTS_FITS(base + (size_t)(K - 1) * p.TV + 2, p.n_T, 31) && ok;
+        ok = DTS_FITS((size_t)p.ctl[1] * p.Fstride + base + (size_t)(K - 1) * p.TV + 2, p.n_F, 32) && ok;
+        ok = DTS_FITS((size_t)b * p.NC + c2 + 2, p.n_phi00, 33) && ok;
+        ok = DTS_FITS((size_t)l_of_k(K - 1) * p.NC + c2 + 2, p.n_sigs, 34) && ok;
+        ok = DTS_FITS((size_t)c2 + 2, (size_t)p.NC, 35) && ok;
+        live = ok;
+    }
+    if (!DTS_FITS(((size_t)b * gridDim.x + blockIdx.x + 1) * 4, p.n_blk, 36)) return;   // uniform per block
+#endif
     // the first octant's fluxes are in flight while the block loads its moment operator
     if (live) psi_issue_first<NDO>(p.part + pofs, p.TV, stg + threadIdx.x);
     load_dpairs<NDO, K>(Dp, Dt);
@@ -1467,10 +1531,15 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_psi(const RedParams<f
 // per source: residual = sqrt(sum dphi^2 / sum phi^2), balance terms and the
 // leakage of the last sweep from its nleak (octant, tile) slots; fixed
 // summation order, so the results do not depend on the order the CTAs ran in
-__global__ void k_resid_final(const double* blk, int nblk, const double* leak, int nleak, double* status)
+__global__ void k_resid_final(const double* blk, int nblk, const double* leak, int nleak, double* status,
+                              size_t n_blk, size_t n_leak, size_t n_status)
 {
     __shared__ double red[32];
     const int b = blockIdx.x;
+    // uniform per block (DTS_DEBUG_BOUNDS build; constant true otherwise)
+    if (!(DTS_FITS(((size_t)b + 1) * nblk * 4, n_blk, 40) && DTS_FITS(((size_t)b + 1) * nleak, n_leak, 41) &&
+          DTS_FITS(((size_t)b + 1) * 4, n_status, 42)))
+        return;
     double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
         const double* o = blk + ((size_t)b * nblk + i) * 4;
@@ -1560,6 +1629,36 @@ __global__ void k_group_init(size_t total, const R* F, R* T)
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < total) T[i] = F[i];
 }
+
+// T = F[slot] + sigma_s phi_guess at the start of a group, and the scalar flux the first
+// iteration's residual is measured against = the guess (dts_set_initial_guess): the guess is
+// member b's collided moments [B][G][K][V] in natural voxel order, zeros for a member without
+// one (which gives exactly T = F, phi = 0). F and T tile-ordered [B][NT][K][TV].
+template <typename R>
+__global__ void k_guess_source(const CellParams c, const double* __restrict__ guess, int g, const R* __restrict__ F,
+                               const R* __restrict__ sigs, R* __restrict__ T, double* __restrict__ phi00, int V)
+{
+    const int ct = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (ct >= c.NC) return;
+    const int tile = ct / c.TV, cl = ct - tile * c.TV;
+    const size_t base = ((size_t)b * c.NT + tile) * (size_t)(c.K * c.TV) + cl;
+    if (c.mat_t[ct] < 0) {   // padding: no source, no flux
+        for (int k = 0; k < c.K; ++k) T[base + (size_t)k * c.TV] = F[base + (size_t)k * c.TV];
+        phi00[(size_t)b * c.NC + ct] = 0.0;
+        return;
+    }
+    const int v = tiled_to_natural(c, ct, nullptr);
+    const double* gb = guess + ((size_t)b * c.G + g) * (size_t)c.K * V + v;
+    for (int k = 0; k < c.K; ++k) {
+        const double ph = gb[(size_t)k * V];
+        T[base + (size_t)k * c.TV] =
+            (R)((double)F[base + (size_t)k * c.TV] + (double)sigs[(size_t)l_of_k(k) * c.NC + ct] * ph);
+        if (k == 0) phi00[(size_t)b * c.NC + ct] = ph;
+    }
+}
+
+// one bounds check of a region of n elements, failing when plant != 0; touches no memory
+__global__ void k_bounds_selftest(int plant, size_t n) { (void)DTS_FITS(plant ? n + 1 : n, n, 63); }
 
 __global__ void k_set_ctl(int* ctl, int g, int slot)
 {

@@ -15,7 +15,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -60,6 +62,10 @@ __attribute__((visibility("hidden"))) void dts_internal_set_thread_error(const c
 struct dts_problem {
     dts_problem_desc d{};
     std::string err = "no error";
+    dts_iteration_fn on_iter = nullptr;   // per-iteration progress callback and its argument
+    void* on_iter_user = nullptr;
+    double* guess = nullptr;              // initial guess [B][G][K][V] (dts_set_initial_guess), or null
+    void* guess_T = nullptr;              // tensor-core forms: the group's first T [B][NT][K][TV] (FP32)
     int V = 0, G = 0, L = 0, K = 0, nd = 0, ndo = 0, B = 0;
     int TX = 0, TY = 0, TZ = 0, TV = 0, NTx = 0, NTy = 0, NTz = 0, NT = 0, NC = 0;
     int n_stages = 0, nsub = 0, n_mat = 0, W = 0, nblk = 0, n_sm = 148;
@@ -75,6 +81,7 @@ struct dts_problem {
     float* Mop = nullptr;             // operator parts M' = 4 pi M, [2][NP][16]
     float* Dop = nullptr;             // Eq. 3 operator parts D, [2][16][N_d] (N_d a multiple of 16)
     int* dev_err = nullptr;           // device error word of the bounded waits
+    int* dev_poison = nullptr;        // dts_debug_poison_wait's flag (tensor-core forms)
     int* h_err = nullptr;             // pinned copy, read after every iteration
     size_t rsz = 8;                   // sizeof(R)
     std::vector<int> stage_off_h;     // [n_stages+1]
@@ -82,6 +89,7 @@ struct dts_problem {
     std::vector<double> sigma_s_h;    // kept for the band width
     // device buffers
     std::vector<void*> allocs;
+    std::map<const void*, size_t> alloc_bytes;   // size of every live allocation (bounds checks)
     unsigned *stage_tiles = nullptr, *diag_cells = nullptr;
     int *stage_off = nullptr, *diag_off = nullptr;
     void *Mt = nullptr, *Dt = nullptr, *At = nullptr;
@@ -188,6 +196,7 @@ dts_status dalloc(dts_problem* p, void** ptr, size_t bytes)
         return fail(p, e == cudaErrorMemoryAllocation ? DTS_ERR_OOM : DTS_ERR_CUDA, buf);
     }
     p->allocs.push_back(*ptr);
+    p->alloc_bytes[*ptr] = bytes;
     return DTS_OK;
 }
 
@@ -202,8 +211,45 @@ void dfree(dts_problem* p, void* ptr)
     if (!ptr) return;
     auto it = std::find(p->allocs.begin(), p->allocs.end(), ptr);
     if (it != p->allocs.end()) p->allocs.erase(it);
+    p->alloc_bytes.erase(ptr);
     cudaFree(ptr);
 }
+
+// element count of a buffer allocated by dalloc (0 for a null or foreign pointer); the kernels'
+// parameters carry these for the checks of the DTS_DEBUG_BOUNDS build
+template <typename T>
+size_t count_of(const dts_problem* p, const void* ptr)
+{
+    auto it = p->alloc_bytes.find(ptr);
+    return it == p->alloc_bytes.end() ? 0 : it->second / sizeof(T);
+}
+
+#ifdef DTS_DEBUG_BOUNDS
+// the first failed bounds check of this unit's kernels or the tensor-core unit's, read and
+// cleared (0: none); called with the solve's kernels complete
+unsigned long long take_bounds_word()
+{
+    unsigned long long w = 0, z = 0;
+    cudaMemcpyFromSymbol(&w, bounds_word, sizeof w);
+    cudaMemcpyToSymbol(bounds_word, &z, sizeof z);
+    const unsigned long long w2 = dts_internal_tc_bounds_take();
+    return w ? w : w2;
+}
+
+std::string bounds_message(unsigned long long w)
+{
+    const unsigned site = (unsigned)(w >> 48);
+    const char* where = site <= 10   ? "k_sweep_batch"
+                        : site < 30  ? "k_moments_q"
+                        : site < 40  ? "k_reduce_psi"
+                        : site < 63  ? "k_resid_final"
+                                     : "dts_debug_bounds_selftest";
+    char buf[160];
+    snprintf(buf, sizeof buf, "bounds check failed in %s: site %u, region end %llu beyond its buffer", where,
+             site, (unsigned long long)(w & 0xffffffffffffull));
+    return buf;
+}
+#endif
 
 bool isfin(double x) { return std::isfinite(x); }
 
@@ -548,13 +594,16 @@ CellParams cell_params(const dts_problem* p)
 // arguments of k_moments_q: init = 1 forms Q = M F of the group's fixed source (phi = 0)
 QParams q_params(const dts_problem* p, int init)
 {
-    QParams q;
+    QParams q{};
     q.B = p->B; q.NT = p->NT; q.TV = p->TV; q.NC = p->NC; q.nitems = p->B * p->NT; q.init = init;
     q.psi = (const float*)p->part; q.Q = (float*)p->Qbuf; q.phi00 = p->phi00;
     q.F = (const float*)p->F; q.Fstride = p->Fstride; q.ctl = p->ctl;
     q.sigs = (const float*)p->sigs; q.sigt = (const float*)p->sigt_r; q.mat_t = p->mat_t;
     q.active = p->active; q.Dt = (const float*)p->Dt; q.Mop = p->Mop; q.Dop = p->Dop;
-    q.vol = p->d.dx * p->d.dy * p->d.dz; q.blk = p->blk; q.err = p->dev_err;
+    q.vol = p->d.dx * p->d.dy * p->d.dz; q.blk = p->blk; q.err = p->dev_err; q.poison = p->dev_poison;
+    q.n_psi = count_of<float>(p, p->part); q.n_Q = count_of<float>(p, p->Qbuf);
+    q.n_phi00 = count_of<double>(p, p->phi00); q.n_F = count_of<float>(p, p->F);
+    q.n_sigs = count_of<float>(p, p->sigs); q.n_blk = count_of<double>(p, p->blk);
     return q;
 }
 
@@ -572,6 +621,10 @@ dts_status record_sweep(dts_problem* p)
     sp.T = (const R*)(p->q_mode ? p->Qbuf : p->T); sp.sigt = (const R*)p->sigt_r; sp.part = (R*)p->part;
     sp.xf = (R*)p->xf; sp.yf = (R*)p->yf; sp.zf = (R*)p->zf;
     sp.active = p->active; sp.leak = p->leak;
+    sp.n_stage_tiles = count_of<unsigned>(p, p->stage_tiles); sp.n_T = count_of<R>(p, sp.T);
+    sp.n_sigt = count_of<R>(p, p->sigt_r); sp.n_part = count_of<R>(p, p->part);
+    sp.n_xf = count_of<R>(p, p->xf); sp.n_yf = count_of<R>(p, p->yf); sp.n_zf = count_of<R>(p, p->zf);
+    sp.n_leak = count_of<double>(p, p->leak);
     const size_t smem = sweep_smem(p);
     if constexpr (sizeof(R) == 4) {
         if (batch_tile(p)) {   // the batched kernel takes the stage's (first tile, count) directly
@@ -609,6 +662,9 @@ dts_status record_reduce(dts_problem* p)
     rp.sigt64 = p->sigt64; rp.sigt = (const R*)p->sigt_r;
     rp.mat_t = p->mat_t; rp.active = p->active; rp.vol = p->d.dx * p->d.dy * p->d.dz;
     rp.blk = p->blk;
+    rp.n_part = count_of<R>(p, p->part); rp.n_T = count_of<R>(p, p->T); rp.n_F = count_of<R>(p, p->F);
+    rp.n_phi00 = count_of<double>(p, p->phi00); rp.n_sigs = count_of<R>(p, p->sigs);
+    rp.n_blk = count_of<double>(p, p->blk);
     int nblk = p->nblk;
     if constexpr (sizeof(R) == 4) {
         if (p->q_mode) {        // moments from the angular fluxes, then Q = M T on the tensor cores
@@ -630,7 +686,9 @@ dts_status record_reduce(dts_problem* p)
     } else {
         reduce_fn<R>(p->K)<<<dim3(nblk, p->B), kRedThreads, 0, p->stream>>>(rp);
     }
-    k_resid_final<<<p->B, 1024, 0, p->stream>>>(p->blk, nblk, p->leak, 8 * p->NT, p->status);
+    k_resid_final<<<p->B, 1024, 0, p->stream>>>(p->blk, nblk, p->leak, 8 * p->NT, p->status,
+                                                count_of<double>(p, p->blk), count_of<double>(p, p->leak),
+                                                count_of<double>(p, p->status));
     p->graph_launches = p->n_stages + 2;
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(double) * 4 * p->B, cudaMemcpyDeviceToHost,
                        p->stream));
@@ -704,10 +762,26 @@ void launch_group_xs(dts_problem* p, int g)
                                              p->sigs0);
 }
 
-// T = F of the group's ring slot (phi = 0 before the first sweep): one device-to-device copy
+// T = F of the group's ring slot (phi = 0 before the first sweep): one device-to-device copy; with an
+// initial guess, T = F + sigma_s phi_guess and phi = phi_guess (tensor-core forms: Q = M T)
 template <typename R>
-dts_status launch_group_init(dts_problem* p, int slot)
+dts_status launch_group_init(dts_problem* p, int g, int slot)
 {
+    if (p->guess) {   // restart: T = F + sigma_s phi_guess, residual measured against the guess
+        R* T = p->q_mode ? (R*)p->guess_T : (R*)p->T;
+        k_guess_source<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(
+            cell_params(p), p->guess, g, (const R*)p->F + (size_t)slot * p->Fstride, (const R*)p->sigs, T,
+            p->phi00, p->V);
+        CK(cudaGetLastError());
+        if (p->q_mode) {   // Q = M T on the tensor cores, T in place of the fixed source
+            QParams q = q_params(p, 1);
+            q.F = (const float*)p->guess_T;
+            q.Fstride = 0;
+            q.n_F = count_of<float>(p, p->guess_T);
+            CK(dts_internal_q_launch(p->ndo, p->K, p->q_kind, q, p->q_grid, p->stream));
+        }
+        return DTS_OK;
+    }
     if (p->q_mode) {   // Q = M F on the tensor cores
         CK(dts_internal_q_launch(p->ndo, p->K, p->q_kind, q_params(p, 1), p->q_grid, p->stream));
         return DTS_OK;
@@ -789,6 +863,9 @@ struct SolveRun {
     dts_status start()
     {
         r_solve = nvtxRangeStartA("dts_solve");
+#ifdef DTS_DEBUG_BOUNDS
+        take_bounds_word();   // a word left by an earlier failure is not this solve's
+#endif
         TRY(ensure_ring(p));
         TRY(build_graph(p));
         if (p->q_mode) {
@@ -848,10 +925,10 @@ struct SolveRun {
         CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
         if (p->fp64) {
             launch_group_xs<double>(p, g);
-            TRY(launch_group_init<double>(p, slot));
+            TRY(launch_group_init<double>(p, g, slot));
         } else {
             launch_group_xs<float>(p, g);
-            TRY(launch_group_init<float>(p, slot));
+            TRY(launch_group_init<float>(p, g, slot));
         }
         CK(cudaGetLastError());
         n_active = B;
@@ -884,6 +961,9 @@ struct SolveRun {
         r_iter = 0;
         if (p->q_mode && *p->h_err)
             return fail(p, DTS_ERR_TIMEOUT, "k_moments_q: a bounded wait on a bulk copy or the tensor cores gave up");
+#ifdef DTS_DEBUG_BOUNDS
+        if (const unsigned long long w = take_bounds_word()) return fail(p, DTS_ERR_INTERNAL, bounds_message(w));
+#endif
         launches += p->graph_launches;
         sweep_launches += p->n_stages;
         {
@@ -923,6 +1003,13 @@ struct SolveRun {
         }
         if (changed && n_active > 0)
             CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+        if (p->on_iter) {
+            // this iteration's residual of every member, NaN where the member had stopped before it
+            std::vector<double> res(B, std::nan(""));
+            for (int b = 0; b < B; ++b)
+                if (p->iters[(size_t)b * G + g] == it) res[b] = p->resid[(size_t)b * G + g];
+            p->on_iter(p->on_iter_user, g, it, res.data(), B);
+        }
         return DTS_OK;
     }
 
@@ -1246,6 +1333,8 @@ dts_status create(const dts_problem_desc* desc, dts_problem* p)
         TRY(upload_qop(p, D, M));
         TRY(dalloc_t(p, &p->dev_err, 1));
         CK(cudaMemset(p->dev_err, 0, sizeof(int)));
+        TRY(dalloc_t(p, &p->dev_poison, 1));
+        CK(cudaMemset(p->dev_poison, 0, sizeof(int)));
         CK(cudaMallocHost((void**)&p->h_err, sizeof(int)));
         *p->h_err = 0;
     }
@@ -1496,7 +1585,10 @@ dts_status run_adjoint(dts_problem* p, int b)
                 adj<<<(unsigned)cnt * 8u, kSweepThreads, smem, p->stream>>>(sp, s);
             }
             rf<<<dim3(p->nblk, 1), kRedThreads, 0, p->stream>>>(rp);
-            k_resid_final<<<1, 256, 0, p->stream>>>(p->adj_blk, p->nblk, p->adj_leak, 1, p->adj_status);
+            k_resid_final<<<1, 256, 0, p->stream>>>(p->adj_blk, p->nblk, p->adj_leak, 1, p->adj_status,
+                                                    count_of<double>(p, p->adj_blk),
+                                                    count_of<double>(p, p->adj_leak),
+                                                    count_of<double>(p, p->adj_status));
             CK(cudaMemcpyAsync(p->h_status, p->adj_status, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                p->stream));
             CK(cudaStreamSynchronize(p->stream));
@@ -2008,6 +2100,70 @@ dts_status dts_get_adjoint_iterations(dts_problem* p, int32_t* out, size_t out_l
 
 const char* dts_last_error(const dts_problem* p) { return p ? p->err.c_str() : g_thread_error.c_str(); }
 
+dts_status dts_debug_bounds_selftest(int plant, int* is_debug_build)
+{
+#ifdef DTS_DEBUG_BOUNDS
+    if (is_debug_build) *is_debug_build = 1;
+    take_bounds_word();
+    k_bounds_selftest<<<1, 1>>>(plant, 1024);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(nullptr, DTS_ERR_CUDA, "selftest kernel failed");
+    if (const unsigned long long w = take_bounds_word()) return fail(nullptr, DTS_ERR_INTERNAL, bounds_message(w));
+    return DTS_OK;
+#else
+    (void)plant;
+    if (is_debug_build) *is_debug_build = 0;
+    return DTS_OK;
+#endif
+}
+
+dts_status dts_set_initial_guess(dts_problem* p, int batch_index, const double* moments, size_t len,
+                                 int is_device)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (batch_index < 0 || batch_index >= p->B) return fail(p, DTS_ERR_INVALID_ARG, "batch_index out of range");
+    const size_t n = (size_t)p->G * p->K * p->V;
+    DevGuard guard(p->d.device);
+    if (!moments) {   // clear: zeros are the default start exactly
+        if (p->guess)
+            CK(cudaMemsetAsync(p->guess + (size_t)batch_index * n, 0, n * sizeof(double), p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+        return DTS_OK;
+    }
+    if (len < n) return fail(p, DTS_ERR_INVALID_ARG, "moments: need G*K*V doubles");
+    if (!is_device)
+        for (size_t i = 0; i < n; ++i)
+            if (!isfin(moments[i])) return fail(p, DTS_ERR_INVALID_ARG, "moments: non-finite value");
+    if (!p->guess) {
+        TRY(dalloc_t(p, &p->guess, (size_t)p->B * n));
+        CK(cudaMemsetAsync(p->guess, 0, (size_t)p->B * n * sizeof(double), p->stream));
+    }
+    if (p->q_mode && !p->guess_T) TRY(dalloc(p, &p->guess_T, (size_t)p->B * p->NC * p->K * sizeof(float)));
+    CK(cudaMemcpyAsync(p->guess + (size_t)batch_index * n, moments, n * sizeof(double),
+                       is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    p->solved = false;
+    return DTS_OK;
+}
+
+dts_status dts_debug_poison_wait(dts_problem* p, int on)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->dev_poison) return fail(p, DTS_ERR_STATE, "only the tensor-core forms have device-side waits");
+    DevGuard guard(p->d.device);
+    const int v = on ? 1 : 0;
+    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaMemcpy(p->dev_poison, &v, sizeof v, cudaMemcpyHostToDevice));
+    return DTS_OK;
+}
+
+dts_status dts_set_iteration_callback(dts_problem* p, dts_iteration_fn fn, void* user)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    p->on_iter = fn;
+    p->on_iter_user = user;
+    return DTS_OK;
+}
+
 void dts_destroy_problem(dts_problem* p)
 {
     if (!p) return;
@@ -2060,10 +2216,67 @@ dts_status dts_moment_tables(int sn_order, int legendre_order, double* D, double
     return DTS_OK;
 }
 
+// The tuner's results, per process and (when a cache file is named) on disk. A file line is
+//   dts-tune-v1 <device name, blanks as '_'> <SMs> nx ny nz N L probe_batch precision tx ty tz rate
+// keyed by everything but the tile and the rate; lines that do not parse are ignored, and a
+// later line for the same key wins. New results are appended.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, std::tuple<int, int, int, double>> g_tune_mem;
+bool g_tune_path_set = false;   // dts_tune_cache_file was called (else DTS_TUNE_CACHE is read)
+std::string g_tune_path;
+
+std::string tune_path_locked()
+{
+    if (g_tune_path_set) return g_tune_path;
+    const char* e = std::getenv("DTS_TUNE_CACHE");
+    return e ? std::string(e) : std::string();
+}
+
+std::string tune_line_key(const std::string& dev, const std::vector<long long>& k)
+{
+    std::string out = "dts-tune-v1 " + dev;
+    for (long long v : k) out += " " + std::to_string(v);
+    return out;
+}
+
+// looks key up in the file at path; true and the entry when found
+bool tune_file_lookup(const std::string& path, const std::string& keyline, std::tuple<int, int, int, double>* hit)
+{
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    bool found = false;
+    char buf[512];
+    while (std::fgets(buf, sizeof buf, f)) {
+        std::string line(buf);
+        while (!line.empty() && (line.back() == '\n' || line.back() == '\r')) line.pop_back();
+        if (line.compare(0, keyline.size(), keyline) != 0 || line.size() <= keyline.size() ||
+            line[keyline.size()] != ' ')
+            continue;
+        int tx = 0, ty = 0, tz = 0;
+        double rate = 0.0;
+        char extra = 0;
+        if (std::sscanf(line.c_str() + keyline.size(), " %d %d %d %lf %c", &tx, &ty, &tz, &rate, &extra) == 4 &&
+            tx >= 1 && tx <= 64 && ty >= 1 && ty <= 64 && tz >= 1 && tz <= 64) {
+            *hit = std::make_tuple(tx, ty, tz, rate);
+            found = true;   // keep reading: a later line for the key wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+}  // namespace
+
+dts_status dts_tune_cache_file(const char* path)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_path_set = true;
+    g_tune_path = path ? std::string(path) : std::string();
+    return DTS_OK;
+}
+
 dts_status dts_tune_tile(dts_problem_desc* desc, double* best_updates_per_s)
 {
-    static std::mutex mu;
-    static std::map<std::vector<long long>, std::tuple<int, int, int, double>> cache;
     if (!desc) return fail(nullptr, DTS_ERR_INVALID_ARG, "desc is NULL");
     int nd = 0;
     {
@@ -2071,24 +2284,38 @@ dts_status dts_tune_tile(dts_problem_desc* desc, double* best_updates_per_s)
         if (dts_quadrature(desc->sn_order, a, b2, c, w, &nd) != DTS_OK)
             return fail(nullptr, DTS_ERR_INVALID_ARG, "sn_order must be 2, 4, 6 or 8");
     }
-    int dev_name_hash = 0;
+    std::string dev;
+    int n_sm = 0;
     {
         cudaDeviceProp prop;
         if (cudaGetDeviceProperties(&prop, desc->device) != cudaSuccess)
             return fail(nullptr, DTS_ERR_CUDA, "cannot query the device");
-        for (const char* q = prop.name; *q; ++q) dev_name_hash = dev_name_hash * 31 + *q;
+        for (const char* q = prop.name; *q; ++q) dev += (*q == ' ' || *q == '\t') ? '_' : *q;
+        n_sm = prop.multiProcessorCount;
     }
     const int probe_b = std::min(desc->batch, 16);
-    const std::vector<long long> key = {desc->nx, desc->ny, desc->nz, desc->sn_order, desc->legendre_order,
-                                        probe_b, (long long)desc->precision, desc->device, dev_name_hash};
+    const std::vector<long long> key = {n_sm, desc->nx, desc->ny, desc->nz, desc->sn_order, desc->legendre_order,
+                                        probe_b, (long long)desc->precision};
+    const std::string keyline = tune_line_key(dev, key);
+    std::vector<long long> mkey = key;
+    mkey.push_back((long long)std::hash<std::string>()(dev));
+    std::string path;
     {
-        std::lock_guard<std::mutex> lk(mu);
-        auto it = cache.find(key);
-        if (it != cache.end()) {
-            desc->tile_x = std::get<0>(it->second);
-            desc->tile_y = std::get<1>(it->second);
-            desc->tile_z = std::get<2>(it->second);
-            if (best_updates_per_s) *best_updates_per_s = std::get<3>(it->second);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_mem.find(mkey);
+        std::tuple<int, int, int, double> hit;
+        path = tune_path_locked();
+        bool found = it != g_tune_mem.end();
+        if (found) hit = it->second;
+        else if (!path.empty() && tune_file_lookup(path, keyline, &hit)) {
+            g_tune_mem[mkey] = hit;
+            found = true;
+        }
+        if (found) {
+            desc->tile_x = std::get<0>(hit);
+            desc->tile_y = std::get<1>(hit);
+            desc->tile_z = std::get<2>(hit);
+            if (best_updates_per_s) *best_updates_per_s = std::get<3>(hit);
             return DTS_OK;
         }
     }
@@ -2142,8 +2369,14 @@ dts_status dts_tune_tile(dts_problem_desc* desc, double* best_updates_per_s)
     desc->tile_y = best_t[1];
     desc->tile_z = best_t[2];
     if (best_updates_per_s) *best_updates_per_s = best;
-    std::lock_guard<std::mutex> lk(mu);
-    cache[key] = std::make_tuple(best_t[0], best_t[1], best_t[2], best);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_mem[mkey] = std::make_tuple(best_t[0], best_t[1], best_t[2], best);
+    if (!path.empty()) {
+        if (FILE* f = std::fopen(path.c_str(), "a")) {   // best effort: an unwritable file is skipped
+            std::fprintf(f, "%s %d %d %d %.6e\n", keyline.c_str(), best_t[0], best_t[1], best_t[2], best);
+            std::fclose(f);
+        }
+    }
     return DTS_OK;
 }
 

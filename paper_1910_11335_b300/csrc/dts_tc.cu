@@ -130,3 +130,15 @@ size_t dts_internal_qsweep_smem(int ndo)
     }
     return 0;
 }
+
+unsigned long long dts_internal_tc_bounds_take()
+{
+#ifdef DTS_DEBUG_BOUNDS
+    unsigned long long w = 0, z = 0;
+    cudaMemcpyFromSymbol(&w, dts::bounds_word, sizeof w);
+    cudaMemcpyToSymbol(dts::bounds_word, &z, sizeof z);
+    return w;
+#else
+    return 0;
+#endif
+}

@@ -55,21 +55,45 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
                  : "memory");
 }
 
-// Bounded wait on an mbarrier phase: false when the phase did not complete
-// within the limit (the caller records an error and stops using the barrier).
+// plain arrival (completes a phase without bytes: a copy skipped by a failed bounds check)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: false when the phase did not complete within about a second
+// (the caller records an error and stops using the barrier). Each try suspends for at most about
+// 20 us; the global timer bounds the total, and an iteration cap bounds it should the timer stall.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 {
-    constexpr int kLimit = 1 << 22;   // try_wait suspends for a while per call: seconds in total
-    for (int i = 0; i < kLimit; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
+    constexpr uint32_t kHintNs = 20000;
+    constexpr uint64_t kLimitNs = 1000000000ull;
+    constexpr int kMaxTries = 1 << 20;
+    if (mbar_try(bar, parity, kHintNs)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (int i = 0; i < kMaxTries; ++i) {
+        if (mbar_try(bar, parity, kHintNs)) return true;
+        if (globaltimer_ns() - t0 > kLimitNs) return false;
     }
     return false;
 }
@@ -198,6 +222,9 @@ struct QParams {
     double vol;
     double* blk;                 // [B][NT][4] residual and balance partials per item
     int* err;                    // device error word (1: a bounded wait gave up)
+    const int* poison;           // test hook (dts_debug_poison_wait): nonzero makes the flux-stage waits run out
+    // element counts of the buffers above (checked in the DTS_DEBUG_BOUNDS build)
+    size_t n_psi, n_Q, n_phi00, n_F, n_sigs, n_blk;
 };
 
 template <int NDO, int K, int MODE>
@@ -295,7 +322,10 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
     uint32_t* slot = reinterpret_cast<uint32_t*>(qsm + S::oSlot);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31, c = t;
 
+    // bytes of a flux stage; the poison hook adds 16 that no copy delivers, so the stage's wait runs out
+    __shared__ uint32_t stage_tx;
     if (t == 0) {
+        stage_tx = (uint32_t)S::PSI_STAGE + ((!p.init && p.poison && *p.poison) ? 16u : 0u);
         mbar_init(full, 1);
         mbar_init(mbar, 1);
         mbar_init(mbar1, 1);
@@ -345,7 +375,11 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
     auto issue = [&](int it) {   // one item's psi: 8 octant blocks of ND/8 x 128 floats
         const int b = it / p.NT, tile = it - b * p.NT;
         constexpr uint32_t ob = NDO * kQCells * 4;
-        mbar_expect_tx(full, (uint32_t)S::PSI_STAGE);
+        if (!DTS_FITS((((size_t)b * 8 + 7) * p.NT + tile + 1) * (size_t)(NDO * kQCells), p.n_psi, 20)) {
+            mbar_arrive(full);
+            return;
+        }
+        mbar_expect_tx(full, stage_tx);   // set once per CTA, above
         for (int o = 0; o < 8; ++o)
             bulk_load(reinterpret_cast<unsigned char*>(spsi) + o * ob,
                       p.psi + (((size_t)b * 8 + o) * p.NT + tile) * (size_t)(NDO * kQCells), ob, full);
@@ -368,16 +402,24 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
         int mat = -1;
         double old = 0.0;
         double* ph = p.phi00 + (size_t)b * p.NC + ct;
+        // the item's regions (DTS_DEBUG_BOUNDS build; constant true otherwise)
+        const bool okF = DTS_FITS((size_t)p.ctl[1] * p.Fstride + ((size_t)b * p.NT + tile + 1) * (size_t)(K * p.TV),
+                                  p.n_F, 21);
+        const bool okS = DTS_FITS((size_t)(NLEG - 1) * p.NC + ct + 1, p.n_sigs, 22) &&
+                         DTS_FITS((size_t)ct + 1, (size_t)p.NC, 26);
+        const bool okP = DTS_FITS((size_t)b * p.NC + ct + 1, p.n_phi00, 23);
+        const bool okQ = DTS_FITS((((size_t)b * 8 + 7) * p.NT + tile + 1) * (size_t)(NDO * p.TV), p.n_Q, 24);
+        const bool okB = DTS_FITS(((size_t)b * p.NT + tile + 1) * 4, p.n_blk, 25);
         auto load_cell = [&]() {
             const float* __restrict__ F = p.F + (size_t)p.ctl[1] * p.Fstride +
                                           ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;
 #pragma unroll
-            for (int k = 0; k < K; ++k) f[k] = F[(size_t)k * p.TV];
+            for (int k = 0; k < K; ++k) f[k] = okF ? F[(size_t)k * p.TV] : 0.f;
 #pragma unroll
-            for (int l = 0; l < NLEG; ++l) sl[l] = p.sigs[(size_t)l * p.NC + ct];
-            stc = p.sigt[ct];
-            mat = p.mat_t[ct];
-            if (!p.init) old = *ph;
+            for (int l = 0; l < NLEG; ++l) sl[l] = okS ? p.sigs[(size_t)l * p.NC + ct] : 0.f;
+            stc = okS ? p.sigt[ct] : 0.f;
+            mat = okS ? p.mat_t[ct] : -1;
+            if (!p.init && okP) old = *ph;
         };
         float T[K];
         RedTail tl;
@@ -488,13 +530,13 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
 #pragma unroll
             for (int o = 0; o < 8; ++o) s0.add(os[o]);
             if (mat < 0) {
-                *ph = 0.0;
+                if (okP) *ph = 0.0;
 #pragma unroll
                 for (int k = 0; k < K; ++k) T[k] = 0.f;
             } else {
                 const double phi = s0.value();
                 T[0] = tl.cell(s0, phi, old, f[0], sl[0], stc);
-                *ph = phi;
+                if (okP) *ph = phi;
 #pragma unroll
                 for (int k = 1; k < K; ++k) T[k] = fmaf(sl[l_of_k(k)], mk[k], f[k]);
             }
@@ -579,11 +621,11 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
                 for (int i = 0; i < 8; ++i) {
                     constexpr int nb = 8 * ch;
                     const int n = nb + i;
-                    if (n < ND) qb[(size_t)(n / NDO) * ostr + (n % NDO) * p.TV] = __uint_as_float(r[i]);
+                    if (n < ND && okQ) qb[(size_t)(n / NDO) * ostr + (n % NDO) * p.TV] = __uint_as_float(r[i]);
                 }
             });
         }
-        if (!p.init && t < 4) {
+        if (!p.init && t < 4 && okB) {
             double a = 0.0;
 #pragma unroll
             for (int i = 0; i < kQThreads / 32; ++i) a += red[i * 4 + t];

@@ -22,3 +22,6 @@ cudaError_t dts_internal_q_launch(int ndo, int K, int mode, const dts::QParams& 
 // the batched sweep that reads the per-direction source Q (8 x 4 x 4 tiles) and its shared memory
 dts_internal_batch_fn dts_internal_qsweep_fn(int ndo);
 size_t dts_internal_qsweep_smem(int ndo);
+// the first failed bounds check of this unit's kernels (DTS_DEBUG_BOUNDS build), read and cleared;
+// always 0 in the normal build
+unsigned long long dts_internal_tc_bounds_take();

@@ -15,7 +15,9 @@ import numpy as np
 from . import inputs
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libdts.so")
+#: DTS_DEBUG_BOUNDS=1 in the environment loads the bounds-checked build instead
+DEBUG_BOUNDS = os.environ.get("DTS_DEBUG_BOUNDS", "") == "1"
+LIB_PATH = os.path.join(_PKG, "libdts_debug.so" if DEBUG_BOUNDS else "libdts.so")
 
 DTS_OK, DTS_ERR_INVALID_ARG, DTS_ERR_STATE, DTS_ERR_OOM, DTS_ERR_CUDA, DTS_ERR_NOT_CONVERGED, \
     DTS_ERR_TIMEOUT, DTS_ERR_INTERNAL = range(8)
@@ -54,6 +56,10 @@ class SolveStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+#: dts_iteration_fn: (user, group, iteration, residuals[batch], batch)
+IterationFn = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int)
+
+
 class DTSError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_status_name(status)}: {msg}")
@@ -69,7 +75,8 @@ EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_sol
            "dts_version", "dts_quadrature", "dts_moment_tables", "dts_subsweep_size",
            "dts_sweep_once_noalloc", "dts_solve_adjoint", "dts_get_adjoint_iterations",
            "dts_tune_tile", "dts_set_source_cones", "dts_get_dose", "dts_debug_fail_allocation",
-           "dts_solve_many")
+           "dts_solve_many", "dts_tune_cache_file", "dts_set_iteration_callback",
+           "dts_debug_bounds_selftest", "dts_set_initial_guess", "dts_debug_poison_wait")
 
 
 def lib():
@@ -79,7 +86,8 @@ def lib():
         return _lib
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"{LIB_PATH} is missing: build it with "
-                           "`python -m paper_1910_11335_b300.build`")
+                           "`python -m paper_1910_11335_b300.build`"
+                           + (" --debug-bounds" if DEBUG_BOUNDS else ""))
     L = C.CDLL(LIB_PATH)
     pp = C.POINTER(C.c_void_p)
     sig = {
@@ -104,6 +112,11 @@ def lib():
         "dts_moment_tables": ([C.c_int, C.c_int, _dp, _dp], C.c_int),
         "dts_subsweep_size": ([C.c_int, C.c_int, C.c_int, C.c_int], C.c_longlong),
         "dts_tune_tile": ([C.POINTER(ProblemDesc), C.POINTER(C.c_double)], C.c_int),
+        "dts_tune_cache_file": ([C.c_char_p], C.c_int),
+        "dts_debug_bounds_selftest": ([C.c_int, C.POINTER(C.c_int)], C.c_int),
+        "dts_set_initial_guess": ([C.c_void_p, C.c_int, _dp, C.c_size_t, C.c_int], C.c_int),
+        "dts_debug_poison_wait": ([C.c_void_p, C.c_int], C.c_int),
+        "dts_set_iteration_callback": ([C.c_void_p, IterationFn, C.c_void_p], C.c_int),
         "dts_solve_adjoint": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_int], C.c_int),
         "dts_get_adjoint_iterations": ([C.c_void_p, _ip, C.c_size_t], C.c_int),
@@ -188,10 +201,23 @@ def sweep_once_noalloc(nx, ny, nz, dx, dy, dz, sn_order, legendre_order, src_mom
                                         stream))
 
 
+def debug_bounds_selftest(plant: bool):
+    """dts_debug_bounds_selftest: (is_debug_build, status, message)."""
+    flag = C.c_int(-1)
+    st = lib().dts_debug_bounds_selftest(int(bool(plant)), C.byref(flag))
+    return flag.value == 1, st, lib().dts_last_error(None).decode()
+
+
 def debug_fail_allocation(after: int):
     """Test hook: the device allocation after `after` more successful ones fails once as
     out-of-memory (DTS_ERR_OOM); a negative value disarms it."""
     lib().dts_debug_fail_allocation(int(after))
+
+
+def tune_cache_file(path: Optional[str]):
+    """Name the tile tuner's cache file for this process (None turns it off;
+    until called, the DTS_TUNE_CACHE environment variable names it)."""
+    _check(lib().dts_tune_cache_file(None if path is None else os.fsencode(path)))
 
 
 def tune_tile(w: inputs.Workload, precision=PREC_FP64, batch=None, device=0):
@@ -266,6 +292,35 @@ class Problem:
                        (C.c_double * 3)(*src.axis), src.half_angle, _dptr(sp), src.aperture,
                        (C.c_double * 3)(*src.normal), src.half_azimuth, src.half_polar)
         _check(lib().dts_set_source(self._h, b, C.byref(s)), self._h)
+
+    def set_initial_guess(self, b: int, moments):
+        """Start member b's source iteration in every group from moments [G][K][V]
+        (as moments() returns per group); None clears it (dts_set_initial_guess)."""
+        if moments is None:
+            _check(lib().dts_set_initial_guess(self._h, b, None, 0, 0), self._h)
+            return
+        m = np.ascontiguousarray(moments, dtype=np.float64).reshape(-1)
+        _check(lib().dts_set_initial_guess(self._h, b, _dptr(m), m.size, 0), self._h)
+
+    def debug_poison_wait(self, on: bool):
+        """Make the tensor-core moment kernel's flux-stage waits run out (their
+        bound ends them; the solve returns DTS_ERR_TIMEOUT), or stop doing so."""
+        _check(lib().dts_debug_poison_wait(self._h, int(bool(on))), self._h)
+
+    def on_iteration(self, fn):
+        """Call fn(group, iteration, residuals) after every source iteration of a
+        solve (residuals: numpy array [batch], NaN for members already stopped);
+        None turns it off (dts_set_iteration_callback)."""
+        if fn is None:
+            self._iter_cb = None
+            _check(lib().dts_set_iteration_callback(self._h, C.cast(None, IterationFn), None), self._h)
+            return
+
+        def tramp(_user, g, it, res, n):
+            fn(g, it, np.ctypeslib.as_array(res, shape=(n,)).copy())
+
+        self._iter_cb = IterationFn(tramp)   # kept alive with the problem
+        _check(lib().dts_set_iteration_callback(self._h, self._iter_cb, None), self._h)
 
     # solve
     def solve(self, allow_not_converged: bool = False) -> SolveStats:

@@ -1,6 +1,8 @@
-"""Failure paths, injected on the host (no device fault, hang or trap): an
-out-of-memory device allocation turns into DTS_ERR_OOM, the failed call
-releases what it had allocated, and the library keeps working afterwards."""
+"""Failure paths, with no device fault, hang or trap: an out-of-memory device
+allocation (injected on the host) turns into DTS_ERR_OOM, the failed call
+releases what it had allocated, and the library keeps working afterwards; a
+bounded device wait made to run out (a byte count no copy delivers) turns into
+DTS_ERR_TIMEOUT after about a second, and the problem then solves correctly."""
 import numpy as np
 import pytest
 
@@ -31,3 +33,26 @@ def test_injected_allocation_failure_is_oom_and_leaks_nothing(ora, after):
     p.solve()
     r = ora.solve(w, tol=0.0, max_iters=3)
     assert rel_max(p.fluence(0, dts.TOTAL), r.total) <= TOL_FP64
+
+
+def test_bounded_wait_runs_out_and_the_problem_recovers():
+    import time
+    w = inputs.small_cone(10, 9, 8, n_groups=2, sn_order=8, legendre_order=3, n_sources=2)
+    ref = dts.problem_from_workload(w, precision=dts.PREC_FP32_SPLITBF16, tol=0.0, max_iters=3)
+    ref.solve(allow_not_converged=True)
+    p = dts.problem_from_workload(w, precision=dts.PREC_FP32_SPLITBF16, tol=0.0, max_iters=3)
+    p.debug_poison_wait(True)
+    t0 = time.perf_counter()
+    with pytest.raises(dts.DTSError) as e:
+        p.solve()
+    dt = time.perf_counter() - t0
+    assert e.value.status == dts.DTS_ERR_TIMEOUT and "bounded wait" in str(e.value)
+    assert dt < 30.0, dt   # each wait ends by its bound (about a second)
+    p.debug_poison_wait(False)
+    p.solve(allow_not_converged=True)
+    for b in range(2):
+        assert np.array_equal(p.fluence(b, dts.TOTAL), ref.fluence(b, dts.TOTAL))
+    q = dts.problem_from_workload(w, precision=dts.PREC_FP32, tol=0.0, max_iters=1)
+    with pytest.raises(dts.DTSError) as e:
+        q.debug_poison_wait(True)
+    assert e.value.status == dts.DTS_ERR_STATE
