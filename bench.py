@@ -216,12 +216,12 @@ MEASURED = {
     "k_sweep_batch": {"inst_per_update": 2.819, "dram_over_design": 1.147, "fma_pipe": 0.2484, "block": "sweep"},
     "k_moments_q": {"inst_per_update": 0.553, "dram_over_design": 0.999, "fma_pipe": 0.1422,
                     "tensor_pipe": 0.0565, "block": "tc"},
-    "k_reduce_psi": {"inst_per_update": 0.603, "dram_over_design": 1.017, "fma_pipe": 0.4856, "block": "reduce_psi"},
+    "k_reduce_psi": {"inst_per_update": 0.603, "dram_over_design": 1.016, "fma_pipe": 0.4854, "block": "reduce_psi"},
 }
 MEASURED_SHA256 = {
     "sweep": "2726b7153ae507306c2f7a808f709fdadd09e7f6f0a52cf1621b44781ce99b1e",
     "tc": "0988329edd12038edf38ea01ef388c0a3090f5df8396a1ac580b1e1181da1a84",
-    "reduce_psi": "d9572bff6a77c2dd828c58bfcd20e651c3b435258948820752e8abd84880557a",
+    "reduce_psi": "c5c4d10f1f70348862cd9f75bb082a02029c31cdbca2759d5c94ba75647bc417",
 }
 
 

@@ -1201,8 +1201,11 @@ struct RedParams {
     const int* active;
     double vol;
     double* blk;               // [B][nblk][4]
-    // element counts of part, T, F, phi00, sigs and blk (checked in the DTS_DEBUG_BOUNDS build)
+#ifdef DTS_DEBUG_BOUNDS
+    // element counts of part, T, F, phi00, sigs and blk (checked in the DTS_DEBUG_BOUNDS build only,
+    // so that the normal build's parameters stay as they were)
     size_t n_part, n_T, n_F, n_phi00, n_sigs, n_blk;
+#endif
 };
 
 template <typename R, int K>
@@ -1464,10 +1467,14 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_psi(const RedParams<f
     __shared__ double red[32];
     const int b = blockIdx.y;
     const int c2 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+#ifdef DTS_DEBUG_BOUNDS
+    bool live = p.active[b] != 0 && c2 < p.NC;
+#else
+    const bool live = p.active[b] != 0 && c2 < p.NC;
+#endif
     const int tile = c2 / p.TV, c = c2 - tile * p.TV;
     const size_t ostride = (size_t)p.NT * NDO * p.TV;
     const size_t pofs = (size_t)b * 8 * ostride + (size_t)tile * NDO * p.TV + c;
-    bool live = p.active[b] != 0 && c2 < p.NC;
 #ifdef DTS_DEBUG_BOUNDS
     if (live) {   // the pair of cells' regions in every buffer
         const size_t base = ((size_t)b * p.NT + tile) * (size_t)(K * p.TV) + c;

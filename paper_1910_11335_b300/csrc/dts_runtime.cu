@@ -662,9 +662,11 @@ dts_status record_reduce(dts_problem* p)
     rp.sigt64 = p->sigt64; rp.sigt = (const R*)p->sigt_r;
     rp.mat_t = p->mat_t; rp.active = p->active; rp.vol = p->d.dx * p->d.dy * p->d.dz;
     rp.blk = p->blk;
+#ifdef DTS_DEBUG_BOUNDS
     rp.n_part = count_of<R>(p, p->part); rp.n_T = count_of<R>(p, p->T); rp.n_F = count_of<R>(p, p->F);
     rp.n_phi00 = count_of<double>(p, p->phi00); rp.n_sigs = count_of<R>(p, p->sigs);
     rp.n_blk = count_of<double>(p, p->blk);
+#endif
     int nblk = p->nblk;
     if constexpr (sizeof(R) == 4) {
         if (p->q_mode) {        // moments from the angular fluxes, then Q = M T on the tensor cores
