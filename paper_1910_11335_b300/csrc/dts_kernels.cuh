@@ -794,8 +794,11 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     const int lane = threadIdx.x;
     const int b0 = grp * SB, nb = min(SB, p.B - b0);
     const int ngrp = (p.B + SB - 1) / SB;
+    // x runs against storage order in odd octants: with the Q input the line data (Q, sigma_t, psi) are
+    // kept in the octant's own x order, so one body serves every octant (NX false) and negx is a value
+    const bool negx = QIN ? (oct & 1) != 0 : NX;
     const bool negy = oct & 2, negz = oct & 4;
-    const int tx = NX ? p.NTx - 1 - ta : ta;
+    const int tx = negx ? p.NTx - 1 - ta : ta;
     const int ty = negy ? p.NTy - 1 - tb : tb;
     const int tz = negz ? p.NTz - 1 - tc : tc;
     const int tile = (tz * p.NTy + ty) * p.NTx + tx;
@@ -930,7 +933,13 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
             const int srow = i / NQ, h = i - srow * NQ;
             const int sy = srow % BY, sz = srow / BY;
             const int ly = negy ? BY - 1 - sy : sy, lz = negz ? BZ - 1 - sz : sz;
-            cp_async16(sg + (lz * BY + ly) * BX + 4 * h, st + srow * BX + 4 * h);   // with the faces' group
+            if (QIN && negx) {   // the line's cells in the octant's x order: quads reversed, and inside them
+                float4 v = *reinterpret_cast<const float4*>(st + srow * BX + 4 * h);
+                v = make_float4(v.w, v.z, v.y, v.x);
+                *reinterpret_cast<float4*>(sg + (lz * BY + ly) * BX + 4 * (NQ - 1 - h)) = v;
+            } else {
+                cp_async16(sg + (lz * BY + ly) * BX + 4 * h, st + srow * BX + 4 * h);   // with the faces' group
+            }
         }
     }
     const size_t og = (size_t)oct * ngrp + grp;
@@ -946,7 +955,9 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 
     const int nvx = p.nx - tx * BX, nvy = p.ny - ty * BY, nvz = p.nz - tz * BZ;
     constexpr unsigned FULL = (1u << BX) - 1u;
-    const unsigned vxs = nvx >= BX ? FULL : (1u << nvx) - 1u;   // valid cells, storage x bits
+    // valid cells as bits of the line's cell index: storage x, or with the Q input in an odd octant the
+    // octant's x (the valid storage cells 0..nvx-1 are the last nvx there)
+    const unsigned vxs = nvx >= BX ? FULL : (QIN && negx) ? (FULL << (BX - nvx)) & FULL : (1u << nvx) - 1u;
     float yv[BX];
     float ysum = 0.f;   // the lane's outgoing y-faces (leakage when the tile is on the y boundary)
 
@@ -1080,7 +1091,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     // outgoing faces; the lane's own faces leaving the grid are its leakage
     if constexpr (!QIN) batch_faces_out<fxn>(fx, gx);
     batch_faces_out<fzn>(fz, gz);
-    const bool lbx = NX ? tx == 0 : tx == p.NTx - 1;
+    const bool lbx = negx ? tx == 0 : tx == p.NTx - 1;
     const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
     const bool lbz = negz ? tz == 0 : tz == p.NTz - 1;
     // the source's leakage from this (octant, tile): its direction lanes summed in direction order
@@ -1133,8 +1144,12 @@ __global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float>
         if (p.active[b0 + i]) okmask |= 1u << i;
     if (okmask == 0) return;
     const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
-    if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
-    else sweep_batch_body<NDO, K, BX, PSI, false, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+    if constexpr (QIN) {   // one body: the octant's x order is in the data
+        sweep_batch_body<NDO, K, BX, PSI, false, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+    } else {
+        if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+        else sweep_batch_body<NDO, K, BX, PSI, false, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+    }
 }
 
 // Error-free FP32 accumulation (Knuth's two-sum): s + e carries the exact sum
@@ -1375,11 +1390,13 @@ __device__ __forceinline__ void psi_issue_first(const float* __restrict__ ps, in
     cp_async_commit();
 }
 
+// flip: 0, or for angular fluxes whose odd octants are stored in the octant's own x order (the
+// tensor-core forms' sweep) the offset of the cell pair there, (c ^ 6) - c, whose two values are swapped
 template <int NDO, int K, bool ISSUED = false>
 __device__ __forceinline__ void psi_moments(const float* __restrict__ ps, size_t ostride, int TV,
                                             const unsigned long long* Dp, unsigned long long* stg,
                                             TwoSum (&s0)[2], float (&m1)[2],
-                                            unsigned long long (&acc)[2][PsiPairs<K>::value])
+                                            unsigned long long (&acc)[2][PsiPairs<K>::value], int flip = 0)
 {
     // stg: this thread's column of a [2][NDO][blockDim.x] staging area; the next
     // octant's fluxes are copied with cp.async while this one is reduced, so the
@@ -1391,8 +1408,9 @@ __device__ __forceinline__ void psi_moments(const float* __restrict__ ps, size_t
     for (int j = 0; j < KP; ++j) acc[0][j] = acc[1][j] = 0ull;
     auto issue = [&](int o) {
         unsigned long long* dst = stg + (o & 1) * NDO * nt;
+        const float* po = ps + o * ostride + ((o & 1) ? flip : 0);
 #pragma unroll
-        for (int d = 0; d < NDO; ++d) cp_async8(dst + d * nt, ps + o * ostride + (size_t)d * TV);
+        for (int d = 0; d < NDO; ++d) cp_async8(dst + d * nt, po + (size_t)d * TV);
         cp_async_commit();
     };
     if (!ISSUED) issue(0);
@@ -1408,6 +1426,11 @@ __device__ __forceinline__ void psi_moments(const float* __restrict__ ps, size_t
             const unsigned long long v = src[d * nt];
             float p0, p1;
             f2unpack(v, p0, p1);
+            if (flip != 0 && (o & 1)) {
+                const float t = p0;
+                p0 = p1;
+                p1 = t;
+            }
             const unsigned long long a = f2pack(p0, p0), bq = f2pack(p1, p1);
             const ulonglong2* dq = reinterpret_cast<const ulonglong2*>(Dp + (o * NDO + d) * KP);
 #pragma unroll
@@ -2247,7 +2270,11 @@ __global__ void __launch_bounds__(256) k_push4(const PushParams<float> p, int g)
 // moments are recomputed from the last sweep's angular fluxes (as k_reduce_psi
 // forms them, two cells per thread), then pushed as in k_push4.
 template <int NDO, int K>
-__global__ void __launch_bounds__(256, 4) k_push_psi(const PushParams<float> p, int g, const float* __restrict__ Dt)
+// xrev: the angular fluxes come from the tensor-core forms' sweep (odd octants in their own x order).
+// w0: this pass updates the lower groups g+1+w0 .. g+w0+kPushRing (a band wider than kPushRing takes
+// several passes); the first pass (w0 = 0) also writes the group's outputs.
+__global__ void __launch_bounds__(256, 4) k_push_psi(const PushParams<float> p, int g, const float* __restrict__ Dt,
+                                                     int xrev, int w0)
 {
     __shared__ __align__(16) unsigned long long Dp[8 * NDO * PsiPairs<K>::value];
     __shared__ unsigned long long stg[2 * NDO * 256];
@@ -2266,12 +2293,12 @@ __global__ void __launch_bounds__(256, 4) k_push_psi(const PushParams<float> p, 
     TwoSum s0t[2];
     float m1[2];
     unsigned long long acc[2][PsiPairs<K>::value];
-    psi_moments<NDO, K>(ps, ostride, c.TV, Dp, stg + threadIdx.x, s0t, m1, acc);
+    psi_moments<NDO, K>(ps, ostride, c.TV, Dp, stg + threadIdx.x, s0t, m1, acc, xrev ? (cc ^ 6) - cc : 0);
     const int v0 = tiled_to_natural(c, c2, nullptr);           // the 2 cells are x-consecutive
     const int x0 = v0 % c.nx;
     const int W1 = p.W + 1;
-    const int nw = min(c.G - 1, g + p.W) - g;
-    // sigma_s(g -> g+1+w) scale_s rounded to FP32 once per (cell, l, lower group): formed for each
+    const int nw = min(c.G - 1, g + p.W) - g - w0;   // lower groups of this pass (may be <= 0)
+    // sigma_s(g -> g+1+w0+w) scale_s rounded to FP32 once per (cell, l, lower group): formed for each
     // Legendre order before its 2l+1 moments (FP64 runs at a small fraction of the FP32 rate)
     constexpr int NL = K == 1 ? 1 : K == 4 ? 2 : K == 9 ? 3 : 4;
     static_assert(NL * NL == K, "K = (L+1)^2");
@@ -2282,7 +2309,8 @@ __global__ void __launch_bounds__(256, 4) k_push_psi(const PushParams<float> p, 
         for (int w = 0; w < kPushRing; ++w)
 #pragma unroll
             for (int j = 0; j < 2; ++j)
-                sc[w][j] = (w >= nw || mm[j] < 0) ? 0.f : push_factor(p, mm[j], l, g, g + 1 + w, c.scale_s_t, c2 + j);
+                sc[w][j] = (w >= nw || mm[j] < 0) ? 0.f
+                                                  : push_factor(p, mm[j], l, g, g + 1 + w0 + w, c.scale_s_t, c2 + j);
 #pragma unroll
         for (int k = l * l; k < (l + 1) * (l + 1); ++k) {
             double ph[2];
@@ -2298,7 +2326,7 @@ __global__ void __launch_bounds__(256, 4) k_push_psi(const PushParams<float> p, 
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                if (mm[j] < 0 || x0 + j >= c.nx) continue;
+                if (w0 != 0 || mm[j] < 0 || x0 + j >= c.nx) continue;
                 if (k == 0) p.col[((size_t)b * c.G + g) * p.V + v0 + j] = ph[j];
                 if (p.mom) p.mom[(((size_t)b * c.G + g) * K + k) * p.V + v0 + j] = ph[j];
             }
@@ -2308,7 +2336,7 @@ __global__ void __launch_bounds__(256, 4) k_push_psi(const PushParams<float> p, 
             float2 fv[kPushRing];
 #pragma unroll
             for (int w = 0; w < kPushRing; ++w) {
-                fp[w] = reinterpret_cast<float2*>(p.F + (size_t)((g + 1 + w) % W1) * p.Fstride + base +
+                fp[w] = reinterpret_cast<float2*>(p.F + (size_t)((g + 1 + w0 + w) % W1) * p.Fstride + base +
                                                   (size_t)k * c.TV);
                 if (w < nw) fv[w] = *fp[w];
             }

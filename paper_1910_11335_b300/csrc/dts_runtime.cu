@@ -494,7 +494,7 @@ BatchFn batch_fn(const dts_problem* p)
 }
 
 using RedPsiFn = void (*)(const RedParams<float>, const float*);
-using PushPsiFn = void (*)(const PushParams<float>, int, const float*);
+using PushPsiFn = void (*)(const PushParams<float>, int, const float*, int, int);
 
 template <int NDO>
 void psi_fns_k(int K, RedPsiFn& r, PushPsiFn& u)
@@ -813,11 +813,14 @@ void launch_push(dts_problem* p, int g)
     pp.col = p->col; pp.mom = p->d.keep_moments ? p->mom : nullptr;
     pp.sigma_s_f = p->sigma_s_f;
     if constexpr (sizeof(R) == 4) {
-        if (p->psi_mode && p->W <= 4) {
+        if (p->psi_mode) {   // the moments from the angular fluxes; kPushRing lower groups per pass
             RedPsiFn rf;
             PushPsiFn uf;
             psi_fns(p, rf, uf);
-            uf<<<dim3((p->NC / 2 + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g, (const float*)p->Dt);
+            // the tensor-core forms' sweep stores odd octants' angular fluxes in their own x order
+            for (int w0 = 0; w0 == 0 || w0 < p->W; w0 += kPushRing)
+                uf<<<dim3((p->NC / 2 + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g, (const float*)p->Dt,
+                                                                              p->q_mode ? 1 : 0, w0);
             return;
         }
         if (p->TX % 4 == 0 && p->W <= 4) {
@@ -830,7 +833,6 @@ void launch_push(dts_problem* p, int g)
     k_push<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g);
 }
 
-// NVTX range for profilers (a no-op unless a tool is attached): the solve, each group, each iteration
 // One solve as a sequence of steps, so that several problems can be interleaved
 // (dts_solve_many): start, then per group begin_group, (launch_iteration,
 // complete_iteration) until the group's members stop, end_group; then finish.
@@ -933,6 +935,9 @@ struct SolveRun {
             TRY(launch_group_init<float>(p, g, slot));
         }
         CK(cudaGetLastError());
+        // set_ctl, group_xs; the group's first source: a copy, or a kernel in the tensor-core forms, plus
+        // the guess kernel when there is an initial guess
+        launches += 2 + (p->q_mode ? 1 : 0) + (p->guess ? 1 : 0);
         n_active = B;
         it = 0;
         return DTS_OK;
@@ -1027,7 +1032,8 @@ struct SolveRun {
         const int slot = g % W1;
         if (p->fp64) launch_push<double>(p, g);
         else launch_push<float>(p, g);
-        launches += 3;   // set_ctl, group_xs, push (the group's T = F is a copy, not a kernel)
+        // the downscatter push: one kernel, or one pass per kPushRing lower groups from angular fluxes
+        launches += (p->psi_mode && !p->fp64) ? std::max(1, (p->W + kPushRing - 1) / kPushRing) : 1;
         if (g + W1 < G) {
             if (p->fp64) launch_fixed_source<double>(p, g + W1, slot);
             else launch_fixed_source<float>(p, g + W1, slot);

@@ -321,6 +321,10 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
     uint64_t* mbar1 = full + 2;                                    // Eq. 3 contraction done
     uint32_t* slot = reinterpret_cast<uint32_t*>(qsm + S::oSlot);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31, c = t;
+    // the sweep keeps odd octants' (negative x cosine) Q and psi in the octant's own x order: cell c of
+    // an 8 x 4 x 4 tile is c ^ 7 there
+    static_assert(kQCells == 128, "8 x 4 x 4 tiles: x is the low 3 bits of the cell index");
+    const int cr = c ^ 7;
 
     // bytes of a flux stage; the poison hook adds 16 that no copy delivers, so the stage's wait runs out
     __shared__ uint32_t stage_tx;
@@ -442,7 +446,7 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
                 for (int o = 0; o < 8; ++o) {
                     float v[NDO];
 #pragma unroll
-                    for (int d = 0; d < NDO; ++d) v[d] = spsi[(o * NDO + d) * kQCells + c];
+                    for (int d = 0; d < NDO; ++d) v[d] = spsi[(o * NDO + d) * kQCells + ((o & 1) ? cr : c)];
                     float s = 0.f;
 #pragma unroll
                     for (int d = 0; d < NDO; ++d) s = fmaf(sw[o * NDO + d], v[d], s);
@@ -499,7 +503,7 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
                     unsigned long long f0 = 0ull;   // moments (0, 1) of this octant
 #pragma unroll
                     for (int d = 0; d < NDO; ++d) {
-                        const float v = spsi[(o * NDO + d) * kQCells + c];
+                        const float v = spsi[(o * NDO + d) * kQCells + ((o & 1) ? cr : c)];
                         const unsigned long long a = f2pack(v, v);
                         const ulonglong2* dq = reinterpret_cast<const ulonglong2*>(Dp + (o * NDO + d) * KP);
 #pragma unroll
@@ -609,8 +613,9 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
         phase_mma ^= 1u;
         tc_fence_after();
         {
-            // column n = o NDO + d of cell c goes to Q[b][o][tile][d][c]
+            // column n = o NDO + d of cell c goes to Q[b][o][tile][d][c], odd octants at c ^ 7
             float* qb = p.Q + ((size_t)b * 8 * p.NT + tile) * (size_t)(NDO * p.TV) + c;
+            float* qbr = qb + (cr - c);
             const size_t ostr = (size_t)p.NT * (NDO * p.TV);
             static_for<0, S::NCH>([&](auto chv) {
                 constexpr int ch = decltype(chv)::value;
@@ -621,7 +626,8 @@ __global__ void __launch_bounds__(kQThreads, 3) k_moments_q(const QParams p)
                 for (int i = 0; i < 8; ++i) {
                     constexpr int nb = 8 * ch;
                     const int n = nb + i;
-                    if (n < ND && okQ) qb[(size_t)(n / NDO) * ostr + (n % NDO) * p.TV] = __uint_as_float(r[i]);
+                    if (n < ND && okQ)
+                        (((n / NDO) & 1) ? qbr : qb)[(size_t)(n / NDO) * ostr + (n % NDO) * p.TV] = __uint_as_float(r[i]);
                 }
             });
         }
