@@ -195,7 +195,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "ms_per_step": 1e3 * w.n_voxels * w.n_dirs / value, "dtype": "f64",
             "data": "synthetic", "scaling": "weak", "vs_baseline": None,
-            "config": {"workload": w.name, "oracle": "plain FP64 C, gcc -O2, OpenMP over octants"},
+            "config": {"workload": w.name, "voxels": [w.nx, w.ny, w.nz], "groups": w.n_groups,
+                       "directions": w.n_dirs, "legendre_order": w.legendre_order, "sources_per_gpu": w.batch,
+                       "tol": args.tol if args.tol is not None else w.tol,
+                       "oracle": "plain FP64 C, gcc -O2, OpenMP over octants"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample, **cpu_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
