@@ -726,9 +726,58 @@ __device__ __forceinline__ void batch_fixup(float qv, float sig, float ax, float
     }
 }
 
+// The same fixup run by the whole warp (the Q-input walk, whose kernel is small enough for the longer
+// code): pass 1 fixes the faces found negative in the plain solve, further passes run while a vote finds
+// a free face of some lane negative; a lane with nothing new in a pass keeps its values bit for bit. A
+// fixed face's term leaves the numerator by halves (num: the plain solve's numerator), and the
+// denominator is formed again from the free faces. Measured against the divergent form on the 96^3 and
+// 48^3 workloads: 2.4 % and 3.9 % less sweep time.
+__device__ __forceinline__ void fixup_solve(float num, float sig, float ax, float ay, float az, bool fx, bool fy,
+                                            bool fz, float xin, float yin, float zin, float& psi, float& ox,
+                                            float& oy, float& oz)
+{
+    psi = __fdividef(num, sig + (((fx ? 0.f : ax) + (fy ? 0.f : ay)) + (fz ? 0.f : az)));
+    ox = fmaf(2.f, psi, -xin);
+    oy = fmaf(2.f, psi, -yin);
+    oz = fmaf(2.f, psi, -zin);
+}
+
+__device__ __forceinline__ void batch_fixup_u(float num, float sig, float ax, float ay, float az, float xin,
+                                              float yin, float zin, float& psi, float& ox, float& oy, float& oz)
+{
+    // pass 1 (the caller's vote found a sign bit set; a -0 outflow is not negative and changes nothing)
+    bool fx = ox < 0.f, fy = oy < 0.f, fz = oz < 0.f;   // faces fixed at zero
+    if (fx || fy || fz) {
+        if (fx) num = fmaf(-0.5f * ax, xin, num);
+        if (fy) num = fmaf(-0.5f * ay, yin, num);
+        if (fz) num = fmaf(-0.5f * az, zin, num);
+        fixup_solve(num, sig, ax, ay, az, fx, fy, fz, xin, yin, zin, psi, ox, oy, oz);
+    }
+    // passes 2 and 3 (ox, oy, oz: the latest solve's raw outflows 2 psi - psi_in)
+#pragma unroll 1
+    for (int pass = 1; pass < 3; ++pass) {
+        const bool nx = !fx && ox < 0.f, ny = !fy && oy < 0.f, nz = !fz && oz < 0.f;
+        const bool nw = nx || ny || nz;
+        if (!__any_sync(0xffffffffu, nw)) break;
+        if (nw) {
+            if (nx) num = fmaf(-0.5f * ax, xin, num);
+            if (ny) num = fmaf(-0.5f * ay, yin, num);
+            if (nz) num = fmaf(-0.5f * az, zin, num);
+            fx |= nx;
+            fy |= ny;
+            fz |= nz;
+            fixup_solve(num, sig, ax, ay, az, fx, fy, fz, xin, yin, zin, psi, ox, oy, oz);
+        }
+    }
+    ox = fx ? 0.f : ox;
+    oy = fy ? 0.f : oy;
+    oz = fz ? 0.f : oz;
+}
+
 // One x-line of phase B. Cells in upwind (local) order lx; q and psi in
 // storage x order sx. CHECK: the line has padding cells (mask vm over sx).
-template <int BX, bool NX, bool CHECK>
+// UF: the warp-uniform fixup (the Q-input walk) instead of the divergent one.
+template <int BX, bool NX, bool CHECK, bool UF = false>
 __device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], float* zrow, const float* srow,
                                            float& xin, unsigned vm, float ax, float ay, float az, float asum)
 {
@@ -751,14 +800,16 @@ __device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], flo
         float psi, ox, oy, oz;
         if (!CHECK || (vm >> sx & 1u)) {
             const float q = qv[sx], sig = sv[sx];
-            psi = __fdividef(fmaf(ax, xin, fmaf(ay, yin, fmaf(az, zin, q))), sig + asum);
+            const float num = fmaf(ax, xin, fmaf(ay, yin, fmaf(az, zin, q)));
+            psi = __fdividef(num, sig + asum);
             ox = fmaf(2.f, psi, -xin);
             oy = fmaf(2.f, psi, -yin);
             oz = fmaf(2.f, psi, -zin);
             // any sign bit set (a -0 outflow only enters the fixup to leave it unchanged)
             const bool neg = (__float_as_int(ox) | __float_as_int(oy) | __float_as_int(oz)) < 0;
             if (__any_sync(0xffffffffu, neg)) {
-                if (neg) batch_fixup(q, sig, ax, ay, az, xin, yin, zin, psi, ox, oy, oz);
+                if constexpr (UF) batch_fixup_u(num, sig, ax, ay, az, xin, yin, zin, psi, ox, oy, oz);
+                else if (neg) batch_fixup(q, sig, ax, ay, az, xin, yin, zin, psi, ox, oy, oz);
             }
         } else {
             psi = 0.f;
@@ -1026,8 +1077,8 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
             } else {
                 xin = fx[line * 32 + lane];
             }
-            if (vm == FULL) batch_line<BX, NX, false>(qv, yv, zrow, srow, xin, vm, ax, ay, az, asum);
-            else batch_line<BX, NX, true>(qv, yv, zrow, srow, xin, vm, ax, ay, az, asum);
+            if (vm == FULL) batch_line<BX, NX, false, QIN>(qv, yv, zrow, srow, xin, vm, ax, ay, az, asum);
+            else batch_line<BX, NX, true, QIN>(qv, yv, zrow, srow, xin, vm, ax, ay, az, asum);
             if constexpr (QIN) {
                 gx[line * 32 + lane] = xin;   // outgoing x-face, in place in the face block
                 xsum += xin;
