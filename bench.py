@@ -258,7 +258,7 @@ def roofline(stats, ms_step, steps, K, ndo, tc, peaks, which, n_sm):
     """The dominant kernel's roofline and the HBM accounting of the iteration.
 
     The wavefront sweep takes most of a step. It moves per update (design of the
-    tensor-core forms, SURVEY 8(d) route beta) the per-direction source Q it
+    tensor-core forms, which materialise the per-direction source) the Q it
     reads (4 B) and the angular flux it writes (4 B) plus sigma_t shared by the
     octant's directions; the fused CUDA-core form reads the K source moments per
     (cell, octant) instead of Q. It is bound by instruction issue and latency,
@@ -266,7 +266,8 @@ def roofline(stats, ms_step, steps, K, ndo, tc, peaks, which, n_sm):
     instructions per update x updates per second of sweep time (CUDA events
     around the sweep graph), peak = 4 warp instructions per cycle per SM x SMs x
     maximum SM clock. The HBM fractions are reported beside it: on the method's
-    algorithmic minimum (2K+1) x 4 / N_d bytes per update, on the
+    algorithmic minimum (2K+1) x 4 / N_d bytes per update (read K source moments
+    and sigma_t, write K moments per cell; faces and fluxes on chip), on the
     design's bytes, and on the DRAM bytes ncu measured; the moment kernel
     (Eq. 3 + scatter-source contraction), which is HBM-bound, gets its own."""
     updates = sum(s["updates"] for s in stats)
