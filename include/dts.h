@@ -22,7 +22,8 @@
  *     of dts_create_problem leave it in dts_last_error(NULL) (per thread).
  *   - The caller owns every buffer it passes in or out. Input arrays are
  *     copied before the call returns. Host pointers must stay valid only for
- *     the duration of the call.
+ *     the duration of the call (except the buffer of dts_set_host_output,
+ *     which later solves write into).
  *   - All device work is ordered on the stream given in dts_problem_desc
  *     (or an internal stream when that is NULL). One problem must be used by
  *     one host thread at a time. Distinct problems are independent.
@@ -194,6 +195,24 @@ dts_status dts_set_source_cones(dts_problem *p, int batch_index, int n_cones,
  * with tol > 0 (results and stats are still filled); DTS_ERR_CUDA.
  */
 dts_status dts_solve(dts_problem *p, dts_solve_stats *stats);
+
+/*
+ * Streamed output: during every later solve of p (dts_solve or
+ * dts_solve_many), component comp of each member's scalar fluence (as
+ * dts_get_scalar_fluence gives it, bit for bit) is copied into
+ * host[b][g][v] (B x G x V doubles, [nz][ny][nx] voxels) group by group: when
+ * group g has converged and pushed its downscatter, its values are gathered
+ * on the device and copied to the host on a second stream while the solve
+ * goes on with the later groups, so the copies overlap the solve; the solve
+ * returns when the last group's copy has landed. Page-locked host memory
+ * (cudaHostAlloc or cudaHostRegister) lets the copies run asynchronously;
+ * pageable memory works but is copied synchronously. host must stay valid
+ * and untouched by the caller while a solve runs; NULL turns the stream off.
+ * The first call allocates two staging slots of B x V doubles on the device.
+ * Errors: DTS_ERR_INVALID_ARG (p NULL, comp, len < B*G*V), DTS_ERR_OOM,
+ * DTS_ERR_CUDA.
+ */
+dts_status dts_set_host_output(dts_problem *p, dts_component comp, double *host, size_t len);
 
 /*
  * Restart from saved moments: member batch_index's source iteration in every

@@ -1738,6 +1738,17 @@ __global__ void k_guess_source(const CellParams c, const double* __restrict__ gu
     }
 }
 
+// one group of the scalar fluence of every member for the streamed output: comp 0 uncollided,
+// 1 collided, 2 their sum; unc and col [B][G][V], out [B][V]
+__global__ void k_gather_component(const double* __restrict__ unc, const double* __restrict__ col, int comp, int g,
+                                   int G, int V, double* __restrict__ out)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (v >= V) return;
+    const size_t i = ((size_t)b * G + g) * V + v;
+    out[(size_t)b * V + v] = comp == 0 ? unc[i] : comp == 1 ? col[i] : unc[i] + col[i];
+}
+
 // one bounds check of a region of n elements, failing when plant != 0; touches no memory
 __global__ void k_bounds_selftest(int plant, size_t n) { (void)DTS_FITS(plant ? n + 1 : n, n, 63); }
 

@@ -66,6 +66,14 @@ struct dts_problem {
     void* on_iter_user = nullptr;
     double* guess = nullptr;              // initial guess [B][G][K][V] (dts_set_initial_guess), or null
     void* guess_T = nullptr;              // tensor-core forms: the group's first T [B][NT][K][TV] (FP32)
+    // streamed output (dts_set_host_output): component host_comp of each finished group copied into
+    // host_out[b][g][v] on copy_stream, through two device staging slots of [B][V] doubles
+    double* host_out = nullptr;
+    int host_comp = 0;
+    cudaStream_t copy_stream = nullptr;
+    double* out_stage[2] = {nullptr, nullptr};
+    cudaEvent_t ev_staged[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    bool copied_pending[2] = {false, false};
     int V = 0, G = 0, L = 0, K = 0, nd = 0, ndo = 0, B = 0;
     int TX = 0, TY = 0, TZ = 0, TV = 0, NTx = 0, NTy = 0, NTz = 0, NT = 0, NC = 0;
     int n_stages = 0, nsub = 0, n_mat = 0, W = 0, nblk = 0, n_sm = 148;
@@ -833,6 +841,28 @@ void launch_push(dts_problem* p, int g)
     k_push<R><<<dim3((p->NC + 255) / 256, p->B), 256, 0, p->stream>>>(pp, g);
 }
 
+// Streamed output of group g (dts_set_host_output): the group's component of every member gathered on
+// the solve's stream into staging slot g & 1, then copied to host_out[b][g][:] on the copy stream while
+// the solve goes on with the next groups; a slot is reused once its previous copy has landed.
+dts_status stream_group_output(dts_problem* p, int g)
+{
+    if (!p->host_out) return DTS_OK;
+    const int slot = g & 1;
+    const size_t V = (size_t)p->V, G = (size_t)p->G;
+    if (p->copied_pending[slot]) CK(cudaStreamWaitEvent(p->stream, p->ev_copied[slot], 0));
+    k_gather_component<<<dim3((unsigned)((V + 255) / 256), p->B), 256, 0, p->stream>>>(
+        p->unc, p->col, p->host_comp, g, (int)G, (int)V, p->out_stage[slot]);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(p->ev_staged[slot], p->stream));
+    CK(cudaStreamWaitEvent(p->copy_stream, p->ev_staged[slot], 0));
+    CK(cudaMemcpy2DAsync(p->host_out + (size_t)g * V, G * V * sizeof(double), p->out_stage[slot],
+                         V * sizeof(double), V * sizeof(double), (size_t)p->B, cudaMemcpyDeviceToHost,
+                         p->copy_stream));
+    CK(cudaEventRecord(p->ev_copied[slot], p->copy_stream));
+    p->copied_pending[slot] = true;
+    return DTS_OK;
+}
+
 // One solve as a sequence of steps, so that several problems can be interleaved
 // (dts_solve_many): start, then per group begin_group, (launch_iteration,
 // complete_iteration) until the group's members stop, end_group; then finish.
@@ -1032,6 +1062,7 @@ struct SolveRun {
         const int slot = g % W1;
         if (p->fp64) launch_push<double>(p, g);
         else launch_push<float>(p, g);
+        TRY(stream_group_output(p, g));
         // the downscatter push: one kernel, or one pass per kPushRing lower groups from angular fluxes
         launches += (p->psi_mode && !p->fp64) ? std::max(1, (p->W + kPushRing - 1) / kPushRing) : 1;
         if (g + W1 < G) {
@@ -1051,6 +1082,10 @@ struct SolveRun {
     {
         CK(cudaEventRecord(p->ev1, p->stream));
         CK(cudaEventSynchronize(p->ev1));
+        if (p->host_out) {   // the last groups' copies to the host
+            CK(cudaStreamSynchronize(p->copy_stream));
+            p->copied_pending[0] = p->copied_pending[1] = false;
+        }
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
         p->solved = true;
@@ -1411,8 +1446,13 @@ void destroy(dts_problem* p)
     if (p->h_status) cudaFreeHost(p->h_status);
     if (p->h_active) cudaFreeHost(p->h_active);
     if (p->h_err) cudaFreeHost(p->h_err);
-    for (cudaEvent_t e : {p->ev0, p->ev1, p->eva, p->evb, p->evc})
+    for (cudaEvent_t e : {p->ev0, p->ev1, p->eva, p->evb, p->evc, p->ev_staged[0], p->ev_staged[1],
+                          p->ev_copied[0], p->ev_copied[1]})
         if (e) cudaEventDestroy(e);
+    if (p->copy_stream) {
+        cudaStreamSynchronize(p->copy_stream);
+        cudaStreamDestroy(p->copy_stream);
+    }
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
 }
 
@@ -2161,6 +2201,32 @@ dts_status dts_debug_poison_wait(dts_problem* p, int on)
     const int v = on ? 1 : 0;
     CK(cudaStreamSynchronize(p->stream));
     CK(cudaMemcpy(p->dev_poison, &v, sizeof v, cudaMemcpyHostToDevice));
+    return DTS_OK;
+}
+
+dts_status dts_set_host_output(dts_problem* p, dts_component comp, double* host, size_t len)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    DevGuard guard(p->d.device);
+    if (p->copy_stream) CK(cudaStreamSynchronize(p->copy_stream));
+    if (!host) {
+        p->host_out = nullptr;
+        return DTS_OK;
+    }
+    if (comp != DTS_COMP_UNCOLLIDED && comp != DTS_COMP_COLLIDED && comp != DTS_COMP_TOTAL)
+        return fail(p, DTS_ERR_INVALID_ARG, "comp must be UNCOLLIDED, COLLIDED or TOTAL");
+    if (len < (size_t)p->B * p->G * p->V) return fail(p, DTS_ERR_INVALID_ARG, "host: need B*G*V doubles");
+    if (!p->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaEventCreateWithFlags(&p->ev_staged[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming));
+            TRY(dalloc_t(p, &p->out_stage[i], (size_t)p->B * p->V));
+        }
+    }
+    p->host_out = host;
+    p->host_comp = (int)comp;
+    p->copied_pending[0] = p->copied_pending[1] = false;
     return DTS_OK;
 }
 

@@ -76,7 +76,8 @@ EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_sol
            "dts_sweep_once_noalloc", "dts_solve_adjoint", "dts_get_adjoint_iterations",
            "dts_tune_tile", "dts_set_source_cones", "dts_get_dose", "dts_debug_fail_allocation",
            "dts_solve_many", "dts_tune_cache_file", "dts_set_iteration_callback",
-           "dts_debug_bounds_selftest", "dts_set_initial_guess", "dts_debug_poison_wait")
+           "dts_debug_bounds_selftest", "dts_set_initial_guess", "dts_debug_poison_wait",
+           "dts_set_host_output")
 
 
 def lib():
@@ -116,6 +117,7 @@ def lib():
         "dts_debug_bounds_selftest": ([C.c_int, C.POINTER(C.c_int)], C.c_int),
         "dts_set_initial_guess": ([C.c_void_p, C.c_int, _dp, C.c_size_t, C.c_int], C.c_int),
         "dts_debug_poison_wait": ([C.c_void_p, C.c_int], C.c_int),
+        "dts_set_host_output": ([C.c_void_p, C.c_int, C.c_void_p, C.c_size_t], C.c_int),
         "dts_set_iteration_callback": ([C.c_void_p, IterationFn, C.c_void_p], C.c_int),
         "dts_solve_adjoint": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_int], C.c_int),
@@ -292,6 +294,19 @@ class Problem:
                        (C.c_double * 3)(*src.axis), src.half_angle, _dptr(sp), src.aperture,
                        (C.c_double * 3)(*src.normal), src.half_azimuth, src.half_polar)
         _check(lib().dts_set_source(self._h, b, C.byref(s)), self._h)
+
+    def set_host_output(self, comp: int, host):
+        """Stream component comp of every member's scalar fluence into host (a
+        C-contiguous float64 array of B*G*V values, page-locked for overlap) group
+        by group during later solves; None turns it off (dts_set_host_output)."""
+        if host is None:
+            self._host_out = None
+            _check(lib().dts_set_host_output(self._h, comp, None, 0), self._h)
+            return
+        if not (isinstance(host, np.ndarray) and host.dtype == np.float64 and host.flags.c_contiguous):
+            raise ValueError("host must be a C-contiguous float64 numpy array")
+        self._host_out = host   # kept alive while the library writes into it
+        _check(lib().dts_set_host_output(self._h, comp, host.ctypes.data_as(C.c_void_p), host.size), self._h)
 
     def set_initial_guess(self, b: int, moments):
         """Start member b's source iteration in every group from moments [G][K][V]
