@@ -467,7 +467,7 @@ def run_ours(args):
         roof["frac_over_timed_steps"] = over / roof["peak"]
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(w, prec, tol, args, dts, local, stream, torch)
+        e2e = end_to_end(w, prec, tol, args, dts, local, stream, torch, world, dev)
     cpu = None
     if rank == 0 and not args.no_cpu:
         threads = oracle_threads()
@@ -580,7 +580,7 @@ def fp64_plain(w, p32, dts, dev, stream, tol):
             "rel_l2_fp32_vs_fp64": err, "rel_l2_fp32_vs_fp64_max_group": max(errs_g)}
 
 
-def end_to_end(w, prec, tol, args, dts, dev, stream, torch):
+def end_to_end(w, prec, tol, args, dts, dev, stream, torch, world=1, device=None):
     """Same metric through the C ABI with HOST buffers: every step uploads the
     materials and sources from pinned host memory and solves; the total scalar
     fluence of every source lands in pinned host memory during the solve, each
@@ -592,7 +592,14 @@ def end_to_end(w, prec, tol, args, dts, dev, stream, torch):
     st_h = torch.from_numpy(np.ascontiguousarray(w.sigma_t)).pin_memory().numpy()
     ss_h = torch.from_numpy(np.ascontiguousarray(w.sigma_s)).pin_memory().numpy()
     parts = Parts(w, prec, tol, args, dts, dev, stream, torch)
-    outs = [torch.empty(len(run) * G * V, dtype=torch.float64).pin_memory().numpy() for run in parts.runs]
+
+    def host_array(n):   # page-locked when the host allows it (the copies then overlap the solve)
+        try:
+            return torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+        except RuntimeError:
+            return np.empty(n)
+
+    outs = [host_array(len(run) * G * V) for run in parts.runs]
     for p, out in zip(parts.probs, outs):
         p.set_host_output(dts.TOTAL, out)
     parts.solve()
@@ -600,6 +607,9 @@ def end_to_end(w, prec, tol, args, dts, dev, stream, torch):
     h2d = len(parts.probs) * (mat.nbytes + st_h.nbytes + ss_h.nbytes) + B * (8 * 7 + 8 * G)
     d2h = B * G * V * 8
     updates = 0
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
         for p, run in zip(parts.probs, parts.runs):
@@ -610,8 +620,10 @@ def end_to_end(w, prec, tol, args, dts, dev, stream, torch):
         updates += st["updates"]
     dt = time.perf_counter() - t0
     parts.close()
-    return {"value": updates / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": steps}
+    # whole job, as for the device-timed value: the slowest rank's time, every rank's updates and bytes
+    ms, total = aggregate(dt * 1e3, updates, world, device)
+    return {"value": total / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d) * world,
+            "d2h_bytes_per_step": int(d2h) * world, "steps": steps}
 
 
 def main():
