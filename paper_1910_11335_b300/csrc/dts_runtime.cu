@@ -886,6 +886,8 @@ struct SolveRun {
     }
     ~SolveRun()
     {
+        // on every way out (an error included) no copy into the caller's host array is left in flight
+        if (p->host_out && p->copy_stream) cudaStreamSynchronize(p->copy_stream);
         if (r_iter) nvtxRangeEnd(r_iter);
         if (r_group) nvtxRangeEnd(r_group);
         if (r_solve) nvtxRangeEnd(r_solve);
@@ -2181,11 +2183,12 @@ dts_status dts_set_initial_guess(dts_problem* p, int batch_index, const double* 
     if (!is_device)
         for (size_t i = 0; i < n; ++i)
             if (!isfin(moments[i])) return fail(p, DTS_ERR_INVALID_ARG, "moments: non-finite value");
+    // the tensor-core forms' first-T buffer before the guess itself: a guess never exists without it
+    if (p->q_mode && !p->guess_T) TRY(dalloc(p, &p->guess_T, (size_t)p->B * p->NC * p->K * sizeof(float)));
     if (!p->guess) {
         TRY(dalloc_t(p, &p->guess, (size_t)p->B * n));
         CK(cudaMemsetAsync(p->guess, 0, (size_t)p->B * n * sizeof(double), p->stream));
     }
-    if (p->q_mode && !p->guess_T) TRY(dalloc(p, &p->guess_T, (size_t)p->B * p->NC * p->K * sizeof(float)));
     CK(cudaMemcpyAsync(p->guess + (size_t)batch_index * n, moments, n * sizeof(double),
                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
     CK(cudaStreamSynchronize(p->stream));
@@ -2216,14 +2219,14 @@ dts_status dts_set_host_output(dts_problem* p, dts_component comp, double* host,
     if (comp != DTS_COMP_UNCOLLIDED && comp != DTS_COMP_COLLIDED && comp != DTS_COMP_TOTAL)
         return fail(p, DTS_ERR_INVALID_ARG, "comp must be UNCOLLIDED, COLLIDED or TOTAL");
     if (len < (size_t)p->B * p->G * p->V) return fail(p, DTS_ERR_INVALID_ARG, "host: need B*G*V doubles");
-    if (!p->copy_stream) {
-        CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
-        for (int i = 0; i < 2; ++i) {
-            CK(cudaEventCreateWithFlags(&p->ev_staged[i], cudaEventDisableTiming));
-            CK(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming));
-            TRY(dalloc_t(p, &p->out_stage[i], (size_t)p->B * p->V));
-        }
+    // each resource on its own, so that a failed call leaves nothing half made for the next one
+    for (int i = 0; i < 2; ++i)
+        if (!p->out_stage[i]) TRY(dalloc_t(p, &p->out_stage[i], (size_t)p->B * p->V));
+    for (int i = 0; i < 2; ++i) {
+        if (!p->ev_staged[i]) CK(cudaEventCreateWithFlags(&p->ev_staged[i], cudaEventDisableTiming));
+        if (!p->ev_copied[i]) CK(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming));
     }
+    if (!p->copy_stream) CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
     p->host_out = host;
     p->host_comp = (int)comp;
     p->copied_pending[0] = p->copied_pending[1] = false;
