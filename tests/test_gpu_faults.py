@@ -56,3 +56,31 @@ def test_bounded_wait_runs_out_and_the_problem_recovers():
     with pytest.raises(dts.DTSError) as e:
         q.debug_poison_wait(True)
     assert e.value.status == dts.DTS_ERR_STATE
+
+
+def test_injected_failures_in_output_and_restart_setup():
+    """An allocation failing halfway through dts_set_host_output (its second staging slot) or
+    dts_set_initial_guess (the guess after its staging T): DTS_ERR_OOM, and the problem still
+    solves as before and takes the call when it is made again."""
+    w = inputs.small_cone(9, 8, 7, n_groups=2, sn_order=8, legendre_order=3, n_sources=2)
+    G, V = w.n_groups, w.n_voxels
+    p = dts.problem_from_workload(w, precision=dts.PREC_FP32_SPLITBF16, tol=0.0, max_iters=2)
+    p.solve(allow_not_converged=True)
+    ref = [p.fluence(b, dts.TOTAL) for b in range(2)]
+    host = np.full(2 * G * V, np.nan)
+    for call in (lambda: p.set_host_output(dts.TOTAL, host),
+                 lambda: p.set_initial_guess(0, np.zeros((G, 16, V)))):
+        dts.debug_fail_allocation(1)
+        try:
+            with pytest.raises(dts.DTSError) as e:
+                call()
+        finally:
+            dts.debug_fail_allocation(-1)
+        assert e.value.status == dts.DTS_ERR_OOM
+        p.solve(allow_not_converged=True)
+        for b in range(2):
+            assert np.array_equal(p.fluence(b, dts.TOTAL), ref[b])
+    p.set_host_output(dts.TOTAL, host)
+    p.solve(allow_not_converged=True)
+    for b in range(2):
+        assert np.array_equal(host.reshape(2, G, V)[b], ref[b])
