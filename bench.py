@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--split", type=int, default=4,
                     help="solve each GPU's sources as this many problems on their own streams "
                          "(dts_solve_many: one part's moment kernels beside another's sweep); 1 = one problem")
+    ap.add_argument("--loop", default="device", choices=["device", "host"],
+                    help="source iterations of a group as one CUDA-graph launch with the convergence "
+                         "decisions on the device (dts_set_device_loop), or one host round trip each")
     return ap.parse_args()
 
 
@@ -331,13 +334,15 @@ class Parts:
     problem on its own stream, solved together by dts_solve_many; with one run,
     one problem on the given stream solved by dts_solve."""
 
-    def __init__(self, w, prec, tol, args, dts, dev, stream, torch, split=None):
+    def __init__(self, w, prec, tol, args, dts, dev, stream, torch, split=None, loop=None):
         self.dts = dts
+        device_loop = (args.loop if loop is None else loop) == "device"
         self.runs = dts.source_parts(w.batch, args.split if split is None else split, w.sn_order)
         tile = tuple(int(x) for x in args.tile.split(","))
         self.streams = [stream] if len(self.runs) == 1 else [torch.cuda.Stream(dev) for _ in self.runs]
         self.probs = [dts.problem_from_workload(w, precision=prec, tol=tol, max_iters=args.max_iters or 1000,
-                                                tile=tile, device=dev, stream=st.cuda_stream, sources=run)
+                                                tile=tile, device=dev, stream=st.cuda_stream, sources=run,
+                                                device_loop=device_loop)
                       for run, st in zip(self.runs, self.streams)]
 
     def solve(self):
@@ -447,7 +452,8 @@ def run_ours(args):
     # region; CUDA events around its sweep graphs on its stream), and the sweep's instruction
     # rate over the timed steps is reported beside it.
     if len(split) > 1:
-        solo = Parts(w, prec, tol, args, dts, local, stream, torch, split=1)
+        # host loop: its CUDA events time the sweep and moment graphs apart
+        solo = Parts(w, prec, tol, args, dts, local, stream, torch, split=1, loop="host")
         solo.solve()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -455,12 +461,22 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         solo_ms = (time.perf_counter() - t0) * 1e3
         solo.close()
-    else:
+    elif args.loop == "host":
         solo_st, solo_ms = stats[-1], ms_rank / args.steps
+    else:   # the device-resident loop times no phases: one more solve with the host loop
+        solo = Parts(w, prec, tol, args, dts, local, stream, torch, split=1, loop="host")
+        solo.solve()
+        torch.cuda.synchronize(dev)
+        solo_st = solo.solve()
+        solo_ms = solo_st["solve_ms"]
+        solo.close()
     roof = roofline([solo_st], solo_st["solve_ms"], 1, K, ndo, tc, peaks, which, n_sm)
-    roof["measured_on"] = ("the timed steps" if len(split) == 1 else
-                           f"one untimed solve of the same {w.batch} sources as one problem "
-                           f"({solo_ms:.0f} ms; the timed steps run {len(split)} overlapping parts)")
+    if len(split) == 1 and args.loop == "host":
+        roof["measured_on"] = "the timed steps"
+    else:
+        roof["measured_on"] = (f"one untimed solve of the same {w.batch} sources as one problem with the "
+                               f"host-driven loop ({solo_ms:.0f} ms; the timed steps run {len(split)} "
+                               f"part(s) with the {args.loop} loop)")
     if roof.get("inst_per_update"):
         over = roof["inst_per_update"] * sum(s["updates"] for s in stats) / (ms_rank / 1e3) / 1e9
         roof["achieved_over_timed_steps"] = over
@@ -506,8 +522,12 @@ def run_ours(args):
             "clocks": clk,
             "solve": {"sweeps_per_step": stats[0]["sweeps"], "updates_per_step": stats[0]["updates"],
                       "max_residual": stats[-1]["max_residual"], "converged": stats[-1]["converged"],
-                      "sweep_ms_per_step": sum(s["sweep_ms"] for s in stats) / args.steps,
-                      "reduce_ms_per_step": sum(s["reduce_ms"] for s in stats) / args.steps},
+                      "loop": args.loop,
+                      # the device-resident loop has no per-phase events (its stats carry 0)
+                      "sweep_ms_per_step": (sum(s["sweep_ms"] for s in stats) / args.steps
+                                            if args.loop == "host" else None),
+                      "reduce_ms_per_step": (sum(s["reduce_ms"] for s in stats) / args.steps
+                                             if args.loop == "host" else None)},
         }
         if gathered is not None:
             line["gathered_sources"] = gathered

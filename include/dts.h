@@ -118,8 +118,10 @@ typedef struct {
     int64_t sweeps;             /* executed (source, group, iteration) sweeps */
     double max_residual;        /* largest final residual over sources and groups */
     double solve_ms;            /* device time of dts_solve, CUDA events on the stream */
-    double sweep_ms;            /* device time of the wavefront sweep launches (all stages) */
-    double reduce_ms;           /* device time of the Eq. 3 reduction + residual launches */
+    double sweep_ms;            /* device time of the wavefront sweep launches (all stages);
+                                   0 when the iterations ran as a device-resident loop */
+    double reduce_ms;           /* device time of the Eq. 3 reduction + residual launches;
+                                   0 when the iterations ran as a device-resident loop */
     int64_t launches;           /* kernels launched by this solve */
     int converged;              /* 1 when every (source, group) reached tol */
     int tile_x, tile_y, tile_z; /* wavefront tile used */
@@ -244,6 +246,31 @@ dts_status dts_set_initial_guess(dts_problem *p, int batch_index, const double *
 typedef void (*dts_iteration_fn)(void *user, int group, int iteration, const double *residuals,
                                  int batch);
 dts_status dts_set_iteration_callback(dts_problem *p, dts_iteration_fn fn, void *user);
+
+/*
+ * Device-resident source iteration (the group loop of Eq. 2, Sec. II.A:
+ * source iteration of each group to convergence, groups high to low). With
+ * on != 0, every later solve of p (dts_solve or dts_solve_many) runs each
+ * group's source iterations as ONE launch of a CUDA graph: a WHILE node whose
+ * body is one iteration (all wavefront stages of the sweep, the Eq. 3
+ * reduction, the residual) followed by a one-block control kernel that makes,
+ * on the device, the decisions the host loop makes after every iteration (a
+ * member stops below tol or, in the FP32 forms, after 10 iterations without a
+ * 1 % improvement; the group ends when no member iterates or at max_iters, or
+ * when a bounded wait of the tensor-core forms has given up). The host then
+ * enqueues a whole solve without waiting on any iteration. The same kernels run
+ * in the same order on the same data, so results, iteration counts, residuals
+ * and balance terms equal those of the host loop bit for bit. Differences: the
+ * stats' sweep_ms and reduce_ms are 0 (no per-phase timing inside the loop);
+ * a timed-out wait (DTS_ERR_TIMEOUT) is reported when the solve finishes, not
+ * after the iteration that met it; no per-iteration NVTX range. A problem with
+ * an iteration callback (dts_set_iteration_callback), and every problem in the
+ * bounds-checked build, keeps the host loop. The first call with on != 0
+ * allocates the loop state on the device (about (12 + 36 G) bytes per member);
+ * on = 0 returns to the host loop. Errors: DTS_ERR_INVALID_ARG (p NULL),
+ * DTS_ERR_OOM.
+ */
+dts_status dts_set_device_loop(dts_problem *p, int on);
 
 /*
  * Solve n problems together, each as dts_solve would: typically disjoint

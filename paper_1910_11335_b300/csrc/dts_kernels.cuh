@@ -14,6 +14,7 @@
 //   xf   [8][B][NTy*NTz][NDO][TY*TZ] R  x-faces in flight (likewise yf, zf)
 #pragma once
 #include <cuda_runtime.h>
+#include <math_constants.h>
 #include <stdint.h>
 
 namespace dts {
@@ -1756,6 +1757,90 @@ __global__ void k_set_ctl(int* ctl, int g, int slot)
 {
     ctl[0] = g;
     ctl[1] = slot;
+}
+
+// ---------------------------------------------------------------------------
+// A7 on the device: the convergence control of one group's source iterations
+// when they run as a WHILE node of a CUDA graph. The decisions are those the
+// host makes after every iteration: a member stops when its residual is below
+// tol or, in the FP32 forms, when its residual has not improved by 1 % in 10
+// iterations; the loop goes on while a member iterates, the iteration cap is
+// not reached and no bounded wait has given up.
+// ---------------------------------------------------------------------------
+constexpr int kLoopThreads = 1024;
+constexpr int kLoopMaxMembers = 32 * kLoopThreads;   // one stop bit per member and thread
+
+struct LoopParams {
+    int B, G, max_iters, fp32_stop;
+    double tol;
+    const double* status;      // [B][4] residual and balance terms of the iteration (k_resid_final)
+    int* active;               // [B] members still iterating (read by the sweep and moment kernels)
+    int* ctl;                  // [0] group, [1] fixed-source slot
+    int* it;                   // iterations of the running group
+    int* last_improve;         // [B] iteration of the last 1 % improvement (FP32 forms)
+    double* best;              // [B] best residual so far (FP32 forms)
+    int* iters;                // [B][G] iterations per (member, group)
+    double* resid;             // [B][G] last residual
+    double* balance;           // [B][G][3] source, absorption, leakage of the last sweep
+    const int* err;            // the tensor-core forms' error word (a bounded wait gave up), or null
+    cudaGraphConditionalHandle h;
+};
+
+// group g starts: its control values, every member active, the loop state cleared
+__global__ void __launch_bounds__(kLoopThreads) k_loop_begin(const LoopParams q, int g, int slot)
+{
+    if (threadIdx.x == 0) {
+        q.ctl[0] = g;
+        q.ctl[1] = slot;
+        *q.it = 0;
+    }
+    for (int b = threadIdx.x; b < q.B; b += blockDim.x) {
+        q.active[b] = 1;
+        q.best[b] = CUDART_INF;
+        q.last_improve[b] = 0;
+        q.iters[(size_t)b * q.G + g] = 0;
+    }
+}
+
+// after each source iteration (one block of kLoopThreads): record every active member's residual and
+// balance, retire the members that stopped, set the WHILE node's condition
+__global__ void __launch_bounds__(kLoopThreads) k_loop_control(const LoopParams q)
+{
+    const int it = *q.it + 1, g = q.ctl[0];
+    unsigned stopped = 0u;
+    int goes_on = 0;
+    for (int j = 0, b = threadIdx.x; b < q.B; ++j, b += blockDim.x) {
+        if (!q.active[b]) continue;
+        const double* s = q.status + 4 * (size_t)b;
+        const size_t bg = (size_t)b * q.G + g;
+        q.iters[bg] = it;
+        q.resid[bg] = s[0];
+        q.balance[bg * 3 + 0] = s[1];
+        q.balance[bg * 3 + 1] = s[2];
+        q.balance[bg * 3 + 2] = s[3];
+        bool stop = q.tol > 0.0 && s[0] < q.tol;
+        if (!stop && q.fp32_stop && q.tol > 0.0) {
+            if (s[0] < 0.99 * q.best[b]) {
+                q.best[b] = s[0];
+                q.last_improve[b] = it;
+            } else if (it - q.last_improve[b] >= 10) {
+                stop = true;
+            }
+        }
+        if (stop) stopped |= 1u << j;
+        else goes_on = 1;
+    }
+    // as on the host: the flags of stopped members change only while some member goes on (the
+    // group ends otherwise, and the next group sets every flag again)
+    const int any = __syncthreads_or(goes_on);
+    if (any)
+        for (int j = 0, b = threadIdx.x; b < q.B; ++j, b += blockDim.x)
+            if (stopped >> j & 1u) q.active[b] = 0;
+    if (threadIdx.x == 0) {
+        *q.it = it;
+        const bool err = q.err && *q.err != 0;
+        cudaGraphSetConditional(q.h, (any && it < q.max_iters && !err) ? 1u : 0u);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -137,6 +137,15 @@ struct dts_problem {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph = nullptr, graph_red = nullptr;
+    // device-resident source iteration (dts_set_device_loop): per group one launch of graph_loop, a
+    // WHILE node whose body is the sweep, the moment graph and k_loop_control; the loop state lives
+    // in one allocation (loop_mem)
+    bool device_loop = false, recording_loop = false;
+    cudaGraphExec_t graph_loop = nullptr;
+    cudaGraphConditionalHandle loop_h = 0;
+    void* loop_mem = nullptr;
+    int *loop_it = nullptr, *loop_last = nullptr, *loop_iters = nullptr;
+    double *loop_best = nullptr, *loop_resid = nullptr, *loop_bal = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t eva = nullptr, evb = nullptr, evc = nullptr;   // around the two graph replays
     // adjoint buffers (allocated by the first dts_solve_adjoint, B = 1)
@@ -700,6 +709,7 @@ dts_status record_reduce(dts_problem* p)
                                                 count_of<double>(p, p->blk), count_of<double>(p, p->leak),
                                                 count_of<double>(p, p->status));
     p->graph_launches = p->n_stages + 2;
+    if (p->recording_loop) return DTS_OK;   // the device-resident loop reads the status on the device
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(double) * 4 * p->B, cudaMemcpyDeviceToHost,
                        p->stream));
     if (p->q_mode) CK(cudaMemcpyAsync(p->h_err, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
@@ -744,6 +754,72 @@ dts_status build_graph(dts_problem* p)
     return DTS_OK;
 }
 
+LoopParams loop_params(const dts_problem* p)
+{
+    LoopParams q;
+    q.B = p->B; q.G = p->G; q.max_iters = p->d.max_iters; q.fp32_stop = p->fp64 ? 0 : 1;
+    q.tol = p->d.tol; q.status = p->status; q.active = p->active; q.ctl = p->ctl;
+    q.it = p->loop_it; q.last_improve = p->loop_last; q.best = p->loop_best;
+    q.iters = p->loop_iters; q.resid = p->loop_resid; q.balance = p->loop_bal;
+    q.err = p->q_mode ? p->dev_err : nullptr; q.h = p->loop_h;
+    return q;
+}
+
+// the body of the device-resident loop: one source iteration (the kernels of both graphs, without the
+// status copies to the host) and the convergence control that sets the WHILE node's condition
+dts_status record_loop_body(dts_problem* p)
+{
+    p->recording_loop = true;
+    dts_status s = p->fp64 ? record_sweep<double>(p) : record_sweep<float>(p);
+    if (s == DTS_OK) s = p->fp64 ? record_reduce<double>(p) : record_reduce<float>(p);
+    p->recording_loop = false;
+    TRY(s);
+    k_loop_control<<<1, kLoopThreads, 0, p->stream>>>(loop_params(p));
+    CK(cudaGetLastError());
+    return DTS_OK;
+}
+
+// graph_loop: one WHILE node (condition 1 at every launch, so the body runs at least once); the
+// body's k_loop_control clears it when the group stops. It stops after max_iters iterations at most.
+dts_status build_loop_graph(dts_problem* p)
+{
+    if (p->graph_loop) return DTS_OK;
+    TRY(build_graph(p));   // the sweep kernel's shared-memory attribute
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    auto bail = [&](cudaError_t e, const char* what) {
+        cudaGraphDestroy(g);
+        return fail(p, DTS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaGraphConditionalHandleCreate(&p->loop_h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return bail(e, "cudaGraphConditionalHandleCreate");
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = p->loop_h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) return bail(e, "cudaGraphAddNode (while)");
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(p->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail(e, "cudaStreamBeginCaptureToGraph");
+    const dts_status s = record_loop_body(p);
+    e = cudaStreamEndCapture(p->stream, &body);
+    if (s != DTS_OK) {
+        cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return bail(e, "loop body capture");
+    e = cudaGraphInstantiate(&p->graph_loop, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        p->graph_loop = nullptr;
+        return fail(p, DTS_ERR_CUDA, std::string("loop graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return DTS_OK;
+}
+
 // fixed-source ring: (W+1) slots of [B][NT][K][TV] doubles
 dts_status ensure_ring(dts_problem* p)
 {
@@ -755,6 +831,10 @@ dts_status ensure_ring(dts_problem* p)
     if (p->graph_red) {
         cudaGraphExecDestroy(p->graph_red);
         p->graph_red = nullptr;
+    }
+    if (p->graph_loop) {
+        cudaGraphExecDestroy(p->graph_loop);
+        p->graph_loop = nullptr;
     }
     dfree(p, p->F);
     p->F = nullptr;
@@ -868,8 +948,20 @@ dts_status stream_group_output(dts_problem* p, int g)
 // complete_iteration) until the group's members stop, end_group; then finish.
 // NVTX ranges are start/end ranges (not a push/pop stack), since the steps of
 // interleaved problems do not nest.
+// the device-resident loop serves a solve when it is switched on and no per-iteration callback is set;
+// the bounds-checked build reads its check word on the host after every iteration, so it keeps the host loop
+bool use_device_loop(const dts_problem* p)
+{
+#ifdef DTS_DEBUG_BOUNDS
+    return false;
+#else
+    return p->device_loop && !p->on_iter && p->loop_mem && p->B <= kLoopMaxMembers;
+#endif
+}
+
 struct SolveRun {
     dts_problem* p;
+    const bool dev;   // the group's source iterations run as one graph launch (dts_set_device_loop)
     int B, G, W1;
     int g = 0, it = 0, n_active = 0;
     int64_t updates = 0, sweeps = 0, sweep_launches = 0, launches = 0;
@@ -880,7 +972,8 @@ struct SolveRun {
     nvtxRangeId_t r_solve = 0, r_group = 0, r_iter = 0;
 
     explicit SolveRun(dts_problem* pp)
-        : p(pp), B(pp->B), G(pp->G), W1(pp->W + 1), u_per_sweep((int64_t)pp->V * pp->nd), best(pp->B),
+        : p(pp), dev(use_device_loop(pp)), B(pp->B), G(pp->G), W1(pp->W + 1),
+          u_per_sweep((int64_t)pp->V * pp->nd), best(pp->B),
           last_improve(pp->B)
     {
     }
@@ -904,6 +997,7 @@ struct SolveRun {
 #endif
         TRY(ensure_ring(p));
         TRY(build_graph(p));
+        if (dev) TRY(build_loop_graph(p));
         if (p->q_mode) {
             CK(cudaMemsetAsync(p->dev_err, 0, sizeof(int), p->stream));
             *p->h_err = 0;
@@ -948,17 +1042,23 @@ struct SolveRun {
         snprintf(gname, sizeof gname, "group %d", g);
         r_group = nvtxRangeStartA(gname);
         const int slot = g % W1;
-        k_set_ctl<<<1, 1, 0, p->stream>>>(p->ctl, g, slot);
-        CK(cudaMemsetAsync(p->phi00, 0, sizeof(double) * B * p->NC, p->stream));
-        for (int b = 0; b < B; ++b) {
-            p->h_active[b] = 1;
-            p->iters[(size_t)b * G + g] = 0;
-            best[b] = INFINITY;
-            last_improve[b] = 0;
+        if (dev) {   // the same set-up on the device: control values, flags, loop state
+            k_loop_begin<<<1, kLoopThreads, 0, p->stream>>>(loop_params(p), g, slot);
+        } else {
+            k_set_ctl<<<1, 1, 0, p->stream>>>(p->ctl, g, slot);
         }
-        // every member is active again before the group's first source is formed (the
-        // tensor-core forms' Q = M F skips inactive members)
-        CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+        CK(cudaMemsetAsync(p->phi00, 0, sizeof(double) * B * p->NC, p->stream));
+        if (!dev) {
+            for (int b = 0; b < B; ++b) {
+                p->h_active[b] = 1;
+                p->iters[(size_t)b * G + g] = 0;
+                best[b] = INFINITY;
+                last_improve[b] = 0;
+            }
+            // every member is active again before the group's first source is formed (the
+            // tensor-core forms' Q = M F skips inactive members)
+            CK(cudaMemcpyAsync(p->active, p->h_active, sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+        }
         if (p->fp64) {
             launch_group_xs<double>(p, g);
             TRY(launch_group_init<double>(p, g, slot));
@@ -977,6 +1077,15 @@ struct SolveRun {
 
     // the group goes on while a member iterates and the iteration cap is not reached
     bool group_iterating() const { return n_active > 0 && it < p->d.max_iters; }
+
+    // device-resident loop: all of the group's source iterations as one graph launch; the host
+    // learns their counts, residuals and balance when the solve finishes
+    dts_status launch_group_loop()
+    {
+        CK(cudaGraphLaunch(p->graph_loop, p->stream));
+        n_active = 0;
+        return DTS_OK;
+    }
 
     // one source iteration (the sweep graph, then the moment graph) enqueued
     dts_status launch_iteration()
@@ -1056,7 +1165,7 @@ struct SolveRun {
     // next group, or the end of the solve
     dts_status end_group()
     {
-        for (int b = 0; b < B; ++b) {
+        for (int b = 0; !dev && b < B; ++b) {   // device-resident loop: in finish()
             const size_t bg = (size_t)b * G + g;
             max_res = std::max(max_res, p->resid[bg]);
             if (p->d.tol > 0.0 && !(p->resid[bg] < p->d.tol)) all_conv = false;
@@ -1080,6 +1189,38 @@ struct SolveRun {
         return DTS_OK;
     }
 
+    // device-resident loop, once the solve's work is complete: the per-(member, group) iteration
+    // counts, residuals and balance terms, and from them the counts the host loop keeps as it goes
+    dts_status collect_device_loop()
+    {
+        const size_t BG = (size_t)B * G;
+        CK(cudaMemcpyAsync(p->iters.data(), p->loop_iters, sizeof(int32_t) * BG, cudaMemcpyDeviceToHost,
+                           p->stream));
+        CK(cudaMemcpyAsync(p->resid.data(), p->loop_resid, sizeof(double) * BG, cudaMemcpyDeviceToHost,
+                           p->stream));
+        CK(cudaMemcpyAsync(p->balance.data(), p->loop_bal, sizeof(double) * 3 * BG, cudaMemcpyDeviceToHost,
+                           p->stream));
+        if (p->q_mode) CK(cudaMemcpyAsync(p->h_err, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+        if (p->q_mode && *p->h_err)
+            return fail(p, DTS_ERR_TIMEOUT, "k_moments_q: a bounded wait on a bulk copy or the tensor cores gave up");
+        for (int gg = 0; gg < G; ++gg) {
+            int trips = 0;   // the WHILE node's iterations: every one counts the members still active
+            for (int b = 0; b < B; ++b) {
+                const size_t bg = (size_t)b * G + gg;
+                const int n_it = p->iters[bg];
+                trips = std::max(trips, n_it);
+                updates += (int64_t)n_it * u_per_sweep;
+                sweeps += n_it;
+                max_res = std::max(max_res, p->resid[bg]);
+                if (p->d.tol > 0.0 && !(p->resid[bg] < p->d.tol)) all_conv = false;
+            }
+            launches += (int64_t)trips * (p->graph_launches + 1);   // + k_loop_control
+            sweep_launches += (int64_t)trips * p->n_stages;
+        }
+        return DTS_OK;
+    }
+
     dts_status finish(dts_solve_stats* st)
     {
         CK(cudaEventRecord(p->ev1, p->stream));
@@ -1088,6 +1229,7 @@ struct SolveRun {
             CK(cudaStreamSynchronize(p->copy_stream));
             p->copied_pending[0] = p->copied_pending[1] = false;
         }
+        if (dev) TRY(collect_device_loop());
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
         p->solved = true;
@@ -1116,6 +1258,13 @@ dts_status run_solve(dts_problem* p, dts_solve_stats* st)
 {
     SolveRun r(p);
     TRY(r.start());
+    if (r.dev) {   // every group enqueued now: no host round trip per iteration
+        while (!r.done) {
+            TRY(r.launch_group_loop());
+            TRY(r.end_group());
+        }
+        return r.finish(st);
+    }
     while (!r.done) {
         while (r.group_iterating()) {
             TRY(r.launch_iteration());
@@ -1443,6 +1592,7 @@ void destroy(dts_problem* p)
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->graph_red) cudaGraphExecDestroy(p->graph_red);
+    if (p->graph_loop) cudaGraphExecDestroy(p->graph_loop);
     for (void* a : p->allocs) cudaFree(a);
     p->allocs.clear();
     if (p->h_status) cudaFreeHost(p->h_status);
@@ -1968,7 +2118,21 @@ dts_status dts_solve_many(dts_problem* const* problems, int n, dts_solve_stats* 
         const dts_status s = runs[i]->start();
         if (s != DTS_OK) return abort_all(i, s);
     }
+    // problems with the device-resident loop: every group enqueued on their streams now; they run
+    // beside the others with no host step until they finish
     int remaining = n;
+    for (int i = 0; i < n; ++i) {
+        SolveRun& r = *runs[i];
+        if (!r.dev) continue;
+        dts_status s = DTS_OK;
+        while (s == DTS_OK && !r.done) {
+            s = r.launch_group_loop();
+            if (s == DTS_OK) s = r.end_group();
+        }
+        if (s != DTS_OK) return abort_all(i, s);
+        finished[i] = 1;
+        --remaining;
+    }
     while (remaining > 0) {
         bool progressed = false;
         for (int i = 0; i < n; ++i) {
@@ -2001,6 +2165,18 @@ dts_status dts_solve_many(dts_problem* const* problems, int n, dts_solve_stats* 
             if (s != DTS_OK) return abort_all(i, s);
         }
         if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!runs[i]->dev) continue;
+        const dts_status s = runs[i]->finish(stats ? &stats[i] : nullptr);
+        if (s == DTS_ERR_NOT_CONVERGED) {
+            if (first_soft == DTS_OK) {
+                first_soft = s;
+                g_thread_error = problems[i]->err;
+            }
+        } else if (s != DTS_OK) {
+            return abort_all(i, s);
+        }
     }
     return first_soft;
 }
@@ -2230,6 +2406,28 @@ dts_status dts_set_host_output(dts_problem* p, dts_component comp, double* host,
     p->host_out = host;
     p->host_comp = (int)comp;
     p->copied_pending[0] = p->copied_pending[1] = false;
+    return DTS_OK;
+}
+
+dts_status dts_set_device_loop(dts_problem* p, int on)
+{
+    if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (on && !p->loop_mem) {
+        // one allocation: it, last_improve [B], iters [B][G] (ints); best [B], resid [B][G],
+        // balance [B][G][3] (doubles, 8-byte aligned)
+        const size_t B = (size_t)p->B, BG = B * (size_t)p->G;
+        const size_t ints = ((1 + B + BG) * sizeof(int) + 7) & ~size_t(7);
+        DevGuard guard(p->d.device);
+        TRY(dalloc(p, &p->loop_mem, ints + sizeof(double) * (B + 4 * BG)));
+        char* m = static_cast<char*>(p->loop_mem);
+        p->loop_it = reinterpret_cast<int*>(m);
+        p->loop_last = p->loop_it + 1;
+        p->loop_iters = p->loop_last + B;
+        p->loop_best = reinterpret_cast<double*>(m + ints);
+        p->loop_resid = p->loop_best + B;
+        p->loop_bal = p->loop_resid + BG;
+    }
+    p->device_loop = on != 0;
     return DTS_OK;
 }
 

@@ -77,7 +77,7 @@ EXPORTS = ("dts_create_problem", "dts_set_materials", "dts_set_source", "dts_sol
            "dts_tune_tile", "dts_set_source_cones", "dts_get_dose", "dts_debug_fail_allocation",
            "dts_solve_many", "dts_tune_cache_file", "dts_set_iteration_callback",
            "dts_debug_bounds_selftest", "dts_set_initial_guess", "dts_debug_poison_wait",
-           "dts_set_host_output")
+           "dts_set_host_output", "dts_set_device_loop")
 
 
 def lib():
@@ -119,6 +119,7 @@ def lib():
         "dts_debug_poison_wait": ([C.c_void_p, C.c_int], C.c_int),
         "dts_set_host_output": ([C.c_void_p, C.c_int, C.c_void_p, C.c_size_t], C.c_int),
         "dts_set_iteration_callback": ([C.c_void_p, IterationFn, C.c_void_p], C.c_int),
+        "dts_set_device_loop": ([C.c_void_p, C.c_int], C.c_int),
         "dts_solve_adjoint": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_int], C.c_int),
         "dts_get_adjoint_iterations": ([C.c_void_p, _ip, C.c_size_t], C.c_int),
@@ -337,6 +338,11 @@ class Problem:
         self._iter_cb = IterationFn(tramp)   # kept alive with the problem
         _check(lib().dts_set_iteration_callback(self._h, self._iter_cb, None), self._h)
 
+    def set_device_loop(self, on: bool):
+        """Run each group's source iterations as one CUDA-graph launch with the
+        convergence decisions made on the device (dts_set_device_loop)."""
+        _check(lib().dts_set_device_loop(self._h, int(bool(on))), self._h)
+
     # solve
     def solve(self, allow_not_converged: bool = False) -> SolveStats:
         st = SolveStats()
@@ -459,7 +465,7 @@ def source_parts(n_sources: int, parts: int, sn_order: int):
 
 def problem_from_workload(w: inputs.Workload, precision=PREC_FP64, tol=None, max_iters=None,
                           tile=(0, 0, 0), keep_moments=False, device=0, stream=None,
-                          sources=None) -> Problem:
+                          sources=None, device_loop=False) -> Problem:
     """Create a Problem for workload w and upload its materials and sources
     (all of w.sources, or the subset `sources`)."""
     srcs = w.sources if sources is None else [w.sources[i] for i in sources]
@@ -473,4 +479,6 @@ def problem_from_workload(w: inputs.Workload, precision=PREC_FP64, tol=None, max
                     None if w.scale_s is None else w.scale_s.reshape(-1))
     for b, s in enumerate(srcs):
         p.set_source(b, s)
+    if device_loop:
+        p.set_device_loop(True)
     return p
