@@ -211,13 +211,16 @@ def run_reference(args):
 # Per-kernel constants measured with ncu on a small case (48^3, 32 sources, S8 P3, 2 groups, 8 x 4 x 4
 # tiles; profiles/k_sweep_batch_cone48_s8p3_x32.md, profiles/k_moments_q_cone48_s8p3_x32.md), used while
 # the kernel's source block is the one that was profiled (its SHA-256), else reported null:
-#   inst_per_update    warp instructions issued per cell-direction update (smsp__inst_executed.sum)
+#   inst_per_update    warp instructions issued per cell-direction update (smsp__inst_executed.sum);
+#                      the Q-input sweep's is the benchmark phantom's at 96^3 over all 19 groups (3
+#                      sources, 2 iterations per group, every sweep launch of the solve:
+#                      profiles/k_sweep_batch_cone96_s8p3_x3_19g.md)
 #   dram_over_design   dram__bytes_read.sum + dram__bytes_write.sum over the design's bytes per update
 #   fma_pipe           sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active / 100
 # The DRAM ratios are a 48^3 case's; at 96^3 the tile-to-tile faces, which make most of the sweep's
 # excess, are the same bytes per update and only their L2 hit rate can differ.
 MEASURED = {
-    "k_sweep_batch (Q input)": {"inst_per_update": 2.059, "dram_over_design": 1.280, "fma_pipe": 0.1909,
+    "k_sweep_batch (Q input)": {"inst_per_update": 1.761, "dram_over_design": 1.280, "fma_pipe": 0.1909,
                                 "block": "sweep"},
     "k_sweep_batch": {"inst_per_update": 2.819, "dram_over_design": 1.147, "fma_pipe": 0.2484, "block": "sweep"},
     "k_moments_q": {"inst_per_update": 0.554, "dram_over_design": 0.999, "fma_pipe": 0.1422,
