@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--split", type=int, default=4,
                     help="solve each GPU's sources as this many problems on their own streams "
                          "(dts_solve_many: one part's moment kernels beside another's sweep); 1 = one problem")
-    ap.add_argument("--loop", default="device", choices=["device", "host"],
-                    help="source iterations of a group as one CUDA-graph launch with the convergence "
-                         "decisions on the device (dts_set_device_loop), or one host round trip each")
+    ap.add_argument("--loop", default="host", choices=["host", "device"],
+                    help="host: one host round trip per source iteration (the kernels the launch-list "
+                         "profile covers); device: a group's source iterations as one CUDA-graph launch "
+                         "with the convergence decisions on the device (dts_set_device_loop)")
     return ap.parse_args()
 
 
