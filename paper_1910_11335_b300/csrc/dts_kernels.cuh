@@ -17,6 +17,8 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include "dts_ptx.cuh"
+
 namespace dts {
 
 // ---------------------------------------------------------------------------
@@ -165,6 +167,7 @@ struct SweepParams {
     double* leak;                  // [B][8][NT] leakage of each (source, octant, tile) sweep, or null
     // element counts of the buffers above (checked in the DTS_DEBUG_BOUNDS build)
     size_t n_stage_tiles, n_T, n_sigt, n_part, n_xf, n_yf, n_zf, n_leak;
+    int* err = nullptr;            // set when a bounded wait on a bulk copy gave up (Q-input sweep), or null
 };
 
 template <typename R, int NDO, int K>
@@ -663,7 +666,9 @@ struct BatchShape {
     static constexpr int oY = oX + (QIN ? 0 : fxn * 32);    // [BX][32] y faces of one z-layer, slot = lx
     static constexpr int oZ = oY + BX * 32;             // [fzn][32] z faces, slot = ly * BX + lx
     static constexpr int oS = oZ + fzn * 32;            // [NLINE][BX] sigma_t, local line, storage x
-    static constexpr int nF = (oS + BV + 3) & ~3;
+    // with the Q input, two mbarriers (8 bytes each) of the bulk copies that land the faces
+    static constexpr int oB = (oS + BV + 3) & ~3;
+    static constexpr int nF = oB + (QIN ? 4 : 0);
     static constexpr size_t bytes = sizeof(float) * nF;
 };
 
@@ -842,6 +847,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     float* fy = smf + S::oY;
     float* fz = smf + S::oZ;
     float* sg = smf + S::oS;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smf + S::oB);   // Q input: [0] tile prologue, [1] y layers
 
     const int lane = threadIdx.x;
     const int b0 = grp * SB, nb = min(SB, p.B - b0);
@@ -998,9 +1004,24 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     float* gx = p.xf + ((og * (p.NTy * p.NTz) + (tz * p.NTy + ty)) * fxn) * 32;
     float* gy = p.yf + ((og * (p.NTx * p.NTz) + (tz * p.NTx + tx)) * fyn) * 32;
     float* gz = p.zf + ((og * (p.NTx * p.NTy) + (ty * p.NTx + tx)) * fzn) * 32;
-    if constexpr (!QIN) batch_faces_in_async<fxn>(fx, gx, ta > 0);   // land with the first line's sources
-    batch_faces_in_async<BX>(fy, gy, tb > 0);    // z-layer 0; later layers stream in with the lines
-    batch_faces_in_async<fzn>(fz, gz, tc > 0);
+    if constexpr (QIN) {
+        // the tile's incoming z-faces and z-layer 0's y-faces: one bulk copy (TMA) each from their
+        // contiguous face blocks, issued by lane 0 on bars[0]; on an inflow boundary the lanes write zeros
+        if (lane == 0) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+            fence_mbar_init();
+            mbar_expect_tx(&bars[0], (tc > 0 ? fzn * 128u : 0u) + (tb > 0 ? BX * 128u : 0u));
+            if (tc > 0) bulk_load(fz, gz, fzn * 128u, &bars[0]);
+            if (tb > 0) bulk_load(fy, gy, BX * 128u, &bars[0]);
+        }
+        if (tc == 0) batch_faces_in_async<fzn>(fz, gz, false);   // zeros
+        if (tb == 0) batch_faces_in_async<BX>(fy, gy, false);
+    } else {
+        batch_faces_in_async<fxn>(fx, gx, ta > 0);   // land with the first line's sources
+        batch_faces_in_async<BX>(fy, gy, tb > 0);    // z-layer 0; later layers stream in with the lines
+        batch_faces_in_async<fzn>(fz, gz, tc > 0);
+    }
     cp_async_commit();
     float xn = 0.f, xsum = 0.f;   // Q input: the next line's incoming x-face; the outgoing ones' sum
     if constexpr (QIN) xn = ta > 0 ? gx[lane] : 0.f;
@@ -1019,6 +1040,20 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         __syncwarp();
         const int ly = line % BY, lz = line / BY;
         const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
+        if constexpr (QIN) {
+            // a layer's first line: line 0 waits for the tile's faces (bars[0]), later layers for their
+            // y-faces (bars[1], the (lz - 1)-th copy on it); a wait that gives up ends the sweep of the tile
+            if (ly == 0 && (lz == 0 || tb > 0)) {
+                uint64_t* bar = lz == 0 ? &bars[0] : &bars[1];
+                const uint32_t parity = lz == 0 ? 0u : (uint32_t)((lz - 1) & 1);
+                if (!__all_sync(0xffffffffu, mbar_wait(bar, parity))) {
+                    if (lane == 0 && p.err) atomicExch(p.err, 1);
+                    (void)mbar_wait(bar, parity);   // its copies, should they still land (bounded)
+                    __syncwarp();
+                    return;
+                }
+            }
+        }
 
         // A: Q for the line's cells, two cells per packed FMA, storage x order
         // (Q input: the line's sources were loaded during the previous line's walk)
@@ -1054,7 +1089,17 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         __syncwarp();
         // the layer's y-faces went to registers during line ly = 0; the next layer's land in the
         // same buffer with the next line's sources
-        if (ly == 1 && lz + 1 < BZ) batch_faces_in_async<BX>(fy, gy + (size_t)(lz + 1) * BX * 32, tb > 0);
+        if constexpr (QIN) {
+            // the next layer's y-faces (bulk copy on bars[1]) into the buffer whose values every lane read
+            // into registers during line ly = 0 (ordered by the __syncwarp above)
+            if (ly == 1 && lz + 1 < BZ && tb > 0 && lane == 0) {
+                fence_async_smem();
+                mbar_expect_tx(&bars[1], BX * 128u);
+                bulk_load(fy, gy + (size_t)(lz + 1) * BX * 32, BX * 128u, &bars[1]);
+            }
+        } else {
+            if (ly == 1 && lz + 1 < BZ) batch_faces_in_async<BX>(fy, gy + (size_t)(lz + 1) * BX * 32, tb > 0);
+        }
         if constexpr (!QIN) {
             if (line + 1 < S::NLINE) stage_line(line + 1, 0);
         } else {
@@ -1141,8 +1186,18 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     }
 
     // outgoing faces; the lane's own faces leaving the grid are its leakage
-    if constexpr (!QIN) batch_faces_out<fxn>(fx, gx);
-    batch_faces_out<fzn>(fz, gz);
+    if constexpr (QIN) {
+        // the z-faces by one bulk store (TMA) once every lane's stores are visible to the async proxy
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            bulk_store(gz, fz, fzn * 128u);
+            bulk_commit();
+        }
+    } else {
+        batch_faces_out<fxn>(fx, gx);
+        batch_faces_out<fzn>(fz, gz);
+    }
     const bool lbx = negx ? tx == 0 : tx == p.NTx - 1;
     const bool lby = negy ? ty == 0 : ty == p.NTy - 1;
     const bool lbz = negz ? tz == 0 : tz == p.NTz - 1;
@@ -1168,12 +1223,13 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         for (int dd = 0; dd < NDO; ++dd) tot += __shfl_sync(0xffffffffu, lk, (srcok ? bl : 0) * NDO + dd);
     }
     if (srcok && d == 0 && p.leak) p.leak[((size_t)(b0 + bl) * 8 + oct) * p.NT + tile] = tot;
+    if (QIN && lane == 0) bulk_wait_read();   // the store has read the z-faces before the CTA's memory goes
 }
 
 // s0, cnt: the stage's first entry in stage_tiles and its tile count (kernel
 // arguments, so a CTA's first dependent global load is its tile)
 template <int NDO, int K, int BX, bool PSI, bool QIN = false>
-__global__ void __launch_bounds__(32, 17) k_sweep_batch(const SweepParams<float> p, const int s0, const int cnt)
+__global__ void __launch_bounds__(32, QIN ? 28 : 17) k_sweep_batch(const SweepParams<float> p, const int s0, const int cnt)
 {
     using S = BatchShape<NDO, K, BX, PSI, QIN>;
     int bid = blockIdx.x;

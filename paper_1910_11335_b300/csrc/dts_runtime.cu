@@ -642,6 +642,7 @@ dts_status record_sweep(dts_problem* p)
     sp.n_sigt = count_of<R>(p, p->sigt_r); sp.n_part = count_of<R>(p, p->part);
     sp.n_xf = count_of<R>(p, p->xf); sp.n_yf = count_of<R>(p, p->yf); sp.n_zf = count_of<R>(p, p->zf);
     sp.n_leak = count_of<double>(p, p->leak);
+    sp.err = p->q_mode ? p->dev_err : nullptr;
     const size_t smem = sweep_smem(p);
     if constexpr (sizeof(R) == 4) {
         if (batch_tile(p)) {   // the batched kernel takes the stage's (first tile, count) directly
