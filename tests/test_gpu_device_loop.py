@@ -191,3 +191,24 @@ def test_device_loop_bounded_wait_runs_out():
     p.solve(allow_not_converged=True)
     for b in range(2):
         assert np.array_equal(p.fluence(b, dts.TOTAL), ref.fluence(b, dts.TOTAL))
+
+
+@pytest.mark.parametrize("prec", [dts.PREC_FP64, dts.PREC_FP32_SPLITBF16], ids=["fp64", "splitbf16"])
+def test_device_loop_restart_from_saved_moments(prec):
+    """An initial guess (dts_set_initial_guess) on some members: the device loop starts from it as the
+    host loop does (same counts, residuals and fluence bit for bit), and a converged guess stops after
+    at most two iterations per group."""
+    w = _mixed_workload(4)
+    G = w.n_groups
+    tol = 1e-8 if prec == dts.PREC_FP64 else 1e-6
+    a = dts.problem_from_workload(w, precision=prec, tol=tol, max_iters=300, tile=(8, 4, 4), keep_moments=True)
+    a.solve(allow_not_converged=True)
+    guess = {m: np.stack([a.moments(m, g) for g in range(G)]) for m in (0, 2)}
+    h, d = _pair(w, prec, tol, 300, keep_moments=True)   # default starts first
+    for p, _ in (h, d):
+        for m, mom in guess.items():
+            p.set_initial_guess(m, mom)
+    sh = h[0].solve(allow_not_converged=True)
+    sd = d[0].solve(allow_not_converged=True)
+    _same((h[0], sh), (d[0], sd), 4)
+    assert (d[0].iterations()[[0, 2]] <= 2).all()
