@@ -48,7 +48,8 @@ typedef enum {
     DTS_ERR_OOM = 3,            /* device or host allocation failed */
     DTS_ERR_CUDA = 4,           /* a CUDA runtime call failed */
     DTS_ERR_NOT_CONVERGED = 5,  /* max_iters reached above tol; results are usable */
-    DTS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up (tensor-core forms) */
+    DTS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up (tensor-core forms: the moment
+                                   kernel's waits on its copies and MMAs, the sweep's on its face copies) */
     DTS_ERR_INTERNAL = 7        /* a device-side consistency check failed */
 } dts_status;
 
@@ -447,7 +448,8 @@ dts_status dts_debug_bounds_selftest(int plant, int *is_debug_build);
  * bounded: it gives up after about a second, the kernel records the failure in
  * a device error word, leaves its item loop with no copy or MMA in flight,
  * frees its tensor memory and returns, and the solve returns DTS_ERR_TIMEOUT
- * after that iteration. With on != 0 every later solve of p makes the flux-stage
+ * after that iteration. (The sweep of these forms waits on mbarriers for its
+ * face copies with the same bound and error word; the hook does not reach it.) With on != 0 every later solve of p makes the flux-stage
  * waits expect 16 bytes that no copy delivers, so they run out (no fault, no
  * trap: the waits end by their bound); on = 0 restores normal operation, and
  * the problem solves correctly again. Errors: DTS_ERR_INVALID_ARG (p NULL),
