@@ -108,3 +108,66 @@ def dense_solve(w, quad, source_dirs=None, phi_u=None, omega_u=None):
         psi_all[g] = x.reshape(V, nd, 4)[:, :, 0]
     phi = psi_all @ wt
     return psi_all, phi
+
+
+def dense_system(w, quad):
+    """The whole multigroup system of workload w (one volumetric source, kind 0)
+    as ONE dense matrix: unknowns (g, v, n, t), t = 0 the cell-average flux and
+    t = 1..3 the x, y, z outflow; per (g, v, n) the balance row
+        sigma_t psi_c + sum_d a_d/2 (psi_out,d - psi_in,d)
+            - sum_{g' <= g} sum_n' K^{g'->g}_{n n'} psi_c(g', n') = q/(4 pi)
+    (downscatter as blocks below the diagonal) and the three closures
+    2 psi_c - psi_in,d - psi_out,d = 0. Returns (A, b, idx) with idx(g, v, n, t)
+    the unknown's index, plus the per-cell kernel blocks K[v][g'][g] ([nd][nd])
+    and sigma_t[V][G], so that derivatives of A with respect to per-voxel
+    multipliers of sigma_t and sigma_s can be written down directly."""
+    mu, eta, xi, wt = quad
+    nd, G, V = len(wt), w.n_groups, w.n_voxels
+    nx, ny, nz = w.nx, w.ny, w.nz
+    L = w.legendre_order
+    omega = np.stack([mu, eta, xi], axis=1)
+    Pl = np.stack([_pl(l, omega @ omega.T) for l in range(L + 1)])
+    mat = w.mat_id.reshape(-1)
+    sig_t = w.sigma_t[mat].copy()
+    sig_s = w.sigma_s[mat].copy()
+    a = np.stack([2 * np.abs(mu) / w.dx, 2 * np.abs(eta) / w.dy, 2 * np.abs(xi) / w.dz], axis=1)
+    src = w.sources[0]
+    assert src.kind == 0
+
+    def idx(g, v, n, t):
+        return ((g * V + v) * nd + n) * 4 + t
+
+    Kb = np.zeros((V, G, G, nd, nd))
+    for v in range(V):
+        for gf in range(G):
+            for gt in range(gf, G):
+                for l in range(L + 1):
+                    Kb[v, gf, gt] += (2 * l + 1) / (4 * np.pi) * sig_s[v, l, gf, gt] * Pl[l]
+                Kb[v, gf, gt] *= wt[None, :]
+    nunk = G * V * nd * 4
+    A = np.zeros((nunk, nunk))
+    b = np.zeros(nunk)
+    for g in range(G):
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    v = (k * ny + j) * nx + i
+                    for n in range(nd):
+                        r = idx(g, v, n, 0)
+                        A[r, r] += sig_t[v, g]
+                        for gp in range(g + 1):
+                            A[r, [idx(gp, v, m, 0) for m in range(nd)]] -= Kb[v, gp, g, n]
+                        b[r] = src.q[g, v] / (4 * np.pi)
+                        step = (int(np.sign(mu[n])), int(np.sign(eta[n])), int(np.sign(xi[n])))
+                        up = [(i - step[0], j, k), (i, j - step[1], k), (i, j, k - step[2])]
+                        for d in range(3):
+                            A[r, idx(g, v, n, 1 + d)] += 0.5 * a[n, d]
+                            rc = idx(g, v, n, 1 + d)
+                            A[rc, r] += 2.0
+                            A[rc, rc] -= 1.0
+                            ii, jj, kk = up[d]
+                            if 0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz:
+                                vu = (kk * ny + jj) * nx + ii
+                                A[r, idx(g, vu, n, 1 + d)] -= 0.5 * a[n, d]
+                                A[rc, idx(g, vu, n, 1 + d)] -= 1.0
+    return A, b, idx, Kb, sig_t
