@@ -443,17 +443,21 @@ dts_status dts_tune_cache_file(const char *path);
 dts_status dts_debug_bounds_selftest(int plant, int *is_debug_build);
 
 /*
- * Failure-path test hook of the tensor-core forms, whose moment kernel waits
- * on mbarriers for its bulk copies and tensor-core results. Every such wait is
+ * Failure-path test hook of the tensor-core forms, whose kernels wait on
+ * mbarriers: the moment kernel for its bulk copies and tensor-core results,
+ * the sweep for the bulk copies of its face blocks. Every such wait is
  * bounded: it gives up after about a second, the kernel records the failure in
- * a device error word, leaves its item loop with no copy or MMA in flight,
- * frees its tensor memory and returns, and the solve returns DTS_ERR_TIMEOUT
- * after that iteration. (The sweep of these forms waits on mbarriers for its
- * face copies with the same bound and error word; the hook does not reach it.) With on != 0 every later solve of p makes the flux-stage
- * waits expect 16 bytes that no copy delivers, so they run out (no fault, no
- * trap: the waits end by their bound); on = 0 restores normal operation, and
- * the problem solves correctly again. Errors: DTS_ERR_INVALID_ARG (p NULL),
- * DTS_ERR_STATE (not a tensor-core form), DTS_ERR_CUDA.
+ * a device error word and returns (the moment kernel leaves its item loop with
+ * no copy or MMA in flight and frees its tensor memory; the sweep's warp waits,
+ * again bounded, for its face copies and leaves its tile), and the solve
+ * returns DTS_ERR_TIMEOUT after that iteration (with the device-resident loop:
+ * when the solve finishes). With on = 1 every later solve of p makes the moment
+ * kernel's flux-stage waits expect 16 bytes that no copy delivers; with on = 2
+ * the sweep's first face wait of every tile does (the sweep's captured graphs
+ * are made again with that byte count). The waits then run out -- no fault, no
+ * trap: they end by their bound. on = 0 restores normal operation, and the
+ * problem solves correctly again. Errors: DTS_ERR_INVALID_ARG (p NULL, on not
+ * 0, 1 or 2), DTS_ERR_STATE (not a tensor-core form), DTS_ERR_CUDA.
  */
 dts_status dts_debug_poison_wait(dts_problem *p, int on);
 dts_status dts_moment_tables(int sn_order, int legendre_order, double *D, double *M);

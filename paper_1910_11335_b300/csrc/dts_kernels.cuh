@@ -168,6 +168,7 @@ struct SweepParams {
     // element counts of the buffers above (checked in the DTS_DEBUG_BOUNDS build)
     size_t n_stage_tiles, n_T, n_sigt, n_part, n_xf, n_yf, n_zf, n_leak;
     int* err = nullptr;            // set when a bounded wait on a bulk copy gave up (Q-input sweep), or null
+    unsigned poison_tx = 0;        // test hook (dts_debug_poison_wait): bytes the face wait expects beyond its copies
 };
 
 template <typename R, int NDO, int K>
@@ -1011,7 +1012,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
             mbar_init(&bars[0], 1);
             mbar_init(&bars[1], 1);
             fence_mbar_init();
-            mbar_expect_tx(&bars[0], (tc > 0 ? fzn * 128u : 0u) + (tb > 0 ? BX * 128u : 0u));
+            mbar_expect_tx(&bars[0], (tc > 0 ? fzn * 128u : 0u) + (tb > 0 ? BX * 128u : 0u) + p.poison_tx);
             if (tc > 0) bulk_load(fz, gz, fzn * 128u, &bars[0]);
             if (tb > 0) bulk_load(fy, gy, BX * 128u, &bars[0]);
         }

@@ -89,7 +89,8 @@ struct dts_problem {
     float* Mop = nullptr;             // operator parts M' = 4 pi M, [2][NP][16]
     float* Dop = nullptr;             // Eq. 3 operator parts D, [2][16][N_d] (N_d a multiple of 16)
     int* dev_err = nullptr;           // device error word of the bounded waits
-    int* dev_poison = nullptr;        // dts_debug_poison_wait's flag (tensor-core forms)
+    int* dev_poison = nullptr;        // dts_debug_poison_wait's flag of the moment kernel (tensor-core forms)
+    unsigned poison_sweep_tx = 0;     // dts_debug_poison_wait: bytes no copy delivers, added to the sweep's face wait
     int* h_err = nullptr;             // pinned copy, read after every iteration
     size_t rsz = 8;                   // sizeof(R)
     std::vector<int> stage_off_h;     // [n_stages+1]
@@ -643,6 +644,7 @@ dts_status record_sweep(dts_problem* p)
     sp.n_xf = count_of<R>(p, p->xf); sp.n_yf = count_of<R>(p, p->yf); sp.n_zf = count_of<R>(p, p->zf);
     sp.n_leak = count_of<double>(p, p->leak);
     sp.err = p->q_mode ? p->dev_err : nullptr;
+    sp.poison_tx = p->q_mode ? p->poison_sweep_tx : 0u;
     const size_t smem = sweep_smem(p);
     if constexpr (sizeof(R) == 4) {
         if (batch_tile(p)) {   // the batched kernel takes the stage's (first tile, count) directly
@@ -2376,11 +2378,21 @@ dts_status dts_set_initial_guess(dts_problem* p, int batch_index, const double* 
 dts_status dts_debug_poison_wait(dts_problem* p, int on)
 {
     if (!p) return fail(nullptr, DTS_ERR_INVALID_ARG, "problem is NULL");
+    if (on < 0 || on > 2) return fail(p, DTS_ERR_INVALID_ARG, "on must be 0, 1 or 2");
     if (!p->dev_poison) return fail(p, DTS_ERR_STATE, "only the tensor-core forms have device-side waits");
     DevGuard guard(p->d.device);
-    const int v = on ? 1 : 0;
+    const int v = on == 1 ? 1 : 0;
     CK(cudaStreamSynchronize(p->stream));
     CK(cudaMemcpy(p->dev_poison, &v, sizeof v, cudaMemcpyHostToDevice));
+    const unsigned tx = on == 2 ? 16u : 0u;
+    if (tx != p->poison_sweep_tx) {   // a sweep parameter: the captured graphs are made again
+        p->poison_sweep_tx = tx;
+        for (cudaGraphExec_t* g : {&p->graph, &p->graph_red, &p->graph_loop})
+            if (*g) {
+                cudaGraphExecDestroy(*g);
+                *g = nullptr;
+            }
+    }
     return DTS_OK;
 }
 

@@ -318,10 +318,11 @@ class Problem:
         m = np.ascontiguousarray(moments, dtype=np.float64).reshape(-1)
         _check(lib().dts_set_initial_guess(self._h, b, _dptr(m), m.size, 0), self._h)
 
-    def debug_poison_wait(self, on: bool):
-        """Make the tensor-core moment kernel's flux-stage waits run out (their
-        bound ends them; the solve returns DTS_ERR_TIMEOUT), or stop doing so."""
-        _check(lib().dts_debug_poison_wait(self._h, int(bool(on))), self._h)
+    def debug_poison_wait(self, on: bool, sweep: bool = False):
+        """Make the tensor-core moment kernel's flux-stage waits (or, with
+        sweep=True, the sweep's face-copy waits) run out (their bound ends them;
+        the solve returns DTS_ERR_TIMEOUT), or stop doing so."""
+        _check(lib().dts_debug_poison_wait(self._h, (2 if sweep else 1) if on else 0), self._h)
 
     def on_iteration(self, fn):
         """Call fn(group, iteration, residuals) after every source iteration of a

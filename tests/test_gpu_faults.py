@@ -58,6 +58,34 @@ def test_bounded_wait_runs_out_and_the_problem_recovers():
     assert e.value.status == dts.DTS_ERR_STATE
 
 
+def test_sweep_face_wait_runs_out_and_the_problem_recovers():
+    """The sweep's bounded face-copy wait made to run out (dts_debug_poison_wait on = 2): every tile's
+    first wait expects 16 bytes more than its copies bring, gives up after about a second, the warp
+    waits (bounded) for the copies it did issue and leaves the tile, and the solve returns
+    DTS_ERR_TIMEOUT; without the hook the problem solves bit for bit as before. On an 8^3 grid of
+    8x4x4 tiles the inner tiles have real y- and z-face copies in flight when their wait gives up."""
+    import time
+    w = inputs.small_cone(8, 8, 8, n_groups=1, sn_order=8, legendre_order=3, n_sources=2)
+    ref = dts.problem_from_workload(w, precision=dts.PREC_FP32_SPLITBF16, tol=0.0, max_iters=2)
+    ref.solve(allow_not_converged=True)
+    p = dts.problem_from_workload(w, precision=dts.PREC_FP32_SPLITBF16, tol=0.0, max_iters=2)
+    p.solve(allow_not_converged=True)   # graphs captured without the hook first
+    p.debug_poison_wait(True, sweep=True)
+    t0 = time.perf_counter()
+    with pytest.raises(dts.DTSError) as e:
+        p.solve()
+    dt = time.perf_counter() - t0
+    assert e.value.status == dts.DTS_ERR_TIMEOUT and "bounded wait" in str(e.value)
+    assert dt < 30.0, dt
+    p.debug_poison_wait(False)
+    p.solve(allow_not_converged=True)
+    for b in range(2):
+        assert np.array_equal(p.fluence(b, dts.TOTAL), ref.fluence(b, dts.TOTAL))
+    with pytest.raises(dts.DTSError) as e:
+        dts._check(dts.lib().dts_debug_poison_wait(p._h, 3), p._h)
+    assert e.value.status == dts.DTS_ERR_INVALID_ARG
+
+
 def test_injected_failures_in_output_and_restart_setup():
     """An allocation failing halfway through dts_set_host_output (its second staging slot) or
     dts_set_initial_guess (the guess after its staging T): DTS_ERR_OOM, and the problem still
