@@ -13,6 +13,7 @@
 //   F    [W+1][B][NT][K][TV] R    fixed-source ring (first-collision + downscatter)
 //   xf   [8][B][NTy*NTz][NDO][TY*TZ] R  x-faces in flight (likewise yf, zf)
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -169,6 +170,9 @@ struct SweepParams {
     size_t n_stage_tiles, n_T, n_sigt, n_part, n_xf, n_yf, n_zf, n_leak;
     int* err = nullptr;            // set when a bounded wait on a bulk copy gave up (Q-input sweep), or null
     unsigned poison_tx = 0;        // test hook (dts_debug_poison_wait): bytes the face wait expects beyond its copies
+    // Q-input sweep: tensor map of Q as 4-D {cell TV, direction NDO, octant x tile 8 NT, source B} (FP32),
+    // box {line BX, NDO, 1, sources per warp}: one TMA per line lands every lane's row in lane order
+    CUtensorMap qmap;
 };
 
 template <typename R, int NDO, int K>
@@ -667,9 +671,11 @@ struct BatchShape {
     static constexpr int oY = oX + (QIN ? 0 : fxn * 32);    // [BX][32] y faces of one z-layer, slot = lx
     static constexpr int oZ = oY + BX * 32;             // [fzn][32] z faces, slot = ly * BX + lx
     static constexpr int oS = oZ + fzn * 32;            // [NLINE][BX] sigma_t, local line, storage x
-    // with the Q input, two mbarriers (8 bytes each) of the bulk copies that land the faces
+    // with the Q input, four mbarriers (8 bytes each): the faces' bulk copies (tile prologue, y layers)
+    // and the Q ring's two slots
     static constexpr int oB = (oS + BV + 3) & ~3;
-    static constexpr int nF = oB + (QIN ? 4 : 0);
+    static constexpr int nF = oB + (QIN ? 8 : 0);
+    static constexpr uint32_t QBOX = 4u * BX * NL;      // bytes of one line's Q box (lanes 0..NL-1)
     static constexpr size_t bytes = sizeof(float) * nF;
 };
 
@@ -841,14 +847,15 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     constexpr int BY = S::BY, BZ = S::BZ, BV = S::BV, SB = S::SB, NL = S::NL, NQ = S::NQ;
     constexpr int TSTR = S::TSTR, PSTR = S::PSTR, NH = S::NH, NJ = S::NJ, NCP = S::NCP;
     constexpr int fxn = S::fxn, fyn = S::fyn, fzn = S::fzn;
-    extern __shared__ __align__(16) float smf[];
+    extern __shared__ __align__(128) float smf[];
     float* Tst = smf + S::oT;
     float* Ps = smf + S::oP;
     float* fx = smf + S::oX;
     float* fy = smf + S::oY;
     float* fz = smf + S::oZ;
     float* sg = smf + S::oS;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smf + S::oB);   // Q input: [0] tile prologue, [1] y layers
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smf + S::oB);   // Q input: [0] tile prologue, [1] y layers,
+                                                                  // [2], [3] the Q ring's slots
 
     const int lane = threadIdx.x;
     const int b0 = grp * SB, nb = min(SB, p.B - b0);
@@ -939,28 +946,41 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
     float* prow = Ps + (srcok ? bl : 0) * PSTR + d * BX;
     const size_t lane_ofs = ((((size_t)(b0 + (srcok ? bl : 0)) * 8 + oct) * p.NT + tile) * NDO + d) * BV;
     float* psi_lane = p.part + lane_ofs;
-    // Q input: the lane's per-direction source Q[b][oct][tile][d][cell] of a line (BX floats),
-    // copied one line ahead into the lane's slot of a two-line ring
-    const float* q_lane = p.T + lane_ofs;
+    // Q input: the line's per-direction source Q[b][oct][tile][d][cell] of the warp's sources (BX
+    // floats per lane), landed one line ahead into a slot of a two-line ring by one tensor-map TMA issued
+    // by lane 0: the box {BX cells, NDO directions, 1, SB sources} arrives in lane order (lane = source x
+    // NDO + direction); sources past B arrive as zeros. Lanes of sources that have stopped iterating sweep
+    // their last Q (valid values; nothing of theirs is stored).
     auto stage_q = [&](int line) {
-        if (!srcok) return;
+        if (lane != 0) return;
         const int ly = line % BY, lz = line / BY;
         const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
-        const float* src = q_lane + (sz * BY + sy) * BX;
-        float* dst = Tst + ((line % S::QRING) * 32 + lane) * BX;
-#pragma unroll
-        for (int h = 0; h < BX / 4; ++h) cp_async16(dst + 4 * h, src + 4 * h);
+        uint64_t* qb = &bars[2 + (line & 1)];
+        fence_async_smem();   // the slot's earlier reads (ordered by the caller's __syncwarp) come first
+        mbar_expect_tx(qb, S::QBOX);
+        tma_load_4d(Tst + (line % S::QRING) * 32 * BX, &p.qmap, (sz * BY + sy) * BX, 0, oct * p.NT + tile, b0, qb);
     };
     if constexpr (QIN) {
-        // a lane without a source sweeps zeros: its ring slots are never copied to
-        if (!srcok) {
+        if (lane == 0) {   // every mbarrier of the tile, before the first copy is issued
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+            fence_mbar_init();
+        }
+        // the ring's TMA destination must be 128-byte aligned: a shared window that is not (never seen)
+        // ends the tile before any copy, with the error word set
+        if ((smem_addr(Tst) & 127u) != 0u) {
+            if (lane == 0 && p.err) atomicExch(p.err, 1);
+            return;
+        }
+        // the lanes past the warp's sources (no copy writes their slots) sweep zeros
+        if (lane >= NL) {
 #pragma unroll
             for (int r = 0; r < S::QRING; ++r)
 #pragma unroll
                 for (int h = 0; h < BX / 4; ++h)
                     *reinterpret_cast<float4*>(Tst + (r * 32 + lane) * BX + 4 * h) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        stage_q(0);   // committed with the prologue's copies
+        stage_q(0);
     }
 
     // phase C lane: (moment kc, group h); items (source il, quad qd) = h + NH * j
@@ -1009,9 +1029,6 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         // the tile's incoming z-faces and z-layer 0's y-faces: one bulk copy (TMA) each from their
         // contiguous face blocks, issued by lane 0 on bars[0]; on an inflow boundary the lanes write zeros
         if (lane == 0) {
-            mbar_init(&bars[0], 1);
-            mbar_init(&bars[1], 1);
-            fence_mbar_init();
             mbar_expect_tx(&bars[0], (tc > 0 ? fzn * 128u : 0u) + (tb > 0 ? BX * 128u : 0u) + p.poison_tx);
             if (tc > 0) bulk_load(fz, gz, fzn * 128u, &bars[0]);
             if (tb > 0) bulk_load(fy, gy, BX * 128u, &bars[0]);
@@ -1037,22 +1054,32 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 
 #pragma unroll 1
     for (int line = 0; line < S::NLINE; ++line) {
-        cp_async_wait0();   // this line's sources (copied during the previous line's walk)
+        // this line's sources (copied during the previous line's walk; with the Q input the cp.async
+        // group is the prologue's sigma_t only)
+        if (!QIN || line == 0) cp_async_wait0();
         __syncwarp();
         const int ly = line % BY, lz = line / BY;
         const int sy = negy ? BY - 1 - ly : ly, sz = negz ? BZ - 1 - lz : lz;
         if constexpr (QIN) {
-            // a layer's first line: line 0 waits for the tile's faces (bars[0]), later layers for their
-            // y-faces (bars[1], the (lz - 1)-th copy on it); a wait that gives up ends the sweep of the tile
+            // this line's Q (ring slot line & 1, its (line >> 1)-th copy); at a layer's first line also the
+            // faces: line 0 the tile's (bars[0]), later layers their y-faces (bars[1], the (lz - 1)-th copy
+            // on it). A wait that gives up ends the sweep of the tile.
+            uint64_t* qb = &bars[2 + (line & 1)];
+            const uint32_t qpar = (uint32_t)((line >> 1) & 1);
+            bool ok = mbar_wait(qb, qpar);
+            uint64_t* fb = nullptr;
+            uint32_t fpar = 0u;
             if (ly == 0 && (lz == 0 || tb > 0)) {
-                uint64_t* bar = lz == 0 ? &bars[0] : &bars[1];
-                const uint32_t parity = lz == 0 ? 0u : (uint32_t)((lz - 1) & 1);
-                if (!__all_sync(0xffffffffu, mbar_wait(bar, parity))) {
-                    if (lane == 0 && p.err) atomicExch(p.err, 1);
-                    (void)mbar_wait(bar, parity);   // its copies, should they still land (bounded)
-                    __syncwarp();
-                    return;
-                }
+                fb = lz == 0 ? &bars[0] : &bars[1];
+                fpar = lz == 0 ? 0u : (uint32_t)((lz - 1) & 1);
+                ok = mbar_wait(fb, fpar) && ok;
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0 && p.err) atomicExch(p.err, 1);
+                (void)mbar_wait(qb, qpar);   // the copies, should they still land (bounded)
+                if (fb) (void)mbar_wait(fb, fpar);
+                __syncwarp();
+                return;
             }
         }
 
@@ -1105,7 +1132,6 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
             if (line + 1 < S::NLINE) stage_line(line + 1, 0);
         } else {
             if (line + 1 < S::NLINE) stage_q(line + 1);   // into the slot of the line before this one
-            cp_async_commit();
         }
 
         // B: walk the line
@@ -1230,7 +1256,8 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 // s0, cnt: the stage's first entry in stage_tiles and its tile count (kernel
 // arguments, so a CTA's first dependent global load is its tile)
 template <int NDO, int K, int BX, bool PSI, bool QIN = false>
-__global__ void __launch_bounds__(32, QIN ? 28 : 17) k_sweep_batch(const SweepParams<float> p, const int s0, const int cnt)
+__global__ void __launch_bounds__(32, QIN ? 28 : 17) k_sweep_batch(const __grid_constant__ SweepParams<float> p,
+                                                                      const int s0, const int cnt)
 {
     using S = BatchShape<NDO, K, BX, PSI, QIN>;
     int bid = blockIdx.x;

@@ -88,4 +88,18 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // until the shared-memory sources of this thread's committed bulk stores have been read
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
+// global -> shared tiled copy through a tensor map (TMA, cp.async.bulk.tensor) of a 4-D box at element
+// coordinates (c0 innermost; c0 * element size a multiple of 16 bytes); tmap is the generic address
+// of a CUtensorMap in kernel-parameter (__grid_constant__), constant or global memory; dst 128-byte
+// aligned. Elements outside the tensor arrive as zeros, and the box's full size counts toward bar.
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
 }  // namespace dts

@@ -6,6 +6,8 @@
 // convergence control, and a CUDA graph holding one iteration (all tile
 // stages of the sweep, the Eq. 3 reduction and the residual), replayed for
 // every iteration of every group.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -625,6 +627,38 @@ QParams q_params(const dts_problem* p, int init)
     return q;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once (the library links only the runtime)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// The Q-input sweep's tensor map of Q [B][8][NT][NDO][TV] (FP32): 4-D {TV, NDO, 8 NT, B} (octant and
+// tile merged: their strides are uniform), box {TX, NDO, 1, sources per warp}, zeros outside
+dts_status encode_qmap(dts_problem* p, CUtensorMap* map)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(p, DTS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t row = (cuuint64_t)p->TV * sizeof(float);
+    const cuuint64_t dim[4] = {(cuuint64_t)p->TV, (cuuint64_t)p->ndo, 8ull * (cuuint64_t)p->NT, (cuuint64_t)p->B};
+    const cuuint64_t stride[3] = {row, row * p->ndo, row * p->ndo * 8ull * (cuuint64_t)p->NT};
+    const cuuint32_t box[4] = {(cuuint32_t)p->TX, (cuuint32_t)p->ndo, 1u, (cuuint32_t)batch_sources_per_warp(p)};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->Qbuf, dim, stride, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(p, DTS_ERR_CUDA, "cuTensorMapEncodeTiled of Q: error " + std::to_string((int)r));
+    return DTS_OK;
+}
+
 template <typename R>
 dts_status record_sweep(dts_problem* p)
 {
@@ -648,6 +682,7 @@ dts_status record_sweep(dts_problem* p)
     const size_t smem = sweep_smem(p);
     if constexpr (sizeof(R) == 4) {
         if (batch_tile(p)) {   // the batched kernel takes the stage's (first tile, count) directly
+            if (p->q_mode) TRY(encode_qmap(p, &sp.qmap));
             BatchFn bf = batch_fn(p);
             if (!bf) return fail(p, DTS_ERR_INTERNAL, "no sweep kernel for this (S_N, P_L)");
             const unsigned groups = (unsigned)((p->B + batch_sources_per_warp(p) - 1) / batch_sources_per_warp(p));
