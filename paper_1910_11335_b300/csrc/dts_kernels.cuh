@@ -170,9 +170,6 @@ struct SweepParams {
     size_t n_stage_tiles, n_T, n_sigt, n_part, n_xf, n_yf, n_zf, n_leak;
     int* err = nullptr;            // set when a bounded wait on a bulk copy gave up (Q-input sweep), or null
     unsigned poison_tx = 0;        // test hook (dts_debug_poison_wait): bytes the face wait expects beyond its copies
-    // Q-input sweep: tensor map of Q as 4-D {cell TV, direction NDO, octant x tile 8 NT, source B} (FP32),
-    // box {line BX, NDO, 1, sources per warp}: one TMA per line lands every lane's row in lane order
-    CUtensorMap qmap;
 };
 
 template <typename R, int NDO, int K>
@@ -838,7 +835,8 @@ __device__ __forceinline__ void batch_line(float (&qv)[BX], float (&yv)[BX], flo
 }
 
 template <int NDO, int K, int BX, bool PSI, bool NX, bool QIN>
-__device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, const int oct, const int grp,
+__device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, const CUtensorMap* qmap,
+                                                 const int oct, const int grp,
                                                  const int ta, const int tb, const int tc, const unsigned okmask,
                                                  const float (&mrow)[K], const float (&arow)[3])
 {
@@ -958,7 +956,7 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
         uint64_t* qb = &bars[2 + (line & 1)];
         fence_async_smem();   // the slot's earlier reads (ordered by the caller's __syncwarp) come first
         mbar_expect_tx(qb, S::QBOX);
-        tma_load_4d(Tst + (line % S::QRING) * 32 * BX, &p.qmap, (sz * BY + sy) * BX, 0, oct * p.NT + tile, b0, qb);
+        tma_load_4d(Tst + (line % S::QRING) * 32 * BX, qmap, (sz * BY + sy) * BX, 0, oct * p.NT + tile, b0, qb);
     };
     if constexpr (QIN) {
         if (lane == 0) {   // every mbarrier of the tile, before the first copy is issued
@@ -1256,8 +1254,12 @@ __device__ __forceinline__ void sweep_batch_body(const SweepParams<float>& p, co
 // s0, cnt: the stage's first entry in stage_tiles and its tile count (kernel
 // arguments, so a CTA's first dependent global load is its tile)
 template <int NDO, int K, int BX, bool PSI, bool QIN = false>
-__global__ void __launch_bounds__(32, QIN ? 28 : 17) k_sweep_batch(const __grid_constant__ SweepParams<float> p,
-                                                                      const int s0, const int cnt)
+// qmap (the Q-input form only): tensor map of Q as 4-D {cell TV, direction NDO, octant x tile 8 NT,
+// source B} (FP32), box {line BX, NDO, 1, sources per warp}, so that one TMA per line lands every
+// lane's row in lane order
+__global__ void __launch_bounds__(32, QIN ? 28 : 17) k_sweep_batch(const SweepParams<float> p, const int s0,
+                                                                      const int cnt,
+                                                                      const __grid_constant__ CUtensorMap qmap)
 {
     using S = BatchShape<NDO, K, BX, PSI, QIN>;
     int bid = blockIdx.x;
@@ -1281,10 +1283,10 @@ __global__ void __launch_bounds__(32, QIN ? 28 : 17) k_sweep_batch(const __grid_
     if (okmask == 0) return;
     const int ta = pk & 1023, tb = (pk >> 10) & 1023, tc = (pk >> 20) & 1023;
     if constexpr (QIN) {   // one body: the octant's x order is in the data
-        sweep_batch_body<NDO, K, BX, PSI, false, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+        sweep_batch_body<NDO, K, BX, PSI, false, QIN>(p, &qmap, oct, grp, ta, tb, tc, okmask, mrow, arow);
     } else {
-        if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
-        else sweep_batch_body<NDO, K, BX, PSI, false, QIN>(p, oct, grp, ta, tb, tc, okmask, mrow, arow);
+        if (oct & 1) sweep_batch_body<NDO, K, BX, PSI, true, QIN>(p, &qmap, oct, grp, ta, tb, tc, okmask, mrow, arow);
+        else sweep_batch_body<NDO, K, BX, PSI, false, QIN>(p, &qmap, oct, grp, ta, tb, tc, okmask, mrow, arow);
     }
 }
 

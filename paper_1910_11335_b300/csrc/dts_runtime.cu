@@ -456,7 +456,7 @@ int batch_sources_per_warp(const dts_problem* p) { return 32 / p->ndo; }
 // partials, so it is taken where that is less traffic (e.g. S8 with P3)
 bool psi_form(const dts_problem* p) { return batch_tile(p) && 8 * p->K > p->nd; }
 
-using BatchFn = void (*)(const SweepParams<float>, int, int);
+using BatchFn = void (*)(const SweepParams<float>, int, int, const CUtensorMap);
 
 template <int NDO, int BX, bool PSI>
 BatchFn batch_fn_k(int K)
@@ -682,13 +682,14 @@ dts_status record_sweep(dts_problem* p)
     const size_t smem = sweep_smem(p);
     if constexpr (sizeof(R) == 4) {
         if (batch_tile(p)) {   // the batched kernel takes the stage's (first tile, count) directly
-            if (p->q_mode) TRY(encode_qmap(p, &sp.qmap));
+            CUtensorMap qmap{};   // read by the Q-input form only
+            if (p->q_mode) TRY(encode_qmap(p, &qmap));
             BatchFn bf = batch_fn(p);
             if (!bf) return fail(p, DTS_ERR_INTERNAL, "no sweep kernel for this (S_N, P_L)");
             const unsigned groups = (unsigned)((p->B + batch_sources_per_warp(p) - 1) / batch_sources_per_warp(p));
             for (int s = 0; s < p->n_stages; ++s) {
                 const int s0 = p->stage_off_h[s], cnt = p->stage_off_h[s + 1] - s0;
-                bf<<<(unsigned)cnt * 8u * groups, 32, smem, p->stream>>>(sp, s0, cnt);
+                bf<<<(unsigned)cnt * 8u * groups, 32, smem, p->stream>>>(sp, s0, cnt, qmap);
             }
             return DTS_OK;
         }

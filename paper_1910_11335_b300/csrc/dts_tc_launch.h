@@ -9,7 +9,7 @@ namespace dts {
 struct QParams;
 }
 
-using dts_internal_batch_fn = void (*)(const dts::SweepParams<float>, int, int);
+using dts_internal_batch_fn = void (*)(const dts::SweepParams<float>, int, int, const CUtensorMap);
 
 // dynamic shared memory of k_moments_q<ndo, K, mode> (mode 0 split BF16, 1 TF32); -1 if unsupported
 int dts_internal_q_smem(int ndo, int K, int mode);
