@@ -68,6 +68,10 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert e.value.status == dts.DTS_ERR_INVALID_ARG
     with pytest.raises(dts.DTSError):
         dts.moment_tables(4, 4)
+    # entry points on a problem reject a NULL problem before any device work
+    for rc in (lib.dts_set_device_loop(None, 1), lib.dts_debug_poison_wait(None, 1),
+               lib.dts_set_iteration_callback(None, dts.IterationFn(), None)):
+        assert rc == dts.DTS_ERR_INVALID_ARG
 
 
 def test_create_without_usable_device_fails_loudly(lib):
